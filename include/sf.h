@@ -1,0 +1,177 @@
+/*
+ * sf.h -- C ABI of the GB300 (sm_103a) SF-sketch library.
+ *
+ * The SF-sketch (Yang et al., "SF-sketch: A Two-stage Sketch for Data Streams") keeps two
+ * subsketches at a monitoring node:
+ *   - the Slim-subsketch A: d arrays of w uint32 counters A_i[j]            (Sec. 3.1, Table 1)
+ *   - the Fat-subsketch  B: d arrays of w buckets of z uint32 counters B_i[j][k]; the bucket of
+ *     item e in row i is h_i(e) (shared with the Slim), the counter inside it is f_i(e)
+ *                                                                           (Sec. 3.4, SF_4/SF_F)
+ * Insertions and deletions update the Fat, read it back, and then raise or lower the item's
+ * Slim counters (Sec. 3.4 "Insertion", Sec. 3.5 "Deletion").  Only the Slim is sent to the
+ * remote collector (Abstract; Sec. 1.1), which answers point queries as the minimum of the
+ * item's d Slim counters (Sec. 3.1 "Query").
+ *
+ * Batched semantics.  The paper updates one item at a time.  A call here processes its stream
+ * in chunks of params.chunk = S updates (a call always starts a new chunk; the last chunk may
+ * be short).  With A0, B0 the state at chunk start: the Fat receives every +1/-1 of the chunk;
+ * each distinct key e inserted c_e times in the chunk raises its Slim counters to
+ *     T_e = min( min_i A0_i[h_i(e)] + c_e ,  min_i B_i[h_i(e)][f_i(e)] after the chunk );
+ * each delete lowers A_i[h_i(e)] to max_k B_i[h_i(e)][k] after the chunk when it is larger;
+ * per counter these operations apply in stream order.  S = 1 is exactly the paper's
+ * one-at-a-time rule.  The result is a deterministic function of the input: every counter
+ * is an exact integer, independent of thread scheduling.
+ *
+ * Hashing (the paper asks only for independent uniform h_i, f_i): row seeds are the first d
+ * outputs of SplitMix64 from params.seed; H_i = mix64(x0 ^ s_i) for keys of at most 8 bytes,
+ * mix64(mix64(x0 ^ s_i) ^ x1) for longer keys (x0, x1 = key bytes 0..7 and 8..15 read
+ * little-endian, zero-padded); h_i = (hi32(H_i) * w) >> 32, f_i = (lo32(H_i) * z) >> 32.
+ *
+ * Memory ownership.  The caller allocates every device buffer (Fat, Slim, scratch, keys,
+ * outputs) and keeps it alive while the handle uses it; sf_required_bytes gives the sizes.
+ * The library allocates no device memory.  Every call is asynchronous on the handle's
+ * CUDA stream; sf_sync waits and reports errors raised on the device.  A handle is used
+ * by one host thread at a time.
+ *
+ * Errors.  No exception crosses the ABI.  Argument errors return immediately; errors found
+ * on the device are latched in the scratch buffer and returned by the next sf_sync.
+ */
+#ifndef SF_H_
+#define SF_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t sf_status;
+
+#define SF_OK              0
+#define SF_ERR_INVALID    -1  /* bad argument, handle, alignment or key id                  */
+#define SF_ERR_OOM        -2  /* a caller buffer is smaller than required                   */
+#define SF_ERR_CUDA       -3  /* a CUDA runtime call failed                                 */
+#define SF_ERR_TIMEOUT    -4  /* a device-side wait gave up; the sketch contents are lost   */
+#define SF_ERR_UNDERFLOW  -5  /* a delete removed an occurrence that was never inserted     */
+#define SF_ERR_BUDGET     -6  /* collector: upload not admissible under the memory budget   */
+#define SF_ERR_VERSION    -7  /* Slim header magic/version/hash id mismatch                 */
+#define SF_PENDING         1  /* collector: ticket not finished yet                         */
+
+#define SF_MAX_D 8
+#define SF_MAX_Z 64
+#define SF_MAX_KEY_BYTES 16
+
+#define SF_SLIM_MAGIC   0x4D494C53u  /* "SLIM" */
+#define SF_SLIM_VERSION 1u
+#define SF_HASH_SPLITMIX_LEMIRE 1u   /* the hash described above                           */
+#define SF_HASH_EXPLICIT        2u   /* indices from a caller table (explicit-index mode)  */
+
+/* params.flags */
+#define SF_FLAG_EXPLICIT_INDEX 1u    /* keys are uint32 ids into a table of (h_i, f_i)    */
+
+typedef struct sf_params {
+    uint32_t d;          /* rows, 1..SF_MAX_D                                   (Table 1: d) */
+    uint32_t w;          /* Slim counters per row = Fat buckets per row, >= 1   (Table 1: w) */
+    uint32_t z;          /* Fat counters per bucket, 1..SF_MAX_Z                (Table 1: z) */
+    uint32_t key_bytes;  /* packed key width, 1..SF_MAX_KEY_BYTES (4 in explicit mode)       */
+    uint64_t seed;       /* hash seed                                                        */
+    uint32_t chunk;      /* S >= 1 updates per chunk (semantic: see above)                   */
+    uint32_t flags;      /* SF_FLAG_*                                                        */
+} sf_params;
+
+typedef struct sf_slim_header {
+    uint32_t magic;      /* SF_SLIM_MAGIC   */
+    uint32_t version;    /* SF_SLIM_VERSION */
+    uint32_t d, w, key_bytes, hash_id;
+    uint64_t seed;
+} sf_slim_header;
+
+/* A Slim-subsketch as the collector sees it: d*w uint32 counters, row-major A[i*w + j]. */
+typedef struct sf_slim_view {
+    const uint32_t *counters;       /* device */
+    sf_slim_header hdr;
+    const uint32_t *index_table;    /* device, explicit-index mode only, else NULL */
+    uint32_t n_index_keys;
+} sf_slim_view;
+
+typedef struct sf_sketch sf_sketch;
+
+/* Human-readable name of a status code (static string). */
+const char *sf_status_str(sf_status s);
+
+/*
+ * Device bytes the caller must provide for a sketch with these parameters
+ * (Sec. 3.4: the Fat is d*w*z counters, the Slim d*w counters).
+ *   fat_bytes     = d*w*z*4, layout B[((i*w + j)*z + k]  (bucket-contiguous, Sec. 3.4: all z
+ *                   counters of a bucket sit together so one access reads them)
+ *   slim_bytes    = d*w*4,   layout A[i*w + j]
+ *   scratch_bytes = control words + the per-chunk key dictionary (grows with params.chunk)
+ * Any output pointer may be NULL.  Returns SF_ERR_INVALID for parameters out of range.
+ */
+sf_status sf_required_bytes(const sf_params *p, uint64_t *fat_bytes, uint64_t *slim_bytes,
+                            uint64_t *scratch_bytes);
+
+/*
+ * Initialisation (Sec. 3.1: all counters set to zero): zeroes the Fat, the Slim and the
+ * scratch on `cuda_stream` (a cudaStream_t; NULL = the legacy default stream) and returns a
+ * host handle in *out.  Buffers: device memory of at least sf_required_bytes, 16-byte aligned,
+ * owned by the caller and not freed before sf_destroy.  The handle captures the current device.
+ */
+sf_status sf_create(const sf_params *p, void *fat_dev, void *slim_dev, void *scratch_dev,
+                    void *cuda_stream, sf_sketch **out);
+
+/* Releases the host handle (not the caller's device buffers).  Does not synchronise. */
+sf_status sf_destroy(sf_sketch *s);
+
+/*
+ * Explicit-index mode (params.flags & SF_FLAG_EXPLICIT_INDEX): keys are uint32 ids and the
+ * device table holds, for id q and row i, h_i = table[(q*d + i)*2], f_i = table[(q*d + i)*2 + 1]
+ * (h_i < w, f_i < z).  Used to replay worked examples with hand-chosen indices (Sec. 3.2).
+ * Ids >= n_keys are rejected on the device (SF_ERR_INVALID at the next sf_sync).
+ */
+sf_status sf_set_index_table(sf_sketch *s, const uint32_t *table_dev, uint32_t n_keys);
+
+/*
+ * Insertion of n items (Sec. 3.4 "Insertion", used unchanged by SF_F, Sec. 3.5), under the
+ * chunked semantics above.  keys_dev: n*key_bytes packed bytes on the device (4- or 8-byte
+ * keys must be aligned to their width).  n = 0 is a no-op.  Asynchronous.
+ */
+sf_status sf_insert_batch(sf_sketch *s, const void *keys_dev, uint64_t n);
+
+/*
+ * Deletion of n items (Sec. 3.5 "Deletion").  Precondition: every deleted occurrence was
+ * inserted before (the paper's proofs assume it).  A Fat counter seen negative at the end
+ * of a chunk is reported as SF_ERR_UNDERFLOW by sf_sync; counters are then unspecified.
+ */
+sf_status sf_delete_batch(sf_sketch *s, const void *keys_dev, uint64_t n);
+
+/*
+ * Mixed stream: ops_dev[t] = +1 (insert) or -1 (delete) for key t, stream order preserved
+ * inside each chunk; 0 skips the update.  Same rules as the two calls above.
+ */
+sf_status sf_update_batch(sf_sketch *s, const void *keys_dev, const int8_t *ops_dev, uint64_t n);
+
+/*
+ * Slim transfer (Abstract, Sec. 1.1: only the Slim goes to the collector): copies the d*w
+ * Slim counters to dst_dev (device, cap_elems >= d*w) after all queued updates, on the
+ * handle's stream, and fills *hdr (may be NULL).  SF_ERR_OOM if cap_elems is too small.
+ */
+sf_status sf_export_slim(const sf_sketch *s, uint32_t *dst_dev, uint64_t cap_elems,
+                         sf_slim_header *hdr);
+
+/*
+ * Point queries (Sec. 3.1 "Query"): out_dev[t] = min_i A_i[h_i(key_t)] on an exported Slim.
+ * keys_dev: n packed keys of slim->hdr.key_bytes bytes (device); out_dev: n uint32 (device).
+ * Runs on cuda_stream.  SF_ERR_VERSION if the header is not a Slim of this library.
+ */
+sf_status sf_query_batch(const sf_slim_view *slim, const void *keys_dev, uint64_t n,
+                         uint32_t *out_dev, void *cuda_stream);
+
+/* Waits for the handle's stream and returns (then clears) errors latched on the device. */
+sf_status sf_sync(sf_sketch *s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SF_H_ */

@@ -1,0 +1,265 @@
+"""GB300 (sm_103a) SF-sketch: Python binding of the C ABI in include/sf.h.
+
+Argument marshalling only: every step of insert, delete, export and query runs in the CUDA
+library ``_build/libsfgb300.so``.  PyTorch supplies device memory and streams.  There is no
+CPU fallback: ``load()`` raises if the library is missing or no GPU is present.
+
+    import torch, paper_1701_04148_gb300 as sf
+    sk = sf.Sketch(d=4, w=1 << 18, z=16, key_bytes=13, seed=2, chunk=65536)
+    sk.insert(keys_u8_on_gpu)          # (n, 13) uint8 device tensor
+    slim, hdr = sk.export_slim()
+    est = sf.query(slim, hdr, flows_u8_on_gpu)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsfgb300.so")
+
+SF_OK = 0
+SF_ERR_INVALID = -1
+SF_ERR_OOM = -2
+SF_ERR_CUDA = -3
+SF_ERR_TIMEOUT = -4
+SF_ERR_UNDERFLOW = -5
+SF_ERR_BUDGET = -6
+SF_ERR_VERSION = -7
+SF_PENDING = 1
+SF_FLAG_EXPLICIT_INDEX = 1
+SF_SLIM_MAGIC = 0x4D494C53
+SF_HASH_SPLITMIX_LEMIRE = 1
+SF_HASH_EXPLICIT = 2
+
+
+class SFError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_str(status)} ({status})")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_uint32), ("w", ctypes.c_uint32), ("z", ctypes.c_uint32),
+                ("key_bytes", ctypes.c_uint32), ("seed", ctypes.c_uint64),
+                ("chunk", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+
+
+class SlimHeader(ctypes.Structure):
+    _fields_ = [("magic", ctypes.c_uint32), ("version", ctypes.c_uint32), ("d", ctypes.c_uint32),
+                ("w", ctypes.c_uint32), ("key_bytes", ctypes.c_uint32), ("hash_id", ctypes.c_uint32),
+                ("seed", ctypes.c_uint64)]
+
+
+class SlimView(ctypes.Structure):
+    _fields_ = [("counters", ctypes.c_void_p), ("hdr", SlimHeader), ("index_table", ctypes.c_void_p),
+                ("n_index_keys", ctypes.c_uint32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "sf_status_str": (ctypes.c_char_p, [ctypes.c_int32]),
+    "sf_required_bytes": (ctypes.c_int32, [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_uint64),
+                                           ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
+    "sf_create": (ctypes.c_int32, [ctypes.POINTER(Params), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "sf_destroy": (ctypes.c_int32, [ctypes.c_void_p]),
+    "sf_set_index_table": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32]),
+    "sf_insert_batch": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64]),
+    "sf_delete_batch": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64]),
+    "sf_update_batch": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64]),
+    "sf_export_slim": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
+                                        ctypes.POINTER(SlimHeader)]),
+    "sf_query_batch": (ctypes.c_int32, [ctypes.POINTER(SlimView), ctypes.c_void_p, ctypes.c_uint64,
+                                        ctypes.c_void_p, ctypes.c_void_p]),
+    "sf_sync": (ctypes.c_int32, [ctypes.c_void_p]),
+}
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGS)
+
+
+def load(path: str | None = None):
+    """Load the CUDA library (raises if it was not built: there is no CPU path)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise RuntimeError(f"SF-sketch CUDA library not built ({p}); run "
+                                   "`python -m paper_1701_04148_gb300.build` on a machine with nvcc")
+            L = ctypes.CDLL(p)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def status_str(st: int) -> str:
+    try:
+        return load().sf_status_str(st).decode()
+    except Exception:  # library not loadable: still name the code
+        return {0: "ok", -1: "invalid argument", -2: "buffer too small", -3: "CUDA runtime error",
+                -4: "device wait timed out", -5: "underflow", -6: "budget", -7: "version"}.get(st, "?")
+
+
+def check(st: int, what: str) -> int:
+    if st < 0:
+        raise SFError(st, what)
+    return st
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream=None) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _dev_ptr(t, what: str) -> int:
+    if t is None:
+        return 0
+    if not t.is_cuda:
+        raise ValueError(f"{what} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    return int(t.data_ptr())
+
+
+def make_params(d, w, z, key_bytes, seed, chunk, flags=0) -> Params:
+    return Params(d, w, z, key_bytes, seed & (2**64 - 1), chunk, flags)
+
+
+def required_bytes(p: Params):
+    fb, sb, xb = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    check(load().sf_required_bytes(ctypes.byref(p), ctypes.byref(fb), ctypes.byref(sb), ctypes.byref(xb)),
+          "sf_required_bytes")
+    return fb.value, sb.value, xb.value
+
+
+class Sketch:
+    """One SF-sketch on the current CUDA device, buffers owned by torch tensors."""
+
+    def __init__(self, d: int, w: int, z: int, key_bytes: int = 4, seed: int = 0, chunk: int = 1,
+                 explicit_index: bool = False, stream=None, device=None):
+        torch = _torch()
+        L = load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the SF-sketch library has no CPU path")
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.params = make_params(d, w, z, key_bytes, seed, chunk, SF_FLAG_EXPLICIT_INDEX if explicit_index else 0)
+        fb, sb, xb = required_bytes(self.params)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        with torch.cuda.device(self.device):
+            self.fat = torch.empty(fb // 4, dtype=torch.int32, device=self.device)
+            self.slim = torch.empty(sb // 4, dtype=torch.int32, device=self.device)
+            self.scratch = torch.empty(max(xb, 16) // 4 + 4, dtype=torch.int32, device=self.device)
+            h = ctypes.c_void_p()
+            check(L.sf_create(ctypes.byref(self.params), self.fat.data_ptr(), self.slim.data_ptr(),
+                              self.scratch.data_ptr(), _stream_handle(self.stream), ctypes.byref(h)), "sf_create")
+        self.handle = h
+        self._index_table = None
+
+    # shapes of the caller-visible views
+    @property
+    def d(self):
+        return self.params.d
+
+    @property
+    def w(self):
+        return self.params.w
+
+    @property
+    def z(self):
+        return self.params.z
+
+    def fat_view(self):
+        return self.fat.view(self.d, self.w, self.z)
+
+    def slim_view(self):
+        return self.slim.view(self.d, self.w)
+
+    def set_index_table(self, table):
+        """Explicit-index mode: table (n_keys, d, 2) uint32/int32 of (h_i, f_i) on the device."""
+        torch = _torch()
+        t = table.to(device=self.device, dtype=torch.int32).contiguous()
+        self._index_table = t
+        check(load().sf_set_index_table(self.handle, t.data_ptr(), t.shape[0]), "sf_set_index_table")
+
+    def _keys(self, keys):
+        if keys.dim() == 2 and keys.dtype == _torch().uint8:
+            if keys.shape[1] != self.params.key_bytes:
+                raise ValueError("key width mismatch")
+            return keys, keys.shape[0]
+        return keys, keys.numel() * keys.element_size() // self.params.key_bytes
+
+    def insert(self, keys):
+        k, n = self._keys(keys)
+        check(load().sf_insert_batch(self.handle, _dev_ptr(k, "keys"), n), "sf_insert_batch")
+
+    def delete(self, keys):
+        k, n = self._keys(keys)
+        check(load().sf_delete_batch(self.handle, _dev_ptr(k, "keys"), n), "sf_delete_batch")
+
+    def update(self, keys, ops):
+        k, n = self._keys(keys)
+        if ops.numel() != n:
+            raise ValueError("ops must have one entry per key")
+        check(load().sf_update_batch(self.handle, _dev_ptr(k, "keys"), _dev_ptr(ops, "ops"), n), "sf_update_batch")
+
+    def sync(self) -> int:
+        return check(load().sf_sync(self.handle), "sf_sync")
+
+    def sync_status(self) -> int:
+        return load().sf_sync(self.handle)
+
+    def export_slim(self, out=None):
+        torch = _torch()
+        n = self.d * self.w
+        if out is None:
+            out = torch.empty(n, dtype=torch.int32, device=self.device)
+        hdr = SlimHeader()
+        check(load().sf_export_slim(self.handle, _dev_ptr(out, "out"), out.numel(), ctypes.byref(hdr)),
+              "sf_export_slim")
+        return out, hdr
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().sf_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def query(slim, hdr: SlimHeader, keys, out=None, stream=None, index_table=None):
+    """Point queries on an exported Slim (device tensors); returns int32 estimates (bit pattern u32)."""
+    torch = _torch()
+    kb = hdr.key_bytes
+    n = keys.shape[0] if (keys.dim() == 2 and keys.dtype == torch.uint8) else keys.numel() * keys.element_size() // kb
+    if out is None:
+        out = torch.empty(n, dtype=torch.int32, device=keys.device)
+    v = SlimView(_dev_ptr(slim, "slim"), hdr, _dev_ptr(index_table, "index_table") if index_table is not None else 0,
+                 index_table.shape[0] if index_table is not None else 0)
+    check(load().sf_query_batch(ctypes.byref(v), _dev_ptr(keys, "keys") if n else 0, n,
+                                _dev_ptr(out, "out") if n else 0, _stream_handle(stream)), "sf_query_batch")
+    return out
+
+
+def as_u32(t):
+    """View an int32 tensor of counters as int64 holding the unsigned values."""
+    return t.to(_torch().int64) & 0xFFFFFFFF

@@ -1,0 +1,284 @@
+// sf_api.cu -- host runtime behind the C ABI of include/sf.h.
+//
+// A handle binds caller-owned device buffers (Fat, Slim, scratch) to one CUDA stream.  No call
+// allocates device memory.  Device-side errors are latched in the control words at the start
+// of the scratch buffer and collected by sf_sync.
+#include <cstdint>
+#include <cstring>
+#include <new>
+
+#include <cuda_runtime.h>
+
+#include "../../include/sf.h"
+#include "sf_internal.h"
+
+struct sf_sketch {
+    sf_params p;
+    uint32_t* A;
+    uint32_t* B;
+    uint8_t* scratch;
+    cudaStream_t stream;
+    int device;
+    int num_sms;
+    int chunk_grid;
+    int smem_optin;
+    uint64_t rs[SF_MAX_D];
+    uint32_t* ctrl;
+    sfk::DictEntry* dict;
+    uint32_t cap;
+    const uint32_t* idx_table;
+    uint32_t n_ids;
+};
+
+namespace {
+
+constexpr uint64_t kCtrlBytes = 256;
+
+uint64_t splitmix64_next(uint64_t* st) {
+    uint64_t z = (*st += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+bool params_ok(const sf_params* p) {
+    if (!p) return false;
+    if (p->d < 1 || p->d > SF_MAX_D) return false;
+    if (p->w < 1 || p->w > 0x7FFFFFFFu) return false;
+    if (p->z < 1 || p->z > SF_MAX_Z) return false;
+    if (p->key_bytes < 1 || p->key_bytes > SF_MAX_KEY_BYTES) return false;
+    if (p->chunk < 1 || p->chunk > (1u << 30)) return false;
+    if ((p->flags & ~SF_FLAG_EXPLICIT_INDEX) != 0) return false;
+    if ((p->flags & SF_FLAG_EXPLICIT_INDEX) && p->key_bytes != 4) return false;
+    if ((uint64_t)p->d * p->w * p->z > (1ull << 40)) return false;
+    return true;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+sfk::SketchDesc desc_of(const sf_sketch* s) {
+    sfk::SketchDesc d{};
+    d.A = s->A;
+    d.B = s->B;
+    d.d = s->p.d;
+    d.w = s->p.w;
+    d.z = s->p.z;
+    d.key_bytes = s->p.key_bytes;
+    for (int i = 0; i < SF_MAX_D; ++i) d.rs[i] = s->rs[i];
+    d.idx_table = s->idx_table;
+    d.n_ids = s->n_ids;
+    return d;
+}
+
+sf_status run_update(sf_sketch* s, const void* keys, const int8_t* ops, int op_const, uint64_t n) {
+    if (!s) return SF_ERR_INVALID;
+    if (n == 0) return SF_OK;
+    if (!keys) return SF_ERR_INVALID;
+    const uint32_t kb = s->p.key_bytes;
+    if ((kb == 4 || kb == 8) && ((uintptr_t)keys % kb) != 0) return SF_ERR_INVALID;
+    if ((s->p.flags & SF_FLAG_EXPLICIT_INDEX) && !s->idx_table) return SF_ERR_INVALID;
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return SF_ERR_CUDA;
+    if (cur != s->device && cudaSetDevice(s->device) != cudaSuccess) return SF_ERR_CUDA;
+    cudaError_t e;
+    if (s->p.chunk == 1) {
+        sfk::SeqArgs a{};
+        a.s = desc_of(s);
+        a.keys = (const uint8_t*)keys;
+        a.ops = ops;
+        a.op_const = op_const;
+        a.n = n;
+        a.ctrl = s->ctrl;
+        e = sfk::launch_seq_update(a, s->stream, s->smem_optin);
+    } else {
+        sfk::ChunkArgs a{};
+        a.s = desc_of(s);
+        a.keys = (const uint8_t*)keys;
+        a.ops = ops;
+        a.op_const = op_const;
+        a.n = n;
+        a.S = s->p.chunk;
+        a.cap_mask = s->cap - 1u;
+        a.dict = s->dict;
+        a.ctrl = s->ctrl;
+        a.timeout_ns = sfk::kBarrierTimeoutNs;
+        e = sfk::launch_chunk_update(a, s->chunk_grid, s->stream);
+    }
+    if (cur != s->device) cudaSetDevice(cur);
+    return e == cudaSuccess ? SF_OK : SF_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sf_status_str(sf_status s) {
+    switch (s) {
+        case SF_OK: return "ok";
+        case SF_ERR_INVALID: return "invalid argument";
+        case SF_ERR_OOM: return "buffer too small";
+        case SF_ERR_CUDA: return "CUDA runtime error";
+        case SF_ERR_TIMEOUT: return "device wait timed out";
+        case SF_ERR_UNDERFLOW: return "delete of an item that was not inserted (Fat counter underflow)";
+        case SF_ERR_BUDGET: return "not admissible under the memory budget";
+        case SF_ERR_VERSION: return "Slim header mismatch";
+        case SF_PENDING: return "pending";
+        default: return "unknown status";
+    }
+}
+
+sf_status sf_required_bytes(const sf_params* p, uint64_t* fat_bytes, uint64_t* slim_bytes,
+                            uint64_t* scratch_bytes) {
+    if (!params_ok(p)) return SF_ERR_INVALID;
+    if (fat_bytes) *fat_bytes = (uint64_t)p->d * p->w * p->z * 4ull;
+    if (slim_bytes) *slim_bytes = (uint64_t)p->d * p->w * 4ull;
+    if (scratch_bytes) {
+        const uint64_t cap = p->chunk > 1 ? sfk::dict_capacity(p->chunk) : 0;
+        *scratch_bytes = kCtrlBytes + cap * sizeof(sfk::DictEntry);
+    }
+    return SF_OK;
+}
+
+sf_status sf_create(const sf_params* p, void* fat_dev, void* slim_dev, void* scratch_dev,
+                    void* cuda_stream, sf_sketch** out) {
+    if (!out) return SF_ERR_INVALID;
+    *out = nullptr;
+    if (!params_ok(p)) return SF_ERR_INVALID;
+    if (!fat_dev || !slim_dev || !scratch_dev) return SF_ERR_INVALID;
+    if (!aligned16(fat_dev) || !aligned16(slim_dev) || !aligned16(scratch_dev)) return SF_ERR_INVALID;
+    sf_sketch* s = new (std::nothrow) sf_sketch();
+    if (!s) return SF_ERR_OOM;
+    s->p = *p;
+    s->A = (uint32_t*)slim_dev;
+    s->B = (uint32_t*)fat_dev;
+    s->scratch = (uint8_t*)scratch_dev;
+    s->stream = (cudaStream_t)cuda_stream;
+    s->ctrl = (uint32_t*)scratch_dev;
+    s->dict = (sfk::DictEntry*)((uint8_t*)scratch_dev + kCtrlBytes);
+    s->cap = p->chunk > 1 ? sfk::dict_capacity(p->chunk) : 0;
+    uint64_t st = p->seed;
+    for (uint32_t i = 0; i < SF_MAX_D; ++i) s->rs[i] = i < p->d ? splitmix64_next(&st) : 0;
+    if (cudaGetDevice(&s->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&s->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device) != cudaSuccess) {
+        delete s;
+        return SF_ERR_CUDA;
+    }
+    const int bps = sfk::chunk_update_blocks_per_sm();
+    if (bps <= 0) {
+        delete s;
+        return SF_ERR_CUDA;
+    }
+    s->chunk_grid = s->num_sms * (bps < 2 ? bps : 2);
+    uint64_t fb, sb, xb;
+    sf_required_bytes(p, &fb, &sb, &xb);
+    if (cudaMemsetAsync(fat_dev, 0, fb, s->stream) != cudaSuccess ||
+        cudaMemsetAsync(slim_dev, 0, sb, s->stream) != cudaSuccess ||
+        cudaMemsetAsync(scratch_dev, 0, xb, s->stream) != cudaSuccess) {
+        delete s;
+        return SF_ERR_CUDA;
+    }
+    *out = s;
+    return SF_OK;
+}
+
+sf_status sf_destroy(sf_sketch* s) {
+    if (!s) return SF_ERR_INVALID;
+    delete s;
+    return SF_OK;
+}
+
+sf_status sf_set_index_table(sf_sketch* s, const uint32_t* table_dev, uint32_t n_keys) {
+    if (!s || !(s->p.flags & SF_FLAG_EXPLICIT_INDEX) || !table_dev) return SF_ERR_INVALID;
+    s->idx_table = table_dev;
+    s->n_ids = n_keys;
+    return SF_OK;
+}
+
+sf_status sf_insert_batch(sf_sketch* s, const void* keys_dev, uint64_t n) {
+    return run_update(s, keys_dev, nullptr, +1, n);
+}
+
+sf_status sf_delete_batch(sf_sketch* s, const void* keys_dev, uint64_t n) {
+    return run_update(s, keys_dev, nullptr, -1, n);
+}
+
+sf_status sf_update_batch(sf_sketch* s, const void* keys_dev, const int8_t* ops_dev, uint64_t n) {
+    if (n && !ops_dev) return SF_ERR_INVALID;
+    return run_update(s, keys_dev, ops_dev, 0, n);
+}
+
+sf_status sf_export_slim(const sf_sketch* s, uint32_t* dst_dev, uint64_t cap_elems, sf_slim_header* hdr) {
+    if (!s || !dst_dev) return SF_ERR_INVALID;
+    const uint64_t nelem = (uint64_t)s->p.d * s->p.w;
+    if (cap_elems < nelem) return SF_ERR_OOM;
+    if (cudaMemcpyAsync(dst_dev, s->A, nelem * 4ull, cudaMemcpyDeviceToDevice, s->stream) != cudaSuccess)
+        return SF_ERR_CUDA;
+    if (hdr) {
+        hdr->magic = SF_SLIM_MAGIC;
+        hdr->version = SF_SLIM_VERSION;
+        hdr->d = s->p.d;
+        hdr->w = s->p.w;
+        hdr->key_bytes = s->p.key_bytes;
+        hdr->hash_id = (s->p.flags & SF_FLAG_EXPLICIT_INDEX) ? SF_HASH_EXPLICIT : SF_HASH_SPLITMIX_LEMIRE;
+        hdr->seed = s->p.seed;
+    }
+    return SF_OK;
+}
+
+sf_status sf_query_batch(const sf_slim_view* v, const void* keys_dev, uint64_t n, uint32_t* out_dev,
+                         void* cuda_stream) {
+    if (!v) return SF_ERR_INVALID;
+    const sf_slim_header& h = v->hdr;
+    if (h.magic != SF_SLIM_MAGIC || h.version != SF_SLIM_VERSION) return SF_ERR_VERSION;
+    if (h.hash_id != SF_HASH_SPLITMIX_LEMIRE && h.hash_id != SF_HASH_EXPLICIT) return SF_ERR_VERSION;
+    if (h.d < 1 || h.d > SF_MAX_D || h.w < 1 || h.key_bytes < 1 || h.key_bytes > SF_MAX_KEY_BYTES)
+        return SF_ERR_INVALID;
+    if (h.hash_id == SF_HASH_EXPLICIT && (!v->index_table || h.key_bytes != 4)) return SF_ERR_INVALID;
+    if (n == 0) return SF_OK;
+    if (!v->counters || !keys_dev || !out_dev) return SF_ERR_INVALID;
+    if ((h.key_bytes == 4 || h.key_bytes == 8) && ((uintptr_t)keys_dev % h.key_bytes) != 0) return SF_ERR_INVALID;
+    sfk::QueryArgs q{};
+    q.s.A = (uint32_t*)v->counters;
+    q.s.B = nullptr;
+    q.s.d = h.d;
+    q.s.w = h.w;
+    q.s.z = 0xFFFFFFFFu;  // a query never reads the Fat: f_i is not bounded by any z here
+    q.s.key_bytes = h.key_bytes;
+    uint64_t st = h.seed;
+    for (uint32_t i = 0; i < SF_MAX_D; ++i) q.s.rs[i] = i < h.d ? splitmix64_next(&st) : 0;
+    q.s.idx_table = h.hash_id == SF_HASH_EXPLICIT ? v->index_table : nullptr;
+    q.s.n_ids = v->n_index_keys;
+    q.keys = (const uint8_t*)keys_dev;
+    q.n = n;
+    q.out = out_dev;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return SF_ERR_CUDA;
+    return sfk::launch_query(q, sms, (cudaStream_t)cuda_stream) == cudaSuccess ? SF_OK : SF_ERR_CUDA;
+}
+
+sf_status sf_sync(sf_sketch* s) {
+    if (!s) return SF_ERR_INVALID;
+    uint32_t err = 0;
+    if (cudaMemcpyAsync(&err, s->ctrl + sfk::kCtrlErr, 4, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess)
+        return SF_ERR_CUDA;
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return SF_ERR_CUDA;
+    if (err == 0) return SF_OK;
+    if (err & sfk::kErrTimeout) {
+        // a grid wait gave up: barrier words and dictionary may be inconsistent; reset them
+        uint64_t xb = 0;
+        sf_required_bytes(&s->p, nullptr, nullptr, &xb);
+        cudaMemsetAsync(s->scratch, 0, xb, s->stream);
+    } else {
+        cudaMemsetAsync(s->ctrl + sfk::kCtrlErr, 0, 4, s->stream);
+    }
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return SF_ERR_CUDA;
+    if (err & sfk::kErrTimeout) return SF_ERR_TIMEOUT;
+    if (err & (sfk::kErrBadKey | sfk::kErrDictFull)) return SF_ERR_INVALID;
+    if (err & sfk::kErrUnderflow) return SF_ERR_UNDERFLOW;
+    return SF_ERR_INVALID;
+}
+
+}  // extern "C"

@@ -1,0 +1,177 @@
+// sf_device.cuh -- device-side building blocks of the SF-sketch kernels (sm_103a).
+//
+// Hashing: SplitMix64's output finaliser (Steele, Lea, Flood, OOPSLA 2014) applied to the key
+// words xor a per-row seed, then multiply-shift range reduction (Lemire, ACM TOMACS 2019):
+//   h_i = (hi32(H_i) * w) >> 32   (bucket / Slim counter, Sec. 3.4: h_i maps to [1, w])
+//   f_i = (lo32(H_i) * z) >> 32   (counter inside the Fat bucket, Sec. 3.4: f_i maps to [1, z])
+// The paper only asks for independent uniformly distributed hash functions (Sec. 3.1, 3.4).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sfk {
+
+constexpr int kMaxD = 8;
+constexpr int kMaxZ = 64;
+
+// Error bits latched in the control block (read and cleared by sf_sync).
+constexpr uint32_t kErrUnderflow = 1u;
+constexpr uint32_t kErrTimeout = 2u;
+constexpr uint32_t kErrBadKey = 4u;
+constexpr uint32_t kErrDictFull = 8u;
+
+// Control block: the first 256 bytes of every scratch buffer.
+enum : uint32_t { kCtrlErr = 0, kCtrlBarCount = 1, kCtrlBarGen = 2, kCtrlWords = 64 };
+
+// Per-chunk key dictionary entry (16 bytes): the first update of the key in the chunk
+// (index + 1, 0 = empty), its inserts c_e, its deletes, and m_e = min_i A0_i[h_i(e)].
+struct DictEntry {
+    uint32_t owner;
+    uint32_t c_ins;
+    uint32_t c_del;
+    uint32_t m;
+};
+
+struct SketchDesc {
+    uint32_t* A;             // Slim, A[i*w + j]
+    uint32_t* B;             // Fat,  B[(i*w + j)*z + k]
+    uint32_t d, w, z, key_bytes;
+    uint64_t rs[kMaxD];      // row seeds
+    const uint32_t* idx_table;  // explicit-index mode table, else nullptr
+    uint32_t n_ids;
+};
+
+__device__ __forceinline__ uint64_t mix64(uint64_t x) {
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+struct Key {
+    uint64_t x0, x1;
+};
+
+// Packed little-endian key t.  4/8-byte keys use one aligned read-only load.
+__device__ __forceinline__ Key load_key(const uint8_t* __restrict__ keys, uint64_t t, uint32_t kb) {
+    Key k{0ull, 0ull};
+    if (kb == 4) {
+        k.x0 = __ldg(reinterpret_cast<const uint32_t*>(keys) + t);
+    } else if (kb == 8) {
+        k.x0 = __ldg(reinterpret_cast<const unsigned long long*>(keys) + t);
+    } else {
+        const uint8_t* p = keys + t * kb;
+        const uint32_t n0 = kb < 8 ? kb : 8;
+        for (uint32_t b = 0; b < n0; ++b) k.x0 |= (uint64_t)__ldg(p + b) << (8 * b);
+        for (uint32_t b = 8; b < kb; ++b) k.x1 |= (uint64_t)__ldg(p + b) << (8 * (b - 8));
+    }
+    return k;
+}
+
+__device__ __forceinline__ uint64_t row_hash(const Key& k, uint32_t kb, uint64_t seed) {
+    uint64_t H = mix64(k.x0 ^ seed);
+    if (kb > 8) H = mix64(H ^ k.x1);
+    return H;
+}
+
+__device__ __forceinline__ uint32_t reduce_hi(uint64_t H, uint32_t range) {
+    return (uint32_t)(((H >> 32) * (uint64_t)range) >> 32);
+}
+
+__device__ __forceinline__ uint32_t reduce_lo(uint64_t H, uint32_t range) {
+    return (uint32_t)(((H & 0xFFFFFFFFull) * (uint64_t)range) >> 32);
+}
+
+// Row indices of one key.  Returns false for a bad key id in explicit-index mode.
+// probe receives a well-mixed 32-bit value independent of the top bits used by h/f.
+__device__ __forceinline__ bool key_indices(const SketchDesc& s, const Key& k, uint32_t* h,
+                                            uint32_t* f, uint32_t* probe) {
+    if (s.idx_table) {
+        const uint64_t id = k.x0;
+        if (id >= s.n_ids) return false;
+        const uint32_t* row = s.idx_table + id * (uint64_t)s.d * 2;
+        bool ok = true;
+#pragma unroll
+        for (int i = 0; i < kMaxD; ++i)
+            if (i < (int)s.d) {
+                h[i] = __ldg(row + 2 * i);
+                f[i] = __ldg(row + 2 * i + 1);
+                ok &= (h[i] < s.w) && (f[i] < s.z);  // a bad table entry must not index out of bounds
+            }
+        *probe = (uint32_t)mix64(id);
+        return ok;
+    }
+    uint64_t H0 = 0;
+#pragma unroll
+    for (int i = 0; i < kMaxD; ++i)
+        if (i < (int)s.d) {
+            const uint64_t H = row_hash(k, s.key_bytes, s.rs[i]);
+            if (i == 0) H0 = H;
+            h[i] = reduce_hi(H, s.w);
+            f[i] = reduce_lo(H, s.z);
+        }
+    *probe = (uint32_t)H0;  // low bits of lo32: f uses the top bits
+    return true;
+}
+
+__device__ __forceinline__ bool key_equal(const uint8_t* __restrict__ keys, uint64_t t, uint32_t kb,
+                                          const Key& k) {
+    const Key o = load_key(keys, t, kb);
+    return o.x0 == k.x0 && o.x1 == k.x1;
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_gpu(uint32_t* p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide barrier for a co-resident (cooperatively launched) grid.  The wait is bounded:
+// after timeout_ns the block latches kErrTimeout and returns false, and so does every block
+// that finds the flag set, so the kernel can leave cleanly instead of hanging.
+__device__ __forceinline__ bool grid_barrier(uint32_t* ctrl, uint32_t nblocks, uint64_t timeout_ns) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const uint32_t g = ld_acquire_gpu(ctrl + kCtrlBarGen);
+        __threadfence();
+        const uint32_t prev = atomicAdd(ctrl + kCtrlBarCount, 1u);
+        if (prev == nblocks - 1) {
+            atomicExch(ctrl + kCtrlBarCount, 0u);
+            __threadfence();
+            st_release_gpu(ctrl + kCtrlBarGen, g + 1u);
+        } else {
+            const uint64_t t0 = globaltimer_ns();
+            while (ld_acquire_gpu(ctrl + kCtrlBarGen) == g) {
+                if (globaltimer_ns() - t0 > timeout_ns) {
+                    atomicOr(ctrl + kCtrlErr, kErrTimeout);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        if (ld_acquire_gpu(ctrl + kCtrlErr) & kErrTimeout) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__device__ __forceinline__ uint32_t warp_min_u32(uint32_t v, uint32_t mask) {
+    return __reduce_min_sync(mask, v);
+}
+
+}  // namespace sfk

@@ -1,0 +1,39 @@
+// sf_query.cu -- batched point queries on an exported Slim-subsketch (sm_103a).
+//
+// Query (Sec. 3.1, unchanged through SF_F, Sec. 3.5): the estimate of item e is the smallest
+// of its d Slim counters, min_i A_i[h_i(e)]; the Fat is never read.  The paper's GPU version
+// (Sec. 4.2) keeps all d arrays resident on the device and answers a batch per launch.
+#include "sf_internal.h"
+
+namespace sfk {
+
+namespace {
+
+__global__ void __launch_bounds__(kQueryBlock) query_kernel(const QueryArgs q) {
+    const SketchDesc& s = q.s;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < q.n; t += stride) {
+        const Key k = load_key(q.keys, t, s.key_bytes);
+        uint32_t h[kMaxD], f[kMaxD], probe;
+        uint32_t m = 0xFFFFFFFFu;
+        if (key_indices(s, k, h, f, &probe)) {
+#pragma unroll
+            for (int i = 0; i < kMaxD; ++i)
+                if (i < (int)s.d) m = min(m, __ldg(s.A + (uint64_t)i * s.w + h[i]));
+        }
+        q.out[t] = m;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_query(const QueryArgs& a, int num_sms, cudaStream_t st) {
+    if (a.n == 0) return cudaSuccess;
+    const uint64_t want = (a.n + kQueryBlock - 1) / kQueryBlock;
+    const uint64_t cap = (uint64_t)num_sms * 8;
+    const unsigned grid = (unsigned)(want < cap ? want : cap);
+    query_kernel<<<grid, kQueryBlock, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace sfk

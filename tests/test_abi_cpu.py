@@ -1,0 +1,80 @@
+"""The C-ABI library builds here, loads without a GPU and exports every function that
+include/*.h declares (no compute calls: there is no GPU on this side)."""
+import ctypes
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w \t\*]*?\b(sfc?_\w+)\s*\(", text, flags=re.M):
+            line = text[m.start():text.find("\n", m.start())]
+            if line.lstrip().startswith(("typedef", "#")):
+                continue
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_1701_04148_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for must in ("sf_create", "sf_insert_batch", "sf_delete_batch", "sf_export_slim", "sf_query_batch",
+                 "sf_required_bytes", "sf_sync", "sf_destroy", "sf_update_batch"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    L = ctypes.CDLL(lib_path)
+    missing = [n for n in sorted(_declared_functions()) if not hasattr(L, n)]
+    assert not missing, f"declared in include/*.h but not exported: {missing}"
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True, text=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if ln.strip()}
+    assert _declared_functions() <= exported
+
+
+def test_binding_covers_the_header(lib_path):
+    import paper_1701_04148_gb300 as sf
+    assert _declared_functions() <= set(sf.exported_symbols())
+
+
+def test_argument_checks_need_no_gpu(lib_path):
+    import paper_1701_04148_gb300 as sf
+    L = sf.load(lib_path)
+    assert L.sf_status_str(sf.SF_ERR_UNDERFLOW).decode().startswith("delete")
+    bad = sf.make_params(0, 16, 16, 4, 1, 64)           # d = 0
+    fb = ctypes.c_uint64()
+    assert L.sf_required_bytes(ctypes.byref(bad), ctypes.byref(fb), None, None) == sf.SF_ERR_INVALID
+    good = sf.make_params(4, 1 << 18, 16, 13, 2, 65536)
+    fb, sb, xb = sf.required_bytes(good)
+    assert fb == 4 * (1 << 18) * 16 * 4 and sb == 4 * (1 << 18) * 4
+    assert xb >= 256 + 2 * 65536 * 16
+    h = ctypes.c_void_p()
+    assert L.sf_create(ctypes.byref(good), None, None, None, None, ctypes.byref(h)) == sf.SF_ERR_INVALID
+    assert L.sf_insert_batch(None, None, 5) == sf.SF_ERR_INVALID
+    assert L.sf_sync(None) == sf.SF_ERR_INVALID
+    v = sf.SlimView(0, sf.SlimHeader(0, 1, 4, 16, 4, 1, 0), 0, 0)
+    assert L.sf_query_batch(ctypes.byref(v), None, 0, None, None) == sf.SF_ERR_VERSION
+
+
+def test_oracle_and_cuda_sources_share_nothing():
+    """The oracle (test infrastructure) and the CUDA library include and import nothing of each other."""
+    osrc = open(os.path.join(ROOT, "oracle", "sf_oracle.c")).read() + open(os.path.join(ROOT, "oracle", "__init__.py")).read()
+    assert "paper_1701_04148_gb300" not in osrc and "csrc" not in osrc
+    for p in glob.glob(os.path.join(ROOT, "paper_1701_04148_gb300", "**", "*.*"), recursive=True):
+        if p.endswith((".cu", ".cuh", ".h", ".py")):
+            txt = open(p).read()
+            assert "import oracle" not in txt and "from oracle" not in txt and "sf_oracle" not in txt, p

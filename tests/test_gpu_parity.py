@@ -1,0 +1,198 @@
+"""GPU parity: every Fat counter, every Slim counter and every query answer of the CUDA path,
+bit-exact against the CPU oracle on the same seeded inputs (integer work: no tolerance)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _np_u32(t):
+    return t.detach().cpu().numpy().view(np.uint32)
+
+
+def _run_both(sf, d, w, z, kb, seed, S, calls):
+    """calls: list of (keys uint8 (n,kb) cpu tensor, ops int8 cpu tensor or None=insert or 'del')."""
+    import torch
+    g = sf.Sketch(d, w, z, kb, seed, S)
+    o = oracle.Sketch(d, w, z, kb, seed)
+    for keys, ops in calls:
+        kd = keys.cuda()
+        if isinstance(ops, str) and ops == "del":
+            g.delete(kd)
+            o.update(keys.numpy(), -np.ones(len(keys), np.int8), S=S)
+        elif ops is None:
+            g.insert(kd)
+            o.update(keys.numpy(), np.ones(len(keys), np.int8), S=S)
+        else:
+            g.update(kd, ops.cuda())
+            o.update(keys.numpy(), ops.numpy(), S=S)
+    g.sync()
+    return g, o
+
+
+def _assert_same(g, o):
+    A = _np_u32(g.slim_view())
+    B = _np_u32(g.fat_view())
+    assert np.array_equal(B, o.B), f"Fat differs at {np.argwhere(B != o.B)[:5].tolist()}"
+    assert np.array_equal(A, o.A), f"Slim differs at {np.argwhere(A != o.A)[:5].tolist()}"
+
+
+def _queries_match(sf, g, o, qkeys):
+    slim, hdr = g.export_slim()
+    got = _np_u32(sf.query(slim, hdr, qkeys.cuda()))
+    want = o.query(qkeys.numpy())
+    assert np.array_equal(got, want)
+
+
+def test_worked_example_sec32_on_gpu(sf):
+    import torch
+    gold = json.load(open(os.path.join(GOLD, "worked_example_fig3.json")))
+    for S in (1, 2):
+        for fchoice in gold["fat_slot_choices"]:
+            table = np.zeros((2, 2, 2), np.uint32)
+            for k, name in enumerate(("e1", "e2")):
+                table[k, :, 0] = gold["keys"][name]["h"]
+                table[k, :, 1] = fchoice[k]
+            g = sf.Sketch(2, 2, 2, 4, 0, S, explicit_index=True)
+            g.set_index_table(torch.from_numpy(table.view(np.int32)))
+            ids = torch.tensor([0, 1], dtype=torch.int32, device="cuda")
+            g.insert(ids)
+            g.sync()
+            after_ins = _np_u32(g.slim_view()).tolist()
+            g.delete(ids[:1].clone())
+            g.sync()
+            after_del = _np_u32(g.slim_view()).tolist()
+            slim, hdr = g.export_slim()
+            q = _np_u32(sf.query(slim, hdr, ids, index_table=g._index_table)).tolist()
+            if S == 1:
+                assert after_ins == gold["after_inserts_printed_by_paper"]["A"]
+            assert after_del == gold["after_delete_e1_by_SF_F_rule"]["A"]
+            assert q == [gold["after_delete_e1_by_SF_F_rule"]["query"]["e1"],
+                         gold["after_delete_e1_by_SF_F_rule"]["query"]["e2"]]
+
+
+@pytest.mark.parametrize("S", [1, 2, 7, 64, 1000, 4096, 65536])
+def test_mixed_stream_u32(sf, S):
+    st, ids = wl.mixed_stream(20_000, 3_000, 1.1, 0.3, 4, seed=11 + S)
+    g, o = _run_both(sf, 4, 97, 16, 4, 5, S, [(st.keys, st.ops)])
+    _assert_same(g, o)
+    _queries_match(sf, g, o, ids)
+
+
+@pytest.mark.parametrize("kb", [1, 3, 8, 13, 16])
+def test_key_widths(sf, kb):
+    import torch
+    gen = torch.Generator().manual_seed(kb)
+    pool = torch.randint(0, 256, (500, kb), dtype=torch.uint8, generator=gen)
+    pool = torch.unique(pool, dim=0)
+    ranks = wl.sample_ranks(30_000, pool.shape[0], 1.2, gen)
+    keys = pool[ranks].contiguous()
+    ops = torch.where(torch.rand(30_000, generator=gen) < 0.15, -1, 1).to(torch.int8)
+    # make the stream strict-turnstile: a delete only if that key has a live insert
+    live = {}
+    ok = []
+    for t in range(len(keys)):
+        kk = bytes(keys[t].tolist())
+        if ops[t] < 0 and live.get(kk, 0) == 0:
+            ops[t] = 1
+        live[kk] = live.get(kk, 0) + int(ops[t])
+    for S in (1, 333, 8192):
+        g, o = _run_both(sf, 3, 50, 8, kb, 77, S, [(keys, ops)])
+        _assert_same(g, o)
+        _queries_match(sf, g, o, pool)
+
+
+@pytest.mark.parametrize("d,w,z", [(1, 1, 1), (2, 5, 3), (5, 300, 7), (8, 4096, 16), (4, 1 << 12, 64)])
+def test_shapes(sf, d, w, z):
+    st, ids = wl.mixed_stream(12_345, 2_000, 0.9, 0.25, 4, seed=d * 100 + z)
+    for S in (1, 3, 4096):
+        g, o = _run_both(sf, d, w, z, 4, 3, S, [(st.keys, st.ops)])
+        _assert_same(g, o)
+        _queries_match(sf, g, o, ids)
+
+
+def test_insert_then_delete_calls_restart_chunks(sf):
+    ins, dels, flows = wl.flows_with_deletes(200_000, 20_000, 1.0, 0.1, seed=3)
+    for S in (65536, 50_000):
+        g, o = _run_both(sf, 4, 1 << 12, 16, 13, 2, S, [(ins[:123_457], None), (ins[123_457:], None), (dels, "del")])
+        _assert_same(g, o)
+        _queries_match(sf, g, o, flows)
+
+
+def test_empty_and_tiny_batches(sf):
+    import torch
+    g = sf.Sketch(4, 64, 16, 4, 1, 64)
+    g.insert(torch.empty(0, dtype=torch.int32, device="cuda"))
+    g.sync()
+    assert int(g.slim.abs().sum()) == 0 and int(g.fat.abs().sum()) == 0
+    o = oracle.Sketch(4, 64, 16, 4, 1)
+    k = torch.tensor([5], dtype=torch.int32)
+    g.insert(k.cuda())
+    g.sync()
+    o.update(k.numpy().view(np.uint8).reshape(-1, 4), np.ones(1, np.int8), S=64)
+    _assert_same(g, o)
+    slim, hdr = g.export_slim()
+    assert sf.query(slim, hdr, torch.empty(0, dtype=torch.int32, device="cuda")).numel() == 0
+
+
+def test_theorem_error_free_fat_on_gpu(sf):
+    """Sec. 3.5 Theorem 1 through the GPU path (explicit indices, insertions only)."""
+    import torch
+    rng = np.random.default_rng(17)
+    n_keys, d, w, z = 200, 3, 32, 16
+    table = np.zeros((n_keys, d, 2), np.uint32)
+    for i in range(d):
+        used = np.zeros(w, np.int64)
+        for k in range(n_keys):
+            j = int(rng.integers(w))
+            while used[j] >= z:
+                j = int(rng.integers(w))
+            table[k, i] = (j, used[j])
+            used[j] += 1
+    ids = ((rng.zipf(1.2, 50_000) - 1) % n_keys).astype(np.uint32)
+    freq = np.bincount(ids, minlength=n_keys)
+    want = np.zeros((d, w), np.int64)
+    for k in range(n_keys):
+        for i in range(d):
+            want[i, table[k, i, 0]] = max(want[i, table[k, i, 0]], freq[k])
+    for S in (1, 5, 4096):
+        g = sf.Sketch(d, w, z, 4, 0, S, explicit_index=True)
+        g.set_index_table(torch.from_numpy(table.view(np.int32)))
+        g.insert(torch.from_numpy(ids.view(np.int32)).cuda())
+        g.sync()
+        assert np.array_equal(_np_u32(g.slim_view()).astype(np.int64), want)
+
+
+def test_underflow_is_reported(sf):
+    import torch
+    for S in (1, 16):
+        g = sf.Sketch(2, 16, 4, 4, 9, S)
+        g.delete(torch.tensor([42], dtype=torch.int32, device="cuda"))
+        assert g.sync_status() == sf.SF_ERR_UNDERFLOW
+        assert g.sync_status() == sf.SF_OK  # cleared after being reported
+
+
+def test_bad_key_id_in_explicit_mode_is_reported(sf):
+    import torch
+    for S in (1, 8):
+        g = sf.Sketch(2, 4, 4, 4, 0, S, explicit_index=True)
+        g.set_index_table(torch.zeros((3, 2, 2), dtype=torch.int32))
+        g.insert(torch.tensor([0, 7], dtype=torch.int32, device="cuda"))
+        assert g.sync_status() == sf.SF_ERR_INVALID
+
+
+def test_flows_zipf_sweep_mid_size(sf):
+    """Shape of the 5-tuple workload (13-byte keys, Zipf sweep, inserts then 10 % deletes,
+    chunk 65,536) at 1/64 of its stream length and Slim width."""
+    for s in wl.ZIPF_SWEEP:
+        ins, dels, flows = wl.flows_with_deletes(500_000, 16_384, s, 0.1, seed=int(s * 10) + 1)
+        g, o = _run_both(sf, 4, 1 << 12, 16, 13, 2, 65536, [(ins, None), (dels, "del")])
+        _assert_same(g, o)
+        _queries_match(sf, g, o, flows)
