@@ -1,0 +1,412 @@
+#!/usr/bin/env python3
+"""Benchmark of the SF-sketch hot path on GB300: one JSON line on rank 0.
+
+Workload (one step = one pass of the whole path over one batch of synthetic input): for each
+Zipf exponent s in {0, 0.5, 1, 1.5, 2, 3}, a fresh sketch (d=4, w=2^18, z=16, 13-byte 5-tuple
+keys, chunk 65,536) takes 32,000,000 inserts drawn Zipf(s) over 1,000,000 distinct flows, then
+deletes of a random 10 % of the inserted occurrences; its Slim-subsketch is exported and all
+1,000,000 flows are queried.  value = (inserts + deletes + queries) of all ranks / step time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (plain sequential C, one core) on a bounded sample of the
+same workload.  Under torchrun (N > 1) every rank runs an independent replica (its own seeds);
+only timing is reduced across ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "M inserts/s + M queries/s, bit-exact; batched vs plain speedup; p99 query ms"
+SWEEP = (0.0, 0.5, 1.0, 1.5, 2.0, 3.0)
+D, W, Z, KB, S = 4, 1 << 18, 16, 13, 65536
+N_INS, N_FLOWS, DEL_FRAC = 32_000_000, 1_000_000, 0.10
+SEED0 = 2
+L2_OPS_PER_UPDATE = 4 * D   # d Fat RMW + d Fat reads + d Slim reads + d Slim RMW (Sec. 3.4/3.5 rules)
+L2_OPS_PER_QUERY = D        # d Slim gathers (Sec. 3.1 query)
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def seed_for(rank, idx):
+    return SEED0 + 1000 * rank + idx
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active," \
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown," \
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, gpu_index: int):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="sf_clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu_index)], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_index_for(local_rank: int) -> int:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if local_rank < len(ids) and ids[local_rank].isdigit():
+            return int(ids[local_rank])
+    return local_rank
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def traffic_record():
+    """DRAM bytes per update of the chunk kernel from the committed ncu summary, if the kernel
+    source has not changed since the counters were taken."""
+    p = os.path.join(ROOT, "profiles", "chunk_update_kernel_traffic.json")
+    if not os.path.exists(p):
+        return None
+    rec = json.load(open(p))
+    src = os.path.join(ROOT, "paper_1701_04148_gb300", "csrc", "sf_update.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    return rec if rec.get("kernel_source_sha256") == sha else None
+
+
+# ------------------------------------------------------------------------------------------
+# reference arm: the CPU oracle on a bounded sample of the same workload
+# ------------------------------------------------------------------------------------------
+
+def oracle_sample_inputs(n_ins: int, n_flows_q: int, rank: int):
+    import workloads as wl
+    out = []
+    for idx, s in enumerate(SWEEP):
+        ins, dels, flows = wl.flows_with_deletes(n_ins, N_FLOWS, s, DEL_FRAC, seed=seed_for(rank, idx), device="cpu")
+        out.append((ins.numpy(), dels.numpy(), flows[:n_flows_q].numpy()))
+    return out
+
+
+def oracle_step(samples):
+    import numpy as np
+    import oracle
+    n = 0
+    answers = []
+    for ins, dels, flows in samples:
+        o = oracle.Sketch(D, W, Z, KB, SEED0)
+        o.update(ins, np.ones(len(ins), np.int8), S=S)
+        o.update(dels, -np.ones(len(dels), np.int8), S=S)
+        answers.append(o.query(flows))
+        n += len(ins) + len(dels) + len(flows)
+    return n, answers
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    n_ins = args.ref_inserts
+    samples = oracle_sample_inputs(n_ins, args.ref_queries, rank)
+    for _ in range(args.warmup):
+        oracle_step(samples)
+    t0 = time.perf_counter()
+    n = 0
+    for _ in range(args.steps):
+        k, _ = oracle_step(samples)
+        n += k
+    dt = time.perf_counter() - t0
+    value = n / dt / 1e6
+    sample = (f"per step, for each s in {list(SWEEP)}: the first {n_ins} of the 32,000,000 inserts, "
+              f"10% of them deleted, {args.ref_queries} flows queried (same recipe and seeds)")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "M ops/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "flows-zipf-sweep-with-deletes (sampled)", "d": D, "w": W, "z": Z,
+                       "key_bytes": KB, "chunk": S},
+            "cpu_baseline": {"value": round(value, 4), "unit": "M ops/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 4), "unit": "M ops/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--ref-inserts", type=int, default=400_000)
+    ap.add_argument("--ref-queries", type=int, default=20_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world, rank, local = dist_env()
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    if args.impl == "reference":
+        rc = run_reference(args, world, rank)
+        if dist is not None:
+            dist.destroy_process_group()
+        return rc
+
+    import numpy as np
+    import paper_1701_04148_gb300 as sf
+    import workloads as wl
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the SF-sketch library has no CPU path)")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    L = sf.load()
+    stream = torch.cuda.current_stream(dev)
+
+    # ---- inputs, resident in HBM ----------------------------------------------------------
+    inputs = []
+    for idx, s in enumerate(SWEEP):
+        ins, dels, flows = wl.flows_with_deletes(N_INS, N_FLOWS, s, DEL_FRAC, seed=seed_for(rank, idx), device=dev)
+        inputs.append((ins, dels, flows))
+    torch.cuda.synchronize()
+    sketches = [sf.Sketch(D, W, Z, KB, SEED0, S, stream=stream) for _ in SWEEP]
+    slims = [torch.empty(D * W, dtype=torch.int32, device=dev) for _ in SWEEP]
+    answers = [torch.empty(N_FLOWS, dtype=torch.int32, device=dev) for _ in SWEEP]
+    n_del = inputs[0][1].shape[0]
+    ops_per_step = len(SWEEP) * (N_INS + n_del + N_FLOWS)
+    launches_per_step = len(SWEEP) * 3  # insert + delete chunk-kernel launches, one query launch
+
+    def step(evs=None, host=None):
+        for idx in range(len(SWEEP)):
+            if host is not None:
+                ins_h, dels_h, flows_h, _ = host[idx]
+                ins_d, dels_d, flows_d = inputs[idx]
+                ins_d.copy_(ins_h, non_blocking=True)
+                dels_d.copy_(dels_h, non_blocking=True)
+                flows_d.copy_(flows_h, non_blocking=True)
+            ins, dels, flows = inputs[idx]
+            sk = sketches[idx]
+            sk.reset()
+            if evs is not None:
+                evs[idx][0].record(stream)
+            sk.insert(ins)
+            if evs is not None:
+                evs[idx][1].record(stream)
+            sk.delete(dels)
+            if evs is not None:
+                evs[idx][2].record(stream)
+            slim, hdr = sk.export_slim(slims[idx])
+            sf.query(slim, hdr, flows, out=answers[idx], stream=stream)
+            if evs is not None:
+                evs[idx][3].record(stream)
+            if host is not None:
+                host[idx][3].copy_(answers[idx], non_blocking=True)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    for sk in sketches:
+        sk.sync()
+
+    # ---- timed region (device-resident inputs) --------------------------------------------
+    evs_all = [[[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in SWEEP] for _ in range(args.steps)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(gpu_index_for(local))
+    clocks.start()
+    time.sleep(0.3)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for k in range(args.steps):
+        step(evs_all[k])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    for sk in sketches:
+        sk.sync()
+    t_ins = sum(evs_all[k][i][0].elapsed_time(evs_all[k][i][1]) for k in range(args.steps) for i in range(len(SWEEP)))
+    t_del = sum(evs_all[k][i][1].elapsed_time(evs_all[k][i][2]) for k in range(args.steps) for i in range(len(SWEEP)))
+    t_qry = sum(evs_all[k][i][2].elapsed_time(evs_all[k][i][3]) for k in range(args.steps) for i in range(len(SWEEP)))
+    ms_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = world * ops_per_step / (ms_max / 1e3) / 1e6
+
+    # ---- roofline denominator measured in this run: random 32-bit L2 loads on 64 MiB ------
+    buf = torch.zeros(1 << 24, dtype=torch.int32, device=dev)
+    h_st = int(stream.cuda_stream)
+    L.sf_bench_random_access(buf.data_ptr(), buf.numel(), 1 << 28, 2, 0, h_st)
+    best = 0.0
+    for _ in range(3):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        L.sf_bench_random_access(buf.data_ptr(), buf.numel(), 1 << 28, 2, 0, h_st)
+        b.record(stream)
+        torch.cuda.synchronize()
+        best = max(best, (1 << 28) / a.elapsed_time(b) / 1e6)  # G ops/s
+    del buf
+    upd_timed = args.steps * len(SWEEP) * (N_INS + n_del)
+    chunk_ms = t_ins + t_del
+    launches_chunk = args.steps * len(SWEEP) * 2
+    achieved = upd_timed * L2_OPS_PER_UPDATE / (chunk_ms / 1e3) / 1e9
+    tr = traffic_record()
+    traffic = None
+    if tr is not None:
+        traffic = round(tr["dram_bytes_per_update"] * upd_timed / launches_chunk)
+    roofline = {"bound": "l2", "kernel": "chunk_update_kernel", "achieved": round(achieved, 2), "peak": round(best, 2),
+                "unit": "G random L2 ops/s", "frac": round(achieved / best, 4), "traffic": traffic,
+                "peak_source": "measured in this run: random 32-bit ld.global.cg on a 64 MiB L2-resident buffer",
+                "ops_per_update": L2_OPS_PER_UPDATE,
+                "avg_launch_ms": round(chunk_ms / launches_chunk, 4)}
+    peaks, psrc = measured_peaks()
+    hbm_bytes = upd_timed * (KB + L2_OPS_PER_UPDATE * 4)
+    roofline_hbm = {"bound": "hbm", "achieved": round(hbm_bytes / (chunk_ms / 1e3) / 1e9, 1),
+                    "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                    "frac": round(hbm_bytes / (chunk_ms / 1e3) / 1e9 / peaks.get("hbm_gbs", 1.0), 4),
+                    "note": f"algorithmic bytes = key + 4 B per counter touched; peak {psrc}"}
+
+    # ---- e2e: host pinned inputs, H2D + path + D2H of the answers inside the timed region ---
+    e2e = None
+    if not args.no_e2e:
+        host = []
+        for ins, dels, flows in inputs:
+            host.append((ins.cpu().pin_memory(), dels.cpu().pin_memory(), flows.cpu().pin_memory(),
+                         torch.empty(N_FLOWS, dtype=torch.int32).pin_memory()))
+        h2d = sum(h[0].numel() + h[1].numel() + h[2].numel() for h in host)
+        d2h = sum(h[3].numel() * 4 for h in host)
+        step(host=host)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            step(host=host)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ems = a.elapsed_time(b) / args.steps
+        if dist is not None:
+            t = torch.tensor([ems], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": round(world * ops_per_step / (ems / 1e3) / 1e6, 2), "unit": "M ops/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ems, 3)}
+        for sk in sketches:
+            sk.sync()
+
+    # ---- CPU baseline (the oracle) and a bit-exact check on the same bounded sample -------
+    cpu = None
+    exact = None
+    if rank == 0 and not args.no_cpu_baseline:
+        samples = []
+        n_i = args.ref_inserts
+        g_cpu = torch.Generator().manual_seed(SEED0)
+        for idx in range(len(SWEEP)):
+            ins, dels, flows = inputs[idx]
+            head = ins[:n_i].cpu()
+            victims = torch.randperm(n_i, generator=g_cpu)[: int(n_i * DEL_FRAC)]
+            samples.append((head.numpy(), head[victims].contiguous().numpy(), flows[: args.ref_queries].cpu().numpy()))
+        t0 = time.perf_counter()
+        n_ops, want = oracle_step(samples)
+        dt = time.perf_counter() - t0
+        cpu = {"value": round(n_ops / dt / 1e6, 4), "unit": "M ops/s", "cores": 1, "kind": "oracle",
+               "sample": f"for each s: first {args.ref_inserts} inserts, {int(args.ref_inserts * DEL_FRAC)} deletes, "
+                         f"{args.ref_queries} queries of this run's inputs ({n_ops} ops, {dt:.1f} s)"}
+        exact = True
+        for idx, (ins_np, dels_np, fl_np) in enumerate(samples):
+            g = sf.Sketch(D, W, Z, KB, SEED0, S, stream=stream)
+            g.insert(torch.from_numpy(ins_np).to(dev))
+            g.delete(torch.from_numpy(dels_np).to(dev))
+            slim, hdr = g.export_slim()
+            got = sf.query(slim, hdr, torch.from_numpy(fl_np).to(dev), stream=stream)
+            g.sync()
+            exact &= bool(np.array_equal(got.cpu().numpy().view(np.uint32), want[idx]))
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": "M ops/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_max, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "flows-zipf-sweep-with-deletes", "d": D, "w": W, "z": Z, "key_bytes": KB,
+                       "chunk": S, "inserts_per_s": N_INS, "deletes_per_s": n_del, "flows": N_FLOWS,
+                       "zipf_s": list(SWEEP), "l2": "inputs larger than L2 (2.7 GB of keys per step)",
+                       "parallelism": f"replicas x{world}"},
+            "breakdown": {"insert_mops": round(args.steps * len(SWEEP) * N_INS / t_ins / 1e3, 1),
+                          "delete_mops": round(args.steps * len(SWEEP) * n_del / t_del / 1e3, 1),
+                          "export_query_mops": round(args.steps * len(SWEEP) * N_FLOWS / t_qry / 1e3, 1)},
+            "roofline": roofline, "roofline_hbm": roofline_hbm,
+            "cpu_baseline": cpu, "bit_exact_sample": exact, "e2e": e2e,
+            "gpu_launches": args.steps * launches_per_step, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

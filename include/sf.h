@@ -24,7 +24,7 @@
  *
  * Hashing (the paper asks only for independent uniform h_i, f_i): row seeds are the first d
  * outputs of SplitMix64 from params.seed; H_i = mix64(x0 ^ s_i) for keys of at most 8 bytes,
- * mix64(mix64(x0 ^ s_i) ^ x1) for longer keys (x0, x1 = key bytes 0..7 and 8..15 read
+ * mix64(mix64(x0 ^ s_i) ^ x1) for longer keys (x0, x1 = key bytes 0..7 and 8..14 read
  * little-endian, zero-padded); h_i = (hi32(H_i) * w) >> 32, f_i = (lo32(H_i) * z) >> 32.
  *
  * Memory ownership.  The caller allocates every device buffer (Fat, Slim, scratch, keys,
@@ -59,7 +59,8 @@ typedef int32_t sf_status;
 
 #define SF_MAX_D 8
 #define SF_MAX_Z 64
-#define SF_MAX_KEY_BYTES 16
+#define SF_MAX_KEY_BYTES 15
+#define SF_MAX_CHUNK (1u << 22)
 
 #define SF_SLIM_MAGIC   0x4D494C53u  /* "SLIM" */
 #define SF_SLIM_VERSION 1u
@@ -75,7 +76,7 @@ typedef struct sf_params {
     uint32_t z;          /* Fat counters per bucket, 1..SF_MAX_Z                (Table 1: z) */
     uint32_t key_bytes;  /* packed key width, 1..SF_MAX_KEY_BYTES (4 in explicit mode)       */
     uint64_t seed;       /* hash seed                                                        */
-    uint32_t chunk;      /* S >= 1 updates per chunk (semantic: see above)                   */
+    uint32_t chunk;      /* S updates per chunk, 1..SF_MAX_CHUNK (semantic: see above)       */
     uint32_t flags;      /* SF_FLAG_*                                                        */
 } sf_params;
 

@@ -1,0 +1,46 @@
+/*
+ * sf_bench.h -- measurement kernels of the GB300 SF-sketch library.
+ *
+ * The paper has no counterpart: these calls measure the roofline denominators the update and
+ * query kernels are judged against (random 32-bit atomics and loads on an L2- or HBM-resident
+ * buffer, and the cost of one grid-wide barrier of the persistent update kernel).  They touch
+ * only the caller's buffer and never a sketch.
+ */
+#ifndef SF_BENCH_H_
+#define SF_BENCH_H_
+
+#include <stdint.h>
+
+#include "sf.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SF_BENCH_RED_ADD   0u  /* atomicAdd, result unused (reduction)   */
+#define SF_BENCH_ATOM_ADD  1u  /* atomicAdd, result used                 */
+#define SF_BENCH_LOAD_CG   2u  /* 32-bit load bypassing L1               */
+#define SF_BENCH_RED_MAX   3u  /* atomicMax, result unused               */
+#define SF_BENCH_CAS       4u  /* atomicCAS, result used                 */
+
+/*
+ * Issues total_ops random 32-bit operations of `kind` on buf_dev[0 .. n_words) (device,
+ * n_words a power of two, caller-owned, contents overwritten) on cuda_stream.  Addresses come
+ * from a 64-bit LCG per thread (uniform over the buffer).  grid_blocks = 0 picks 8 blocks of
+ * 256 threads per SM.  The caller times the call with CUDA events.
+ */
+sf_status sf_bench_random_access(uint32_t *buf_dev, uint64_t n_words, uint64_t total_ops, uint32_t kind,
+                                 uint32_t grid_blocks, void *cuda_stream);
+
+/*
+ * Runs n_barriers grid-wide barriers of the persistent update kernel's kind (cooperative
+ * launch, same grid shape), with no other work.  scratch_dev: >= 256 device bytes, zeroed by
+ * the call.  Returns SF_ERR_TIMEOUT if a wait gave up (after synchronising the stream).
+ */
+sf_status sf_bench_grid_barrier(void *scratch_dev, uint32_t n_barriers, void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SF_BENCH_H_ */

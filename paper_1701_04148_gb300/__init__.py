@@ -77,6 +77,9 @@ _SIGS = {
     "sf_query_batch": (ctypes.c_int32, [ctypes.POINTER(SlimView), ctypes.c_void_p, ctypes.c_uint64,
                                         ctypes.c_void_p, ctypes.c_void_p]),
     "sf_sync": (ctypes.c_int32, [ctypes.c_void_p]),
+    "sf_bench_random_access": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
+                                                ctypes.c_uint32, ctypes.c_void_p]),
+    "sf_bench_grid_barrier": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]),
 }
 
 
@@ -170,6 +173,17 @@ class Sketch:
                               self.scratch.data_ptr(), _stream_handle(self.stream), ctypes.byref(h)), "sf_create")
         self.handle = h
         self._index_table = None
+
+    def reset(self):
+        """Initialisation again (Sec. 3.1: all counters zero) on the same device buffers."""
+        self.close()
+        h = ctypes.c_void_p()
+        check(load().sf_create(ctypes.byref(self.params), self.fat.data_ptr(), self.slim.data_ptr(),
+                               self.scratch.data_ptr(), _stream_handle(self.stream), ctypes.byref(h)), "sf_create")
+        self.handle = h
+        if self._index_table is not None:
+            check(load().sf_set_index_table(self.handle, self._index_table.data_ptr(), self._index_table.shape[0]),
+                  "sf_set_index_table")
 
     # shapes of the caller-visible views
     @property

@@ -28,6 +28,8 @@ struct sf_sketch {
     uint32_t cap;
     const uint32_t* idx_table;
     uint32_t n_ids;
+    uint64_t bar_epoch;     // grid barriers passed on this scratch buffer (monotonic counter)
+    uint32_t claims_cap;    // per-block claim list length of the chunk kernel
 };
 
 namespace {
@@ -47,7 +49,7 @@ bool params_ok(const sf_params* p) {
     if (p->w < 1 || p->w > 0x7FFFFFFFu) return false;
     if (p->z < 1 || p->z > SF_MAX_Z) return false;
     if (p->key_bytes < 1 || p->key_bytes > SF_MAX_KEY_BYTES) return false;
-    if (p->chunk < 1 || p->chunk > (1u << 30)) return false;
+    if (p->chunk < 1 || p->chunk > SF_MAX_CHUNK) return false;
     if ((p->flags & ~SF_FLAG_EXPLICIT_INDEX) != 0) return false;
     if ((p->flags & SF_FLAG_EXPLICIT_INDEX) && p->key_bytes != 4) return false;
     if ((uint64_t)p->d * p->w * p->z > (1ull << 40)) return false;
@@ -101,8 +103,11 @@ sf_status run_update(sf_sketch* s, const void* keys, const int8_t* ops, int op_c
         a.cap_mask = s->cap - 1u;
         a.dict = s->dict;
         a.ctrl = s->ctrl;
+        a.bar_base = s->bar_epoch;
+        a.claims_cap = s->claims_cap;
         a.timeout_ns = sfk::kBarrierTimeoutNs;
         e = sfk::launch_chunk_update(a, s->chunk_grid, s->stream);
+        if (e == cudaSuccess) s->bar_epoch += 2ull * ((n + s->p.chunk - 1) / s->p.chunk);
     }
     if (cur != s->device) cudaSetDevice(cur);
     return e == cudaSuccess ? SF_OK : SF_ERR_CUDA;
@@ -164,12 +169,14 @@ sf_status sf_create(const sf_params* p, void* fat_dev, void* slim_dev, void* scr
         delete s;
         return SF_ERR_CUDA;
     }
-    const int bps = sfk::chunk_update_blocks_per_sm();
+    const int bps = sfk::chunk_update_blocks_per_sm(p->d);
     if (bps <= 0) {
         delete s;
         return SF_ERR_CUDA;
     }
     s->chunk_grid = s->num_sms * (bps < 2 ? bps : 2);
+    s->claims_cap = sfk::chunk_claims_cap(p->chunk, s->chunk_grid);
+    s->bar_epoch = 0;
     uint64_t fb, sb, xb;
     sf_required_bytes(p, &fb, &sb, &xb);
     if (cudaMemsetAsync(fat_dev, 0, fb, s->stream) != cudaSuccess ||
@@ -271,6 +278,7 @@ sf_status sf_sync(sf_sketch* s) {
         uint64_t xb = 0;
         sf_required_bytes(&s->p, nullptr, nullptr, &xb);
         cudaMemsetAsync(s->scratch, 0, xb, s->stream);
+        s->bar_epoch = 0;
     } else {
         cudaMemsetAsync(s->ctrl + sfk::kCtrlErr, 0, 4, s->stream);
     }

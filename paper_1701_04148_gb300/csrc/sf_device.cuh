@@ -21,16 +21,21 @@ constexpr uint32_t kErrTimeout = 2u;
 constexpr uint32_t kErrBadKey = 4u;
 constexpr uint32_t kErrDictFull = 8u;
 
-// Control block: the first 256 bytes of every scratch buffer.
-enum : uint32_t { kCtrlErr = 0, kCtrlBarCount = 1, kCtrlBarGen = 2, kCtrlWords = 64 };
+// Control block: the first 256 bytes of every scratch buffer.  Word 0 latches error bits;
+// bytes 8..15 hold the 64-bit arrival counter of the grid barrier (monotonic across launches).
+enum : uint32_t { kCtrlErr = 0, kCtrlBarrier64 = 2, kCtrlWords = 64 };
 
-// Per-chunk key dictionary entry (16 bytes): the first update of the key in the chunk
-// (index + 1, 0 = empty), its inserts c_e, its deletes, and m_e = min_i A0_i[h_i(e)].
-struct DictEntry {
-    uint32_t owner;
+// Per-chunk key dictionary entry (32 bytes).  The key is claimed with one 128-bit CAS:
+// key_lo = bytes 0..7, key_hi = bytes 8..14 with bit 63 set (so an occupied entry is never 0).
+// The counters hold the key's inserts c_e and deletes in the chunk and m_e = min_i A0_i[h_i(e)].
+constexpr unsigned long long kKeyTag = 1ull << 63;
+struct alignas(32) DictEntry {
+    unsigned long long key_lo;
+    unsigned long long key_hi;
     uint32_t c_ins;
     uint32_t c_del;
     uint32_t m;
+    uint32_t pad;
 };
 
 struct SketchDesc {
@@ -82,18 +87,21 @@ __device__ __forceinline__ uint32_t reduce_lo(uint64_t H, uint32_t range) {
     return (uint32_t)(((H & 0xFFFFFFFFull) * (uint64_t)range) >> 32);
 }
 
-// Row indices of one key.  Returns false for a bad key id in explicit-index mode.
-// probe receives a well-mixed 32-bit value independent of the top bits used by h/f.
-__device__ __forceinline__ bool key_indices(const SketchDesc& s, const Key& k, uint32_t* h,
-                                            uint32_t* f, uint32_t* probe) {
+// Row indices of one key for D rows (D = 0: the runtime s.d rows, at most kMaxD).  Returns
+// false for a bad key id or table entry in explicit-index mode.  probe receives a well-mixed
+// 32-bit value for the dictionary; its low bits are independent of the top bits h/f use.
+template <int D>
+__device__ __forceinline__ bool key_indices(const SketchDesc& s, const Key& k, uint32_t* h, uint32_t* f,
+                                            uint32_t* probe) {
+    constexpr int N = D ? D : kMaxD;
     if (s.idx_table) {
         const uint64_t id = k.x0;
         if (id >= s.n_ids) return false;
         const uint32_t* row = s.idx_table + id * (uint64_t)s.d * 2;
         bool ok = true;
 #pragma unroll
-        for (int i = 0; i < kMaxD; ++i)
-            if (i < (int)s.d) {
+        for (int i = 0; i < N; ++i)
+            if (D || i < (int)s.d) {
                 h[i] = __ldg(row + 2 * i);
                 f[i] = __ldg(row + 2 * i + 1);
                 ok &= (h[i] < s.w) && (f[i] < s.z);  // a bad table entry must not index out of bounds
@@ -103,14 +111,14 @@ __device__ __forceinline__ bool key_indices(const SketchDesc& s, const Key& k, u
     }
     uint64_t H0 = 0;
 #pragma unroll
-    for (int i = 0; i < kMaxD; ++i)
-        if (i < (int)s.d) {
+    for (int i = 0; i < N; ++i)
+        if (D || i < (int)s.d) {
             const uint64_t H = row_hash(k, s.key_bytes, s.rs[i]);
             if (i == 0) H0 = H;
             h[i] = reduce_hi(H, s.w);
             f[i] = reduce_lo(H, s.z);
         }
-    *probe = (uint32_t)H0;  // low bits of lo32: f uses the top bits
+    *probe = (uint32_t)H0;
     return true;
 }
 
@@ -132,34 +140,52 @@ __device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t* p) {
     return v;
 }
 
-__device__ __forceinline__ void st_release_gpu(uint32_t* p, uint32_t v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ unsigned long long ld_acquire_gpu_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
 }
 
-// Grid-wide barrier for a co-resident (cooperatively launched) grid.  The wait is bounded:
-// after timeout_ns the block latches kErrTimeout and returns false, and so does every block
-// that finds the flag set, so the kernel can leave cleanly instead of hanging.
-__device__ __forceinline__ bool grid_barrier(uint32_t* ctrl, uint32_t nblocks, uint64_t timeout_ns) {
+__device__ __forceinline__ void red_release_gpu_add_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// 128-bit compare-and-swap in global memory (atom.cas.b128, sm_90 and later).
+__device__ __forceinline__ void cas128(unsigned long long* addr, unsigned long long cmp_lo,
+                                       unsigned long long cmp_hi, unsigned long long new_lo,
+                                       unsigned long long new_hi, unsigned long long& old_lo,
+                                       unsigned long long& old_hi) {
+    asm volatile(
+        "{\n\t.reg .b128 c, v, o;\n\t"
+        "mov.b128 c, {%2, %3};\n\t"
+        "mov.b128 v, {%4, %5};\n\t"
+        "atom.global.cas.b128 o, [%6], c, v;\n\t"
+        "mov.b128 {%0, %1}, o;\n\t}"
+        : "=l"(old_lo), "=l"(old_hi)
+        : "l"(cmp_lo), "l"(cmp_hi), "l"(new_lo), "l"(new_hi), "l"(addr)
+        : "memory");
+}
+
+// Grid-wide barrier for a co-resident (cooperatively launched) grid.  Every block adds 1 to a
+// monotonic 64-bit counter and waits until it reaches `target` = (barriers passed so far + 1) *
+// gridDim.x.  The wait is bounded: after timeout_ns the block latches kErrTimeout and returns
+// false, and so does every block that finds the flag set, so the kernel leaves instead of hanging.
+__device__ __forceinline__ bool grid_barrier(uint32_t* ctrl, unsigned long long target, uint64_t timeout_ns) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        const uint32_t g = ld_acquire_gpu(ctrl + kCtrlBarGen);
+        unsigned long long* cnt = reinterpret_cast<unsigned long long*>(ctrl + kCtrlBarrier64);
         __threadfence();
-        const uint32_t prev = atomicAdd(ctrl + kCtrlBarCount, 1u);
-        if (prev == nblocks - 1) {
-            atomicExch(ctrl + kCtrlBarCount, 0u);
-            __threadfence();
-            st_release_gpu(ctrl + kCtrlBarGen, g + 1u);
-        } else {
+        red_release_gpu_add_u64(cnt, 1ull);
+        if (ld_acquire_gpu_u64(cnt) < target) {
             const uint64_t t0 = globaltimer_ns();
-            while (ld_acquire_gpu(ctrl + kCtrlBarGen) == g) {
+            while (ld_acquire_gpu_u64(cnt) < target) {
                 if (globaltimer_ns() - t0 > timeout_ns) {
                     atomicOr(ctrl + kCtrlErr, kErrTimeout);
                     ok = 0;
                     break;
                 }
-                __nanosleep(32);
             }
         }
         __threadfence();

@@ -16,7 +16,7 @@ __global__ void __launch_bounds__(kQueryBlock) query_kernel(const QueryArgs q) {
         const Key k = load_key(q.keys, t, s.key_bytes);
         uint32_t h[kMaxD], f[kMaxD], probe;
         uint32_t m = 0xFFFFFFFFu;
-        if (key_indices(s, k, h, f, &probe)) {
+        if (key_indices<0>(s, k, h, f, &probe)) {
 #pragma unroll
             for (int i = 0; i < kMaxD; ++i)
                 if (i < (int)s.d) m = min(m, __ldg(s.A + (uint64_t)i * s.w + h[i]));

@@ -55,113 +55,274 @@ __device__ __forceinline__ uint32_t bucket_max_cg(const SketchDesc& s, uint32_t 
     return mx;
 }
 
-__global__ void __launch_bounds__(kChunkBlock) chunk_update_kernel(const ChunkArgs a) {
+// Per-warp load of up to 32 packed keys of a width other than 4 or 8 bytes: the warp reads the
+// 16-byte-aligned granules covering its keys with vector loads into shared memory (streaming,
+// evict-first: each key byte is read once), and reads a granule that straddles either end of the
+// caller's buffer byte by byte, so no byte outside [keys, keys + n*kb) is ever touched.
+__device__ __forceinline__ Key load_key_staged(const uint8_t* __restrict__ keys, uint64_t total_bytes,
+                                               uint64_t first, uint32_t nvalid, uint32_t kb, uint32_t lane,
+                                               uint4* stage) {
+    const uintptr_t kaddr = reinterpret_cast<uintptr_t>(keys);
+    const uint8_t* kal = reinterpret_cast<const uint8_t*>(kaddr & ~(uintptr_t)15);
+    const uint64_t lo = kaddr & 15u, hi = lo + total_bytes;  // valid bytes, relative to kal
+    const uint64_t b0 = lo + first * kb, b1 = b0 + (uint64_t)nvalid * kb;
+    const uint64_t g0 = b0 & ~15ull;
+    const uint32_t ngran = (uint32_t)((b1 - g0 + 15) >> 4);  // <= 31 for kb <= 15
+    if (lane < ngran) {
+        const uint64_t gb = g0 + 16ull * lane;
+        uint4 v;
+        if (gb >= lo && gb + 16 <= hi) {
+            v = __ldcs(reinterpret_cast<const uint4*>(kal + gb));
+        } else {
+            uint32_t w[4] = {0u, 0u, 0u, 0u};
+            for (uint32_t q = 0; q < 16; ++q)
+                if (gb + q >= lo && gb + q < hi) w[q >> 2] |= (uint32_t)__ldg(kal + gb + q) << (8 * (q & 3));
+            v = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        stage[lane] = v;
+    }
+    __syncwarp();
+    Key k{0ull, 0ull};
+    if (lane < nvalid) {
+        const uint8_t* sb = reinterpret_cast<const uint8_t*>(stage) + (b0 - g0) + (uint64_t)lane * kb;
+        const uint32_t n0 = kb < 8 ? kb : 8;
+        for (uint32_t b = 0; b < n0; ++b) k.x0 |= (uint64_t)sb[b] << (8 * b);
+        for (uint32_t b = 8; b < kb; ++b) k.x1 |= (uint64_t)sb[b] << (8 * (b - 8));
+    }
+    __syncwarp();
+    return k;
+}
+
+constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
+
+__device__ __forceinline__ void ld_entry(const DictEntry* ep, unsigned long long& k0, unsigned long long& k1,
+                                         unsigned long long& c01, unsigned long long& c23) {
+    asm volatile("ld.global.cg.v4.u64 {%0, %1, %2, %3}, [%4];"
+                 : "=l"(k0), "=l"(k1), "=l"(c01), "=l"(c23)
+                 : "l"(ep));
+}
+
+__device__ __forceinline__ void clear_entry(DictEntry* ep) {
+    asm volatile("st.global.cg.v4.u64 [%0], {%1, %1, %1, %1};" ::"l"(ep), "l"(0ull) : "memory");
+}
+
+// One lane's update of the current warp-iteration, loaded and hashed (independent of the
+// sketch state, so the next chunk's first iteration can be prepared before the barrier).
+template <int D>
+struct LaneWork {
+    Key k;
+    int op;
+    uint32_t probe;
+    uint32_t h[D], f[D];
+};
+
+template <int D>
+__device__ __forceinline__ void prepare(const ChunkArgs& a, uint64_t base, uint64_t len, uint64_t j, uint32_t lane,
+                                        uint64_t total_bytes, uint4* stage, LaneWork<D>& L) {
+    const SketchDesc& s = a.s;
+    const uint32_t kb = s.key_bytes;
+    const uint64_t rel = j + lane;
+    L.k = Key{0ull, 0ull};
+    L.op = 0;
+    L.probe = 0;
+    if (kb != 4 && kb != 8)
+        L.k = load_key_staged(a.keys, total_bytes, base + j, (uint32_t)((len - j) < 32 ? (len - j) : 32), kb, lane,
+                              stage);
+    else if (rel < len)
+        L.k = load_key(a.keys, base + rel, kb);
+    if (rel < len) {
+        L.op = a.ops ? (int)a.ops[base + rel] : a.op_const;
+        if (L.op != 0 && !key_indices<D>(s, L.k, L.h, L.f, &L.probe)) {
+            atomicOr(a.ctrl + kCtrlErr, kErrBadKey);
+            L.op = 0;
+        }
+    }
+}
+
+// Phase 1 for one warp-iteration: warp aggregation, Fat RED, dictionary claim/lookup and counts.
+// Returns the dictionary slot this lane claimed, or kNoSlot.
+template <int D>
+__device__ __forceinline__ uint32_t phase1(const ChunkArgs& a, const LaneWork<D>& L, uint32_t lane) {
+    const SketchDesc& s = a.s;
+    const unsigned act = __ballot_sync(kFull, L.op != 0);
+    if (act == 0u) return kNoSlot;
+    const unsigned ins = __ballot_sync(kFull, L.op > 0);
+    unsigned grp = __match_any_sync(kFull, L.k.x0);
+    if (s.key_bytes > 8) grp &= __match_any_sync(kFull, L.k.x1);
+    grp &= act;
+    if (L.op == 0 || lane != (uint32_t)(__ffs(grp) - 1)) return kNoSlot;
+
+    const uint32_t ci = __popc(grp & ins), cd = __popc(grp & ~ins);
+    const int32_t net = (int32_t)ci - (int32_t)cd;
+    if (net != 0) {
+#pragma unroll
+        for (int i = 0; i < D; ++i) atomicAdd(fat_ptr(s, i, L.h[i], L.f[i]), (uint32_t)net);
+    }
+    uint32_t av[D];
+    if (ci) {  // chunk-start Slim values, issued before the CAS so the latencies overlap
+#pragma unroll
+        for (int i = 0; i < D; ++i) av[i] = __ldcg(slim_ptr(s, i, L.h[i]));
+    }
+    const unsigned long long tag = L.k.x1 | kKeyTag;
+    uint32_t slot = L.probe & a.cap_mask;
+    bool found = false, claimed = false;
+    for (uint32_t p = 0; p <= a.cap_mask; ++p) {
+        unsigned long long ol, oh;
+        cas128(&a.dict[slot].key_lo, 0ull, 0ull, L.k.x0, tag, ol, oh);
+        if (oh == 0ull) {
+            found = claimed = true;
+            break;
+        }
+        if (ol == L.k.x0 && oh == tag) {
+            found = true;
+            break;
+        }
+        slot = (slot + 1u) & a.cap_mask;
+    }
+    if (!found) {
+        atomicOr(a.ctrl + kCtrlErr, kErrDictFull);
+        return kNoSlot;
+    }
+    if (ci) {
+        atomicAdd(&a.dict[slot].c_ins, ci);
+        uint32_t m = 0xFFFFFFFFu, mask = 0u;
+#pragma unroll
+        for (int i = 0; i < D; ++i) m = min(m, av[i]);
+#pragma unroll
+        for (int i = 0; i < D; ++i) mask |= (av[i] == m ? 1u : 0u) << i;
+        // every leader of this key stores the same chunk-start minimum and minimal-row mask
+        asm volatile("st.global.cg.v2.u32 [%0], {%1, %2};" ::"l"(&a.dict[slot].m), "r"(m), "r"(mask) : "memory");
+    }
+    if (cd) atomicAdd(&a.dict[slot].c_del, cd);
+    return claimed ? slot : kNoSlot;
+}
+
+// Phase 2 for one distinct key of the chunk (its entry ep, indices h/f).
+//   raise: T = min(m + c_ins, F); a row whose chunk-start value A0_i >= T needs no atomicMax
+//          (its final value is >= T anyway because T <= the bucket maximum).  Rows with
+//          A0_i == m are known from the mask; when c_ins == 1 every other row has A0_i >= m + 1 >= T.
+//   clamp: atomicMin of the bucket maximum for every row of a deleted key.
+template <int D>
+__device__ __forceinline__ void phase2_key(const ChunkArgs& a, DictEntry* ep, const uint32_t* h, const uint32_t* f,
+                                           uint32_t c_ins, uint32_t c_del, uint32_t m, uint32_t mask,
+                                           const uint32_t* Fv) {
+    const SketchDesc& s = a.s;
+    if (c_ins) {
+        uint32_t F = 0xFFFFFFFFu;
+#pragma unroll
+        for (int i = 0; i < D; ++i) F = min(F, Fv[i]);
+        const uint64_t mc = (uint64_t)m + c_ins;
+        const uint32_t T = mc < (uint64_t)F ? (uint32_t)mc : F;
+        if (T > m) {
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+                if (((mask >> i) & 1u) || c_ins > 1u) atomicMax(slim_ptr(s, i, h[i]), T);
+        }
+    }
+    if (c_del) {
+        bool under = false;
+#pragma unroll
+        for (int i = 0; i < D; ++i) atomicMin(slim_ptr(s, i, h[i]), bucket_max_cg(s, i, h[i], f[i], &under));
+        if (under) atomicOr(a.ctrl + kCtrlErr, kErrUnderflow);
+    }
+    clear_entry(ep);
+}
+
+template <int D>
+__global__ void __launch_bounds__(kChunkBlock, 1) chunk_update_kernel(const ChunkArgs a) {
+    extern __shared__ uint32_t s_claims[];  // dictionary slots this block claimed in the chunk
+    __shared__ uint32_t s_nclaims;
+    __shared__ uint4 s_stage[kChunkBlock / 32][32];
     const SketchDesc& s = a.s;
     const uint32_t lane = threadIdx.x & 31u;
-    const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint64_t gthreads = (uint64_t)gridDim.x * blockDim.x;
-    const uint64_t gwarp = gtid >> 5, nwarps = gthreads >> 5;
+    const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint64_t nchunks = (a.n + a.S - 1) / a.S;
+    const uint64_t total_bytes = a.n * s.key_bytes;
+    // one warp-iteration per chunk: each lane claims at most one slot and keeps it in registers
+    const bool single = 32ull * nwarps >= (uint64_t)a.S;
+    const bool may_ins = a.ops != nullptr || a.op_const > 0;
+    uint4* stage = s_stage[threadIdx.x >> 5];
+    unsigned long long target = (a.bar_base + 1ull) * gridDim.x;
 
+    LaneWork<D> pre;
+    bool have_pre = false;
     for (uint64_t c = 0; c < nchunks; ++c) {
         const uint64_t base = c * (uint64_t)a.S;
         const uint64_t len = min((uint64_t)a.S, a.n - base);
+        if (!single) {
+            if (threadIdx.x == 0) s_nclaims = 0u;
+            __syncthreads();
+        }
 
         // ---- phase 1: Fat updates and the chunk dictionary --------------------------------
+        uint32_t my_slot = kNoSlot;
+        uint32_t my_h[D], my_f[D];
         for (uint64_t j = gwarp * 32; j < len; j += nwarps * 32) {
-            const uint64_t rel = j + lane;
-            uint32_t h[kMaxD], f[kMaxD], probe = 0;
-            Key k{0ull, 0ull};
-            int op = 0;
-            if (rel < len) {
-                op = a.ops ? (int)a.ops[base + rel] : a.op_const;
-                if (op != 0) {
-                    k = load_key(a.keys, base + rel, s.key_bytes);
-                    if (!key_indices(s, k, h, f, &probe)) {
-                        atomicOr(a.ctrl + kCtrlErr, kErrBadKey);
-                        op = 0;
+            LaneWork<D> L;
+            if (have_pre && j == gwarp * 32) L = pre;
+            else prepare<D>(a, base, len, j, lane, total_bytes, stage, L);
+            have_pre = false;
+            const uint32_t slot = phase1<D>(a, L, lane);
+            if (slot != kNoSlot) {
+                if (single) {
+                    my_slot = slot;
+#pragma unroll
+                    for (int i = 0; i < D; ++i) {
+                        my_h[i] = L.h[i];
+                        my_f[i] = L.f[i];
                     }
+                } else {
+                    const uint32_t q = atomicAdd(&s_nclaims, 1u);
+                    if (q < a.claims_cap) s_claims[q] = slot;
+                    else atomicOr(a.ctrl + kCtrlErr, kErrDictFull);
                 }
             }
-            const unsigned act = __ballot_sync(kFull, op != 0);
-            if (act == 0u) continue;
-            const unsigned ins = __ballot_sync(kFull, op > 0);
-            unsigned grp = __match_any_sync(kFull, k.x0);
-            if (s.key_bytes > 8) grp &= __match_any_sync(kFull, k.x1);
-            grp &= act;
-            if (op == 0 || lane != (uint32_t)(__ffs(grp) - 1)) continue;
+        }
+        if (!grid_barrier(a.ctrl, target, a.timeout_ns)) return;
+        target += gridDim.x;
 
-            // one leader per distinct key of this warp
-            const uint32_t ci = __popc(grp & ins), cd = __popc(grp & ~ins);
-            const int32_t net = (int32_t)ci - (int32_t)cd;
-            if (net != 0) {
+        // ---- phase 2: Slim raises and clamps, once per distinct key (by its claimer) --------
+        if (single) {
+            if (my_slot != kNoSlot) {
+                DictEntry* ep = a.dict + my_slot;
+                const uint4 cn = __ldcg(reinterpret_cast<const uint4*>(ep) + 1);  // c_ins, c_del, m, mask
+                uint32_t Fv[D];
+                if (may_ins) {
 #pragma unroll
-                for (int i = 0; i < kMaxD; ++i)
-                    if (i < (int)s.d) atomicAdd(fat_ptr(s, i, h[i], f[i]), (uint32_t)net);
-            }
-            uint32_t slot = probe & a.cap_mask;
-            const uint32_t me = (uint32_t)rel + 1u;
-            bool found = false;
-            for (uint32_t p = 0; p <= a.cap_mask; ++p) {
-                const uint32_t cur = atomicCAS(&a.dict[slot].owner, 0u, me);
-                if (cur == 0u || key_equal(a.keys, base + cur - 1u, s.key_bytes, k)) {
-                    found = true;
-                    break;
+                    for (int i = 0; i < D; ++i) Fv[i] = __ldcg(fat_ptr(s, i, my_h[i], my_f[i]));
                 }
-                slot = (slot + 1u) & a.cap_mask;
+                phase2_key<D>(a, ep, my_h, my_f, cn.x, cn.y, cn.z, cn.w, Fv);
             }
-            if (!found) {
-                atomicOr(a.ctrl + kCtrlErr, kErrDictFull);
-                continue;
-            }
-            if (ci) {
-                atomicAdd(&a.dict[slot].c_ins, ci);
-                uint32_t m = 0xFFFFFFFFu;
+        } else {
+            const uint32_t nclaims = min(s_nclaims, a.claims_cap);
+            for (uint32_t q = threadIdx.x; q < nclaims; q += blockDim.x) {
+                DictEntry* ep = a.dict + s_claims[q];
+                unsigned long long k0, k1, c01, c23;
+                ld_entry(ep, k0, k1, c01, c23);
+                const Key k{k0, k1 & ~kKeyTag};
+                uint32_t h[D], f[D], probe, Fv[D];
+                key_indices<D>(s, k, h, f, &probe);
+                const uint32_t c_ins = (uint32_t)c01;
+                if (c_ins) {
 #pragma unroll
-                for (int i = 0; i < kMaxD; ++i)
-                    if (i < (int)s.d) m = min(m, __ldcg(slim_ptr(s, i, h[i])));
-                __stcg(&a.dict[slot].m, m);  // every writer stores the same chunk-start value
+                    for (int i = 0; i < D; ++i) Fv[i] = __ldcg(fat_ptr(s, i, h[i], f[i]));
+                }
+                phase2_key<D>(a, ep, h, f, c_ins, (uint32_t)(c01 >> 32), (uint32_t)c23, (uint32_t)(c23 >> 32), Fv);
             }
-            if (cd) atomicAdd(&a.dict[slot].c_del, cd);
         }
-        if (!grid_barrier(a.ctrl, gridDim.x, a.timeout_ns)) return;
 
-        // ---- phase 2: Slim raises and clamps, one thread per distinct key -----------------
-        for (uint64_t slot = gtid; slot <= a.cap_mask; slot += gthreads) {
-            uint4* ep = reinterpret_cast<uint4*>(a.dict + slot);
-            const uint4 e = __ldcg(ep);
-            if (e.x == 0u) continue;
-            const Key k = load_key(a.keys, base + e.x - 1u, s.key_bytes);
-            uint32_t h[kMaxD], f[kMaxD], probe;
-            key_indices(s, k, h, f, &probe);
-            if (e.y) {
-                uint32_t F = 0xFFFFFFFFu;
-#pragma unroll
-                for (int i = 0; i < kMaxD; ++i)
-                    if (i < (int)s.d) F = min(F, __ldcg(fat_ptr(s, i, h[i], f[i])));
-                const uint64_t mc = (uint64_t)e.w + e.y;
-                const uint32_t T = mc < (uint64_t)F ? (uint32_t)mc : F;
-#pragma unroll
-                for (int i = 0; i < kMaxD; ++i)
-                    if (i < (int)s.d) {
-                        uint32_t* ap = slim_ptr(s, i, h[i]);
-                        if (__ldcg(ap) < T) atomicMax(ap, T);
-                    }
+        // prepare the next chunk's first iteration (keys, ops, hashes) while others finish
+        if (c + 1 < nchunks) {
+            const uint64_t base1 = base + a.S;
+            const uint64_t len1 = min((uint64_t)a.S, a.n - base1);
+            if (gwarp * 32 < len1) {
+                prepare<D>(a, base1, len1, gwarp * 32, lane, total_bytes, stage, pre);
+                have_pre = true;
             }
-            if (e.z) {
-                bool under = false;
-#pragma unroll
-                for (int i = 0; i < kMaxD; ++i)
-                    if (i < (int)s.d) {
-                        const uint32_t M = bucket_max_cg(s, i, h[i], f[i], &under);
-                        uint32_t* ap = slim_ptr(s, i, h[i]);
-                        if (__ldcg(ap) > M) atomicMin(ap, M);
-                    }
-                if (under) atomicOr(a.ctrl + kCtrlErr, kErrUnderflow);
-            }
-            __stcg(ep, make_uint4(0u, 0u, 0u, 0u));
         }
-        if (!grid_barrier(a.ctrl, gridDim.x, a.timeout_ns)) return;
+        if (!grid_barrier(a.ctrl, target, a.timeout_ns)) return;
+        target += gridDim.x;
     }
 }
 
@@ -237,25 +398,69 @@ __global__ void __launch_bounds__(kSeqBlock) seq_update_kernel(const SeqArgs a) 
 
 }  // namespace
 
-int chunk_update_blocks_per_sm() {
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, chunk_update_kernel, kChunkBlock, 0) != cudaSuccess)
-        return 0;
-    return nb;
-}
-
-cudaError_t launch_chunk_update(const ChunkArgs& a, int grid, cudaStream_t st) {
+template <int D>
+static cudaError_t launch_chunk_d(const ChunkArgs& a, int grid, cudaStream_t st) {
+    const size_t smem = (size_t)a.claims_cap * sizeof(uint32_t);
+    cudaError_t e = cudaFuncSetAttribute(chunk_update_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(kChunkBlock);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, chunk_update_kernel, a);
+    return cudaLaunchKernelEx(&cfg, chunk_update_kernel<D>, a);
+}
+
+template <int D>
+static int blocks_per_sm_d() {
+    int nb = 0;
+    // the claim list of the largest chunk fits in 64 KiB of dynamic shared memory per block
+    if (cudaFuncSetAttribute(chunk_update_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, chunk_update_kernel<D>, kChunkBlock, 65536) != cudaSuccess)
+        return 0;
+    return nb;
+}
+
+int chunk_update_blocks_per_sm(uint32_t d) {
+    switch (d) {
+        case 1: return blocks_per_sm_d<1>();
+        case 2: return blocks_per_sm_d<2>();
+        case 3: return blocks_per_sm_d<3>();
+        case 4: return blocks_per_sm_d<4>();
+        case 5: return blocks_per_sm_d<5>();
+        case 6: return blocks_per_sm_d<6>();
+        case 7: return blocks_per_sm_d<7>();
+        case 8: return blocks_per_sm_d<8>();
+        default: return 0;
+    }
+}
+
+uint32_t chunk_claims_cap(uint32_t S, int grid) {
+    // a block claims at most one slot per update it handles: iterations per chunk x block size
+    const uint64_t per_iter = (uint64_t)grid * kChunkBlock;
+    const uint64_t iters = (S + per_iter - 1) / per_iter;
+    return (uint32_t)(iters * kChunkBlock);
+}
+
+cudaError_t launch_chunk_update(const ChunkArgs& a, int grid, cudaStream_t st) {
+    switch (a.s.d) {
+        case 1: return launch_chunk_d<1>(a, grid, st);
+        case 2: return launch_chunk_d<2>(a, grid, st);
+        case 3: return launch_chunk_d<3>(a, grid, st);
+        case 4: return launch_chunk_d<4>(a, grid, st);
+        case 5: return launch_chunk_d<5>(a, grid, st);
+        case 6: return launch_chunk_d<6>(a, grid, st);
+        case 7: return launch_chunk_d<7>(a, grid, st);
+        case 8: return launch_chunk_d<8>(a, grid, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_seq_update(const SeqArgs& a, cudaStream_t st, int smem_limit) {
