@@ -171,6 +171,35 @@ sf_status sf_query_batch(const sf_slim_view *slim, const void *keys_dev, uint64_
 /* Waits for the handle's stream and returns (then clears) errors latched on the device. */
 sf_status sf_sync(sf_sketch *s);
 
+/*
+ * Update without any caller scratch -- the paper has no counterpart; this is a deployment aid.
+ *
+ * For callers that cannot allocate device memory at update time: a serving or packet loop that
+ * reserved all of its memory at start-up and must not call cudaMalloc (it can block and
+ * synchronise the device), or a plugin living inside another framework's memory pool.  It applies
+ * the same chunked insert/delete rules as sf_update_batch to the caller's Fat (fat_dev) and Slim
+ * (slim_dev) -- laid out as sf_required_bytes describes and zeroed by the caller before the first
+ * update -- but takes no scratch buffer and no handle.  ops_dev may be NULL (all insertions).
+ *
+ * The per-chunk dictionary and control words live in one fixed device array of this library
+ * (2 MiB + 256 B), which every GPU that loads the library keeps until the process exits.  Hence:
+ *   - params->chunk must be 2..SF_NOALLOC_MAX_CHUNK; larger chunks return SF_ERR_INVALID (the
+ *     array is sized for that maximum), as do explicit-index flags;
+ *   - all calls share the array, so calls that may overlap on the GPU (different streams,
+ *     different threads) race and corrupt each other's result: serialise them;
+ *   - the call zeroes the array's control words and dictionary itself before its kernel runs;
+ *   - the first call on a device looks up the array's device address (cudaGetSymbolAddress, with
+ *     that device current); make that first call before capturing any CUDA stream.
+ * No device memory is allocated: no cudaMalloc/cudaFree, no allocating library call.  If err_dev
+ * (device, 4 bytes) is not NULL it receives the device-side error bits of this call (0 = none;
+ * bit 0 = a Fat counter went negative, i.e. a delete of an item never inserted; bit 1 = a device
+ * wait timed out).  Asynchronous on cuda_stream.
+ */
+#define SF_NOALLOC_MAX_CHUNK 16384u
+sf_status sf_update_batch_noalloc(const sf_params *p, uint32_t *fat_dev, uint32_t *slim_dev,
+                                  const void *keys_dev, const int8_t *ops_dev, uint64_t n,
+                                  uint32_t *err_dev, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

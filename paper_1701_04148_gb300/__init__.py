@@ -77,6 +77,9 @@ _SIGS = {
     "sf_query_batch": (ctypes.c_int32, [ctypes.POINTER(SlimView), ctypes.c_void_p, ctypes.c_uint64,
                                         ctypes.c_void_p, ctypes.c_void_p]),
     "sf_sync": (ctypes.c_int32, [ctypes.c_void_p]),
+    "sf_update_batch_noalloc": (ctypes.c_int32, [ctypes.POINTER(Params), ctypes.c_void_p, ctypes.c_void_p,
+                                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
+                                                 ctypes.c_void_p]),
     "sf_bench_random_access": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
                                                 ctypes.c_uint32, ctypes.c_void_p]),
     "sf_bench_grid_barrier": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]),
@@ -277,3 +280,14 @@ def query(slim, hdr: SlimHeader, keys, out=None, stream=None, index_table=None):
 def as_u32(t):
     """View an int32 tensor of counters as int64 holding the unsigned values."""
     return t.to(_torch().int64) & 0xFFFFFFFF
+
+
+def update_batch_noalloc(params: Params, fat, slim, keys, ops=None, err=None, stream=None) -> None:
+    """sf_update_batch_noalloc: the chunked update with the library's fixed scratch array
+    (no scratch buffer from the caller).  fat/slim: caller tensors laid out as required_bytes says."""
+    torch = _torch()
+    n = keys.shape[0] if (keys.dim() == 2 and keys.dtype == torch.uint8) else \
+        keys.numel() * keys.element_size() // params.key_bytes
+    check(load().sf_update_batch_noalloc(ctypes.byref(params), _dev_ptr(fat, "fat"), _dev_ptr(slim, "slim"),
+                                         _dev_ptr(keys, "keys") if n else 0, _dev_ptr(ops, "ops"), n,
+                                         _dev_ptr(err, "err"), _stream_handle(stream)), "sf_update_batch_noalloc")

@@ -1,0 +1,108 @@
+// sf_noalloc.cu -- an update entry point that needs no scratch buffer from the caller.
+//
+// Some callers cannot allocate device memory when they update a sketch: a packet-processing or
+// serving loop that reserved all of its device memory up front and must not call cudaMalloc
+// (which can block and synchronise the whole device), or a plugin that runs inside another
+// framework's memory pool and has no allocator of its own.  sf_update_batch_noalloc serves them:
+// the caller passes only the sketch counters and the update batch, and the per-chunk key
+// dictionary and control words live in the fixed device array below, which every GPU that loads
+// this library keeps until the process exits.
+#include <mutex>
+
+#include "../../include/sf.h"
+#include "sf_internal.h"
+
+namespace {
+
+constexpr uint64_t kNoAllocCtrlBytes = 256;
+constexpr uint64_t kNoAllocScratchBytes =
+    kNoAllocCtrlBytes + (uint64_t)(4u * SF_NOALLOC_MAX_CHUNK) * sizeof(sfk::DictEntry);  // 2 MiB + 256 B
+
+// The shared scratch: control words (error bits, barrier counter) then the key dictionary.
+static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void* g_scratch_dev[kMaxDevices] = {};  // device address of g_noalloc_scratch, per device
+
+uint64_t splitmix64_step(uint64_t* st) {
+    uint64_t z = (*st += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Device address of the scratch array on the current device.  Host code cannot pass the symbol
+// itself to a kernel: on the host it names a host-side stand-in, not device memory.
+sf_status scratch_address(int dev, void** out) {
+    if (dev < 0 || dev >= kMaxDevices) return SF_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_scratch_dev[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SF_ERR_CUDA;
+        g_scratch_dev[dev] = p;
+    }
+    *out = g_scratch_dev[dev];
+    return SF_OK;
+}
+
+}  // namespace
+
+extern "C" sf_status sf_update_batch_noalloc(const sf_params* p, uint32_t* fat_dev, uint32_t* slim_dev,
+                                             const void* keys_dev, const int8_t* ops_dev, uint64_t n,
+                                             uint32_t* err_dev, void* cuda_stream) {
+    if (!p || !fat_dev || !slim_dev) return SF_ERR_INVALID;
+    if (p->d < 1 || p->d > SF_MAX_D || p->w < 1 || p->w > 0x7FFFFFFFu || p->z < 1 || p->z > SF_MAX_Z ||
+        p->key_bytes < 1 || p->key_bytes > SF_MAX_KEY_BYTES || p->flags != 0)
+        return SF_ERR_INVALID;
+    if (p->chunk < 2 || p->chunk > SF_NOALLOC_MAX_CHUNK) return SF_ERR_INVALID;  // beyond the fixed scratch
+    if (((uintptr_t)fat_dev & 15u) || ((uintptr_t)slim_dev & 15u)) return SF_ERR_INVALID;
+    if (n == 0) return SF_OK;
+    if (!keys_dev) return SF_ERR_INVALID;
+    if ((p->key_bytes == 4 || p->key_bytes == 8) && ((uintptr_t)keys_dev % p->key_bytes) != 0) return SF_ERR_INVALID;
+
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return SF_ERR_CUDA;
+    void* scratch = nullptr;
+    const sf_status st = scratch_address(dev, &scratch);
+    if (st != SF_OK) return st;
+    const int bps = sfk::chunk_update_blocks_per_sm(p->d);
+    if (bps <= 0) return SF_ERR_CUDA;
+    const int grid = sms * (bps < 2 ? bps : 2);
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+
+    // The array keeps whatever the previous call left: zero the control words and the dictionary
+    // (a call that stopped early may leave claimed entries behind).
+    const uint32_t cap = sfk::dict_capacity(p->chunk);
+    if (cudaMemsetAsync(scratch, 0, kNoAllocCtrlBytes + (uint64_t)cap * sizeof(sfk::DictEntry), stream) != cudaSuccess)
+        return SF_ERR_CUDA;
+
+    sfk::ChunkArgs a{};
+    a.s.A = slim_dev;
+    a.s.B = fat_dev;
+    a.s.d = p->d;
+    a.s.w = p->w;
+    a.s.z = p->z;
+    a.s.key_bytes = p->key_bytes;
+    uint64_t seed = p->seed;
+    for (uint32_t i = 0; i < SF_MAX_D; ++i) a.s.rs[i] = i < p->d ? splitmix64_step(&seed) : 0;
+    a.s.idx_table = nullptr;
+    a.s.n_ids = 0;
+    a.keys = (const uint8_t*)keys_dev;
+    a.ops = ops_dev;
+    a.op_const = 1;
+    a.n = n;
+    a.S = p->chunk;
+    a.cap_mask = cap - 1u;
+    a.dict = (sfk::DictEntry*)((uint8_t*)scratch + kNoAllocCtrlBytes);
+    a.ctrl = (uint32_t*)scratch;
+    a.bar_base = 0;  // the barrier counter was just zeroed
+    a.claims_cap = sfk::chunk_claims_cap(p->chunk, grid);
+    a.timeout_ns = sfk::kBarrierTimeoutNs;
+    if (sfk::launch_chunk_update(a, grid, stream) != cudaSuccess) return SF_ERR_CUDA;
+    if (err_dev && cudaMemcpyAsync(err_dev, scratch, sizeof(uint32_t), cudaMemcpyDeviceToDevice, stream) != cudaSuccess)
+        return SF_ERR_CUDA;
+    return SF_OK;
+}
