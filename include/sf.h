@@ -60,7 +60,7 @@ typedef int32_t sf_status;
 #define SF_MAX_D 8
 #define SF_MAX_Z 64
 #define SF_MAX_KEY_BYTES 15
-#define SF_MAX_CHUNK (1u << 22)
+#define SF_MAX_CHUNK (1u << 20)
 
 #define SF_SLIM_MAGIC   0x4D494C53u  /* "SLIM" */
 #define SF_SLIM_VERSION 1u
@@ -170,6 +170,54 @@ sf_status sf_query_batch(const sf_slim_view *slim, const void *keys_dev, uint64_
 
 /* Waits for the handle's stream and returns (then clears) errors latched on the device. */
 sf_status sf_sync(sf_sketch *s);
+
+/*
+ * ---- Batched many-sketch update --------------------------------------------------------------
+ * Monitoring nodes each fill their own sketch (Sec. 1.1); a collector-side or node-side host may
+ * hold thousands of them.  The paper updates one sketch at a time; a batch applies one call's
+ * stream to each of many sketches in ONE persistent cooperative launch (captured in a CUDA graph
+ * and replayed when the batch shape repeats).  Every sketch gets exactly the chunked semantics of
+ * sf_update_batch with its own params.chunk: round r of the launch processes chunk r of every
+ * sketch, so the result equals one sf_update_batch call per sketch, bit for bit.
+ */
+typedef struct sf_batch sf_batch;
+
+typedef struct sf_batch_item {
+    sf_sketch *sketch;        /* distinct sketches, all with the same d, on the batch's device   */
+    const void *keys_dev;     /* n packed keys of the sketch's key_bytes (device)                */
+    const int8_t *ops_dev;    /* +1 insert / -1 delete / 0 skip per key, or NULL (all inserts)  */
+    uint64_t n;
+} sf_batch_item;
+
+#define SF_BATCH_GRAPH 1u     /* capture the launch in a CUDA graph and replay it               */
+
+/* Device scratch of a batch of up to max_sketches items: control words + the run table. */
+sf_status sf_batch_required_bytes(uint32_t max_sketches, uint64_t *scratch_bytes);
+
+/*
+ * Creates a batch bound to cuda_stream and to caller-owned scratch_dev (sf_batch_required_bytes,
+ * 16-byte aligned; zeroed here).  The batch allocates a pinned host staging table and a private
+ * capture stream, no device memory.  flags: SF_BATCH_GRAPH or 0 (direct launches).
+ */
+sf_status sf_batch_create(uint32_t max_sketches, void *scratch_dev, void *cuda_stream, uint32_t flags,
+                          sf_batch **out);
+
+/*
+ * Enqueues items[0..n_items) as one launch on the batch's stream.  The sketches' own pending work
+ * must be ordered before it (same stream, or synchronised).  A call whose per-round slot count
+ * exceeds what one launch can hold returns SF_ERR_INVALID.  Device errors: sf_batch_sync.
+ */
+sf_status sf_batch_update(sf_batch *b, uint32_t n_items, const sf_batch_item *items);
+
+/* Waits for the batch's stream; returns (then clears) device errors of the batch's launches.
+ * After SF_ERR_TIMEOUT the sketches of the last call must be re-created. */
+sf_status sf_batch_sync(sf_batch *b);
+
+/* Counters: graph launches, graph captures, and the round count of the last call. */
+sf_status sf_batch_info(const sf_batch *b, uint32_t *graph_launches, uint32_t *graph_captures,
+                        uint64_t *rounds_last);
+
+sf_status sf_batch_destroy(sf_batch *b);
 
 /*
  * Update without any caller scratch -- the paper has no counterpart; this is a deployment aid.

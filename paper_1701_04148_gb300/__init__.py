@@ -77,6 +77,14 @@ _SIGS = {
     "sf_query_batch": (ctypes.c_int32, [ctypes.POINTER(SlimView), ctypes.c_void_p, ctypes.c_uint64,
                                         ctypes.c_void_p, ctypes.c_void_p]),
     "sf_sync": (ctypes.c_int32, [ctypes.c_void_p]),
+    "sf_batch_required_bytes": (ctypes.c_int32, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64)]),
+    "sf_batch_create": (ctypes.c_int32, [ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32,
+                                         ctypes.POINTER(ctypes.c_void_p)]),
+    "sf_batch_update": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]),
+    "sf_batch_sync": (ctypes.c_int32, [ctypes.c_void_p]),
+    "sf_batch_info": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32),
+                                       ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint64)]),
+    "sf_batch_destroy": (ctypes.c_int32, [ctypes.c_void_p]),
     "sf_update_batch_noalloc": (ctypes.c_int32, [ctypes.POINTER(Params), ctypes.c_void_p, ctypes.c_void_p,
                                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
                                                  ctypes.c_void_p]),
@@ -254,6 +262,66 @@ class Sketch:
     def close(self):
         if getattr(self, "handle", None):
             load().sf_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [("sketch", ctypes.c_void_p), ("keys_dev", ctypes.c_void_p), ("ops_dev", ctypes.c_void_p),
+                ("n", ctypes.c_uint64)]
+
+
+SF_BATCH_GRAPH = 1
+
+
+class Batch:
+    """Many sketches updated by one persistent launch (sf_batch_*), CUDA graph replay by default."""
+
+    def __init__(self, max_sketches: int, graph: bool = True, stream=None, device=None):
+        torch = _torch()
+        L = load()
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        xb = ctypes.c_uint64()
+        check(L.sf_batch_required_bytes(max_sketches, ctypes.byref(xb)), "sf_batch_required_bytes")
+        self.scratch = torch.empty(xb.value // 4 + 4, dtype=torch.int32, device=self.device)
+        h = ctypes.c_void_p()
+        check(L.sf_batch_create(max_sketches, self.scratch.data_ptr(), _stream_handle(self.stream),
+                                SF_BATCH_GRAPH if graph else 0, ctypes.byref(h)), "sf_batch_create")
+        self.handle = h
+        self.max_sketches = max_sketches
+        self._keep = None
+
+    def update(self, items):
+        """items: list of (Sketch, keys tensor, ops tensor or None)."""
+        arr = (BatchItem * len(items))()
+        keep = []
+        for i, (sk, keys, ops) in enumerate(items):
+            k, n = sk._keys(keys)
+            arr[i] = BatchItem(sk.handle.value, _dev_ptr(k, "keys") if n else 0, _dev_ptr(ops, "ops"), n)
+            keep.append((k, ops))
+        self._keep = keep
+        check(load().sf_batch_update(self.handle, len(items), ctypes.cast(arr, ctypes.c_void_p)), "sf_batch_update")
+
+    def sync(self) -> int:
+        return check(load().sf_batch_sync(self.handle), "sf_batch_sync")
+
+    def sync_status(self) -> int:
+        return load().sf_batch_sync(self.handle)
+
+    def info(self):
+        gl, gc, rl = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint64()
+        check(load().sf_batch_info(self.handle, ctypes.byref(gl), ctypes.byref(gc), ctypes.byref(rl)), "sf_batch_info")
+        return {"graph_launches": gl.value, "graph_captures": gc.value, "rounds_last": rl.value}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().sf_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -12,25 +12,7 @@
 #include "../../include/sf.h"
 #include "sf_internal.h"
 
-struct sf_sketch {
-    sf_params p;
-    uint32_t* A;
-    uint32_t* B;
-    uint8_t* scratch;
-    cudaStream_t stream;
-    int device;
-    int num_sms;
-    int chunk_grid;
-    int smem_optin;
-    uint64_t rs[SF_MAX_D];
-    uint32_t* ctrl;
-    sfk::DictEntry* dict;
-    uint32_t cap;
-    const uint32_t* idx_table;
-    uint32_t n_ids;
-    uint64_t bar_epoch;     // grid barriers passed on this scratch buffer (monotonic counter)
-    uint32_t claims_cap;    // per-block claim list length of the chunk kernel
-};
+#include "sf_handle.h"
 
 namespace {
 
@@ -93,20 +75,17 @@ sf_status run_update(sf_sketch* s, const void* keys, const int8_t* ops, int op_c
         a.ctrl = s->ctrl;
         e = sfk::launch_seq_update(a, s->stream, s->smem_optin);
     } else {
-        sfk::ChunkArgs a{};
-        a.s = desc_of(s);
-        a.keys = (const uint8_t*)keys;
-        a.ops = ops;
-        a.op_const = op_const;
-        a.n = n;
-        a.S = s->p.chunk;
-        a.cap_mask = s->cap - 1u;
-        a.dict = s->dict;
-        a.ctrl = s->ctrl;
-        a.bar_base = s->bar_epoch;
-        a.claims_cap = s->claims_cap;
-        a.timeout_ns = sfk::kBarrierTimeoutNs;
-        e = sfk::launch_chunk_update(a, s->chunk_grid, s->stream);
+        sfk::SketchRun one{};
+        one.s = desc_of(s);
+        one.keys = (const uint8_t*)keys;
+        one.ops = ops;
+        one.op_const = op_const;
+        one.S = s->p.chunk;
+        one.n = n;
+        one.flat_base = 0;
+        one.dict = s->dict;
+        one.cap_mask = s->cap - 1u;
+        e = sfk::launch_chunk_update(one, s->ctrl, s->bar_epoch, s->claims_cap, s->chunk_grid, s->stream);
         if (e == cudaSuccess) s->bar_epoch += 2ull * ((n + s->p.chunk - 1) / s->p.chunk);
     }
     if (cur != s->device) cudaSetDevice(cur);
@@ -175,7 +154,7 @@ sf_status sf_create(const sf_params* p, void* fat_dev, void* slim_dev, void* scr
         return SF_ERR_CUDA;
     }
     s->chunk_grid = s->num_sms * (bps < 2 ? bps : 2);
-    s->claims_cap = sfk::chunk_claims_cap(p->chunk, s->chunk_grid);
+    s->claims_cap = sfk::chunk_claims_cap(sfk::round_up32(p->chunk), s->chunk_grid);
     s->bar_epoch = 0;
     uint64_t fb, sb, xb;
     sf_required_bytes(p, &fb, &sb, &xb);

@@ -1,0 +1,237 @@
+// sf_batch.cu -- batched many-sketch update: one persistent cooperative launch per call,
+// captured in a CUDA graph and replayed while the batch shape repeats.
+//
+// The launch walks all sketches of the call in lockstep rounds (round r = chunk r of every
+// sketch, each with its own chunk size), with two grid barriers per round; see sf_update.cu for
+// the per-chunk phases.  Sketches are independent, so the lockstep changes nothing in any
+// sketch's result: it only spreads every stream over the whole GPU.
+#include <cstring>
+#include <new>
+
+#include "sf_handle.h"
+
+struct sf_batch {
+    uint32_t max_sketches;
+    uint8_t* scratch;
+    uint32_t* ctrl;
+    sfk::SketchRun* table_dev;
+    sfk::SketchRun* staging;  // pinned host copy of the run table
+    cudaStream_t stream;
+    cudaStream_t cap_stream;  // private stream used only for graph capture
+    cudaEvent_t staged;
+    bool staging_busy;
+    uint32_t flags;
+    int device;
+    int num_sms;
+    // graph of the last shape
+    bool have_exec;
+    cudaGraphExec_t exec;
+    sfk::BatchArgs exec_args;
+    uint32_t exec_d;
+    int exec_grid;
+    uint32_t graph_launches, graph_captures;
+    uint64_t rounds_last;
+};
+
+namespace {
+
+constexpr uint64_t kBatchCtrlBytes = 256;
+
+bool same_shape(const sfk::BatchArgs& x, const sfk::BatchArgs& y) {
+    return x.n_runs == y.n_runs && x.claims_cap == y.claims_cap && x.flat_len == y.flat_len &&
+           x.n_rounds == y.n_rounds && x.may_ins == y.may_ins && x.may_del == y.may_del && x.runs == y.runs;
+}
+
+cudaError_t enqueue(sf_batch* b, const sfk::BatchArgs& a, uint32_t d, int grid, size_t table_bytes,
+                    cudaStream_t st) {
+    cudaError_t e = cudaMemcpyAsync(b->table_dev, b->staging, table_bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(b->ctrl + sfk::kCtrlBarrier64, 0, sizeof(unsigned long long), st);  // barrier counter
+    if (e != cudaSuccess) return e;
+    return sfk::launch_batch_update(a, d, grid, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+sf_status sf_batch_required_bytes(uint32_t max_sketches, uint64_t* scratch_bytes) {
+    if (max_sketches == 0 || !scratch_bytes) return SF_ERR_INVALID;
+    *scratch_bytes = kBatchCtrlBytes + (uint64_t)max_sketches * sizeof(sfk::SketchRun);
+    return SF_OK;
+}
+
+sf_status sf_batch_create(uint32_t max_sketches, void* scratch_dev, void* cuda_stream, uint32_t flags,
+                          sf_batch** out) {
+    if (!out || !scratch_dev || max_sketches == 0 || ((uintptr_t)scratch_dev & 15u) || (flags & ~SF_BATCH_GRAPH))
+        return SF_ERR_INVALID;
+    *out = nullptr;
+    sf_batch* b = new (std::nothrow) sf_batch();
+    if (!b) return SF_ERR_OOM;
+    b->max_sketches = max_sketches;
+    b->scratch = (uint8_t*)scratch_dev;
+    b->ctrl = (uint32_t*)scratch_dev;
+    b->table_dev = (sfk::SketchRun*)((uint8_t*)scratch_dev + kBatchCtrlBytes);
+    b->stream = (cudaStream_t)cuda_stream;
+    b->flags = flags;
+    uint64_t xb = 0;
+    sf_batch_required_bytes(max_sketches, &xb);
+    if (cudaGetDevice(&b->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess ||
+        cudaHostAlloc((void**)&b->staging, (size_t)max_sketches * sizeof(sfk::SketchRun), cudaHostAllocDefault) !=
+            cudaSuccess) {
+        delete b;
+        return SF_ERR_CUDA;
+    }
+    if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMemsetAsync(scratch_dev, 0, xb, b->stream) != cudaSuccess) {
+        cudaFreeHost(b->staging);
+        delete b;
+        return SF_ERR_CUDA;
+    }
+    *out = b;
+    return SF_OK;
+}
+
+sf_status sf_batch_update(sf_batch* b, uint32_t n_items, const sf_batch_item* items) {
+    if (!b || (n_items && !items) || n_items > b->max_sketches) return SF_ERR_INVALID;
+    if (n_items == 0) return SF_OK;
+    const uint32_t d = items[0].sketch ? items[0].sketch->p.d : 0;
+    for (uint32_t i = 0; i < n_items; ++i) {
+        const sf_sketch* s = items[i].sketch;
+        if (!s || s->p.d != d || s->p.chunk < 2 || s->device != b->device || (s->p.flags & SF_FLAG_EXPLICIT_INDEX))
+            return SF_ERR_INVALID;
+        if (items[i].n && !items[i].keys_dev) return SF_ERR_INVALID;
+        const uint32_t kb = s->p.key_bytes;
+        if ((kb == 4 || kb == 8) && ((uintptr_t)items[i].keys_dev % kb) != 0) return SF_ERR_INVALID;
+    }
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return SF_ERR_CUDA;
+    if (cur != b->device && cudaSetDevice(b->device) != cudaSuccess) return SF_ERR_CUDA;
+    if (b->staging_busy && cudaEventSynchronize(b->staged) != cudaSuccess) return SF_ERR_CUDA;
+
+    uint64_t flat = 0, rounds = 0;
+    bool may_ins = false, may_del = false;
+    for (uint32_t i = 0; i < n_items; ++i) {
+        const sf_sketch* s = items[i].sketch;
+        sfk::SketchRun& R = b->staging[i];
+        std::memset(&R, 0, sizeof(R));
+        R.s.A = s->A;
+        R.s.B = s->B;
+        R.s.d = s->p.d;
+        R.s.w = s->p.w;
+        R.s.z = s->p.z;
+        R.s.key_bytes = s->p.key_bytes;
+        for (int r = 0; r < SF_MAX_D; ++r) R.s.rs[r] = s->rs[r];
+        R.keys = (const uint8_t*)items[i].keys_dev;
+        R.ops = items[i].ops_dev;
+        R.op_const = 1;
+        R.S = s->p.chunk;
+        R.n = items[i].n;
+        R.flat_base = flat;
+        R.dict = s->dict;
+        R.cap_mask = s->cap - 1u;
+        flat += sfk::round_up32(R.S);
+        const uint64_t nr = (R.n + R.S - 1) / R.S;
+        rounds = nr > rounds ? nr : rounds;
+        if (R.n) {
+            may_ins |= R.ops != nullptr;
+            may_del |= R.ops != nullptr;
+            may_ins |= R.ops == nullptr;
+        }
+    }
+    const int bps = sfk::chunk_update_blocks_per_sm(d);
+    if (bps <= 0) return SF_ERR_CUDA;
+    const int grid = b->num_sms * (bps < 2 ? bps : 2);
+    sfk::BatchArgs a{};
+    a.runs = b->table_dev;
+    a.n_runs = n_items;
+    a.flat_len = flat;
+    a.n_rounds = rounds;
+    a.claims_cap = sfk::chunk_claims_cap(flat, grid);
+    a.ctrl = b->ctrl;
+    a.bar_base = 0;  // the launch zeroes the barrier counter first
+    a.timeout_ns = sfk::kBarrierTimeoutNs;
+    a.may_ins = may_ins;
+    a.may_del = may_del;
+    if ((uint64_t)a.claims_cap * sizeof(uint2) > (uint64_t)sfk::kMaxClaimSmem) return SF_ERR_INVALID;
+    const size_t table_bytes = (size_t)n_items * sizeof(sfk::SketchRun);
+    b->rounds_last = rounds;
+
+    cudaError_t e = cudaSuccess;
+    bool launched = false;
+    if (b->flags & SF_BATCH_GRAPH) {
+        if (!b->have_exec || !same_shape(b->exec_args, a) || b->exec_d != d || b->exec_grid != grid) {
+            if (b->have_exec) {
+                cudaGraphExecDestroy(b->exec);
+                b->have_exec = false;
+            }
+            cudaGraph_t g = nullptr;
+            bool ok = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            if (ok) {
+                const cudaError_t ce = enqueue(b, a, d, grid, table_bytes, b->cap_stream);
+                ok = cudaStreamEndCapture(b->cap_stream, &g) == cudaSuccess && ce == cudaSuccess && g;
+            }
+            if (ok) ok = cudaGraphInstantiate(&b->exec, g, 0) == cudaSuccess;
+            if (g) cudaGraphDestroy(g);
+            if (ok) {
+                b->have_exec = true;
+                b->exec_args = a;
+                b->exec_d = d;
+                b->exec_grid = grid;
+                b->graph_captures++;
+            } else {
+                cudaGetLastError();           // capture not supported here: launch directly from now on
+                b->flags &= ~SF_BATCH_GRAPH;
+            }
+        }
+        if (b->have_exec) {
+            e = cudaGraphLaunch(b->exec, b->stream);
+            launched = true;
+            if (e == cudaSuccess) b->graph_launches++;
+        }
+    }
+    if (!launched) e = enqueue(b, a, d, grid, table_bytes, b->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(b->staged, b->stream);
+    b->staging_busy = true;
+    if (cur != b->device) cudaSetDevice(cur);
+    return e == cudaSuccess ? SF_OK : SF_ERR_CUDA;
+}
+
+sf_status sf_batch_sync(sf_batch* b) {
+    if (!b) return SF_ERR_INVALID;
+    uint32_t err = 0;
+    if (cudaMemcpyAsync(&err, b->ctrl + sfk::kCtrlErr, 4, cudaMemcpyDeviceToHost, b->stream) != cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess)
+        return SF_ERR_CUDA;
+    if (err == 0) return SF_OK;
+    if (cudaMemsetAsync(b->ctrl, 0, kBatchCtrlBytes, b->stream) != cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess)
+        return SF_ERR_CUDA;
+    if (err & sfk::kErrTimeout) return SF_ERR_TIMEOUT;
+    if (err & (sfk::kErrBadKey | sfk::kErrDictFull)) return SF_ERR_INVALID;
+    if (err & sfk::kErrUnderflow) return SF_ERR_UNDERFLOW;
+    return SF_ERR_INVALID;
+}
+
+sf_status sf_batch_info(const sf_batch* b, uint32_t* graph_launches, uint32_t* graph_captures, uint64_t* rounds_last) {
+    if (!b) return SF_ERR_INVALID;
+    if (graph_launches) *graph_launches = b->graph_launches;
+    if (graph_captures) *graph_captures = b->graph_captures;
+    if (rounds_last) *rounds_last = b->rounds_last;
+    return SF_OK;
+}
+
+sf_status sf_batch_destroy(sf_batch* b) {
+    if (!b) return SF_ERR_INVALID;
+    if (b->staging_busy) cudaEventSynchronize(b->staged);
+    if (b->have_exec) cudaGraphExecDestroy(b->exec);
+    cudaEventDestroy(b->staged);
+    cudaStreamDestroy(b->cap_stream);
+    cudaFreeHost(b->staging);
+    delete b;
+    return SF_OK;
+}
+
+}  // extern "C"

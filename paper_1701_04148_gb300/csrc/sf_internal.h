@@ -8,20 +8,36 @@
 
 namespace sfk {
 
-struct ChunkArgs {
+// One sketch's share of a chunked-update launch.  A launch walks its sketches in lockstep
+// rounds: round r processes chunk r (updates [r*S, min((r+1)*S, n))) of every sketch.
+struct SketchRun {
     SketchDesc s;
     const uint8_t* keys;
-    const int8_t* ops;    // nullptr: every update is op_const
+    const int8_t* ops;     // nullptr: every update is op_const
     int32_t op_const;
-    uint64_t n;
-    uint32_t S;
-    uint32_t cap_mask;    // dictionary capacity - 1 (power of two)
-    DictEntry* dict;
-    uint32_t* ctrl;
-    uint64_t bar_base;    // grid barriers this scratch buffer has passed before this launch
-    uint32_t claims_cap;  // dictionary claims one block can make per chunk (shared-memory list)
-    uint64_t timeout_ns;
+    uint32_t S;            // chunk size (semantic)
+    uint64_t n;            // updates of this call
+    uint64_t flat_base;    // first slot of this sketch in every round's flat slot range (multiple of 32)
+    DictEntry* dict;       // this sketch's chunk dictionary
+    uint32_t cap_mask;     // its capacity - 1 (power of two)
+    uint32_t pad;
 };
+
+struct BatchArgs {
+    const SketchRun* runs;  // device table of n_runs sketches, sorted by flat_base; nullptr: `one`
+    SketchRun one;
+    uint32_t n_runs;
+    uint32_t claims_cap;    // dictionary claims one block can make per round (shared-memory list)
+    uint64_t flat_len;      // slots per round: sum of S rounded up to a multiple of 32
+    uint64_t n_rounds;      // max over sketches of ceil(n / S)
+    uint32_t* ctrl;         // error word + barrier counter
+    uint64_t bar_base;      // grid barriers the counter has passed before this launch
+    uint64_t timeout_ns;
+    int32_t may_ins;        // some update of the launch may be an insertion
+    int32_t may_del;        // ... a deletion
+};
+
+inline uint64_t round_up32(uint64_t x) { return (x + 31) & ~31ull; }
 
 struct SeqArgs {
     SketchDesc s;
@@ -44,11 +60,16 @@ constexpr int kChunkBlock = 512;
 constexpr int kSeqBlock = 256;
 constexpr int kQueryBlock = 256;
 constexpr uint64_t kBarrierTimeoutNs = 2000000000ull;  // 2 s per wait
+constexpr int kMaxClaimSmem = 96 * 1024;               // dynamic shared memory for the claim list
 
-// Chunked update: one cooperative persistent launch for the whole call; 2 grid barriers per chunk.
-cudaError_t launch_chunk_update(const ChunkArgs& a, int grid, cudaStream_t st);
+// Chunked update: one cooperative persistent launch per call (one sketch or a batch of sketches
+// sharing d); 2 grid barriers per round.
+cudaError_t launch_batch_update(const BatchArgs& a, uint32_t d, int grid, cudaStream_t st);
 int chunk_update_blocks_per_sm(uint32_t d);
-uint32_t chunk_claims_cap(uint32_t S, int grid);
+uint32_t chunk_claims_cap(uint64_t flat_len, int grid);
+// Single sketch: a batch of one.
+cudaError_t launch_chunk_update(const SketchRun& one, uint32_t* ctrl, uint64_t bar_base, uint32_t claims_cap,
+                                int grid, cudaStream_t st);
 // One-at-a-time update (S = 1).
 cudaError_t launch_seq_update(const SeqArgs& a, cudaStream_t st, int smem_limit);
 // Point queries.

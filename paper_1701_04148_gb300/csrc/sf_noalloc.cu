@@ -79,29 +79,28 @@ extern "C" sf_status sf_update_batch_noalloc(const sf_params* p, uint32_t* fat_d
     if (cudaMemsetAsync(scratch, 0, kNoAllocCtrlBytes + (uint64_t)cap * sizeof(sfk::DictEntry), stream) != cudaSuccess)
         return SF_ERR_CUDA;
 
-    sfk::ChunkArgs a{};
-    a.s.A = slim_dev;
-    a.s.B = fat_dev;
-    a.s.d = p->d;
-    a.s.w = p->w;
-    a.s.z = p->z;
-    a.s.key_bytes = p->key_bytes;
+    sfk::SketchRun one{};
+    one.s.A = slim_dev;
+    one.s.B = fat_dev;
+    one.s.d = p->d;
+    one.s.w = p->w;
+    one.s.z = p->z;
+    one.s.key_bytes = p->key_bytes;
     uint64_t seed = p->seed;
-    for (uint32_t i = 0; i < SF_MAX_D; ++i) a.s.rs[i] = i < p->d ? splitmix64_step(&seed) : 0;
-    a.s.idx_table = nullptr;
-    a.s.n_ids = 0;
-    a.keys = (const uint8_t*)keys_dev;
-    a.ops = ops_dev;
-    a.op_const = 1;
-    a.n = n;
-    a.S = p->chunk;
-    a.cap_mask = cap - 1u;
-    a.dict = (sfk::DictEntry*)((uint8_t*)scratch + kNoAllocCtrlBytes);
-    a.ctrl = (uint32_t*)scratch;
-    a.bar_base = 0;  // the barrier counter was just zeroed
-    a.claims_cap = sfk::chunk_claims_cap(p->chunk, grid);
-    a.timeout_ns = sfk::kBarrierTimeoutNs;
-    if (sfk::launch_chunk_update(a, grid, stream) != cudaSuccess) return SF_ERR_CUDA;
+    for (uint32_t i = 0; i < SF_MAX_D; ++i) one.s.rs[i] = i < p->d ? splitmix64_step(&seed) : 0;
+    one.s.idx_table = nullptr;
+    one.s.n_ids = 0;
+    one.keys = (const uint8_t*)keys_dev;
+    one.ops = ops_dev;
+    one.op_const = 1;
+    one.S = p->chunk;
+    one.n = n;
+    one.dict = (sfk::DictEntry*)((uint8_t*)scratch + kNoAllocCtrlBytes);
+    one.cap_mask = cap - 1u;
+    // the barrier counter was just zeroed, so this launch starts from barrier 0
+    if (sfk::launch_chunk_update(one, (uint32_t*)scratch, 0, sfk::chunk_claims_cap(sfk::round_up32(p->chunk), grid),
+                                 grid, stream) != cudaSuccess)
+        return SF_ERR_CUDA;
     if (err_dev && cudaMemcpyAsync(err_dev, scratch, sizeof(uint32_t), cudaMemcpyDeviceToDevice, stream) != cudaSuccess)
         return SF_ERR_CUDA;
     return SF_OK;

@@ -107,7 +107,7 @@ __device__ __forceinline__ void clear_entry(DictEntry* ep) {
 }
 
 // One lane's update of the current warp-iteration, loaded and hashed (independent of the
-// sketch state, so the next chunk's first iteration can be prepared before the barrier).
+// sketch state, so the next round's first iteration can be prepared before the barrier).
 template <int D>
 struct LaneWork {
     Key k;
@@ -116,24 +116,25 @@ struct LaneWork {
     uint32_t h[D], f[D];
 };
 
+// Lane `lane` of the warp-iteration starting at update `first` of sketch R (len updates valid
+// from `first` on, at most 32 used).
 template <int D>
-__device__ __forceinline__ void prepare(const ChunkArgs& a, uint64_t base, uint64_t len, uint64_t j, uint32_t lane,
-                                        uint64_t total_bytes, uint4* stage, LaneWork<D>& L) {
-    const SketchDesc& s = a.s;
+__device__ __forceinline__ void prepare(const SketchRun& R, uint32_t* ctrl, uint64_t first, uint64_t len,
+                                        uint32_t lane, uint4* stage, LaneWork<D>& L) {
+    const SketchDesc& s = R.s;
     const uint32_t kb = s.key_bytes;
-    const uint64_t rel = j + lane;
+    const uint32_t nvalid = (uint32_t)(len < 32 ? len : 32);
     L.k = Key{0ull, 0ull};
     L.op = 0;
     L.probe = 0;
     if (kb != 4 && kb != 8)
-        L.k = load_key_staged(a.keys, total_bytes, base + j, (uint32_t)((len - j) < 32 ? (len - j) : 32), kb, lane,
-                              stage);
-    else if (rel < len)
-        L.k = load_key(a.keys, base + rel, kb);
-    if (rel < len) {
-        L.op = a.ops ? (int)a.ops[base + rel] : a.op_const;
+        L.k = load_key_staged(R.keys, R.n * kb, first, nvalid, kb, lane, stage);
+    else if (lane < nvalid)
+        L.k = load_key(R.keys, first + lane, kb);
+    if (lane < nvalid) {
+        L.op = R.ops ? (int)R.ops[first + lane] : R.op_const;
         if (L.op != 0 && !key_indices<D>(s, L.k, L.h, L.f, &L.probe)) {
-            atomicOr(a.ctrl + kCtrlErr, kErrBadKey);
+            atomicOr(ctrl + kCtrlErr, kErrBadKey);
             L.op = 0;
         }
     }
@@ -142,8 +143,9 @@ __device__ __forceinline__ void prepare(const ChunkArgs& a, uint64_t base, uint6
 // Phase 1 for one warp-iteration: warp aggregation, Fat RED, dictionary claim/lookup and counts.
 // Returns the dictionary slot this lane claimed, or kNoSlot.
 template <int D>
-__device__ __forceinline__ uint32_t phase1(const ChunkArgs& a, const LaneWork<D>& L, uint32_t lane) {
-    const SketchDesc& s = a.s;
+__device__ __forceinline__ uint32_t phase1(const SketchRun& R, uint32_t* ctrl, const LaneWork<D>& L,
+                                           uint32_t lane) {
+    const SketchDesc& s = R.s;
     const unsigned act = __ballot_sync(kFull, L.op != 0);
     if (act == 0u) return kNoSlot;
     const unsigned ins = __ballot_sync(kFull, L.op > 0);
@@ -164,11 +166,11 @@ __device__ __forceinline__ uint32_t phase1(const ChunkArgs& a, const LaneWork<D>
         for (int i = 0; i < D; ++i) av[i] = __ldcg(slim_ptr(s, i, L.h[i]));
     }
     const unsigned long long tag = L.k.x1 | kKeyTag;
-    uint32_t slot = L.probe & a.cap_mask;
+    uint32_t slot = L.probe & R.cap_mask;
     bool found = false, claimed = false;
-    for (uint32_t p = 0; p <= a.cap_mask; ++p) {
+    for (uint32_t p = 0; p <= R.cap_mask; ++p) {
         unsigned long long ol, oh;
-        cas128(&a.dict[slot].key_lo, 0ull, 0ull, L.k.x0, tag, ol, oh);
+        cas128(&R.dict[slot].key_lo, 0ull, 0ull, L.k.x0, tag, ol, oh);
         if (oh == 0ull) {
             found = claimed = true;
             break;
@@ -177,23 +179,23 @@ __device__ __forceinline__ uint32_t phase1(const ChunkArgs& a, const LaneWork<D>
             found = true;
             break;
         }
-        slot = (slot + 1u) & a.cap_mask;
+        slot = (slot + 1u) & R.cap_mask;
     }
     if (!found) {
-        atomicOr(a.ctrl + kCtrlErr, kErrDictFull);
+        atomicOr(ctrl + kCtrlErr, kErrDictFull);
         return kNoSlot;
     }
     if (ci) {
-        atomicAdd(&a.dict[slot].c_ins, ci);
+        atomicAdd(&R.dict[slot].c_ins, ci);
         uint32_t m = 0xFFFFFFFFu, mask = 0u;
 #pragma unroll
         for (int i = 0; i < D; ++i) m = min(m, av[i]);
 #pragma unroll
         for (int i = 0; i < D; ++i) mask |= (av[i] == m ? 1u : 0u) << i;
         // every leader of this key stores the same chunk-start minimum and minimal-row mask
-        asm volatile("st.global.cg.v2.u32 [%0], {%1, %2};" ::"l"(&a.dict[slot].m), "r"(m), "r"(mask) : "memory");
+        asm volatile("st.global.cg.v2.u32 [%0], {%1, %2};" ::"l"(&R.dict[slot].m), "r"(m), "r"(mask) : "memory");
     }
-    if (cd) atomicAdd(&a.dict[slot].c_del, cd);
+    if (cd) atomicAdd(&R.dict[slot].c_del, cd);
     return claimed ? slot : kNoSlot;
 }
 
@@ -203,10 +205,9 @@ __device__ __forceinline__ uint32_t phase1(const ChunkArgs& a, const LaneWork<D>
 //          A0_i == m are known from the mask; when c_ins == 1 every other row has A0_i >= m + 1 >= T.
 //   clamp: atomicMin of the bucket maximum for every row of a deleted key.
 template <int D>
-__device__ __forceinline__ void phase2_key(const ChunkArgs& a, DictEntry* ep, const uint32_t* h, const uint32_t* f,
-                                           uint32_t c_ins, uint32_t c_del, uint32_t m, uint32_t mask,
-                                           const uint32_t* Fv) {
-    const SketchDesc& s = a.s;
+__device__ __forceinline__ void phase2_key(const SketchDesc& s, uint32_t* ctrl, DictEntry* ep, const uint32_t* h,
+                                           const uint32_t* f, uint32_t c_ins, uint32_t c_del, uint32_t m,
+                                           uint32_t mask, const uint32_t* Fv) {
     if (c_ins) {
         uint32_t F = 0xFFFFFFFFu;
 #pragma unroll
@@ -223,50 +224,66 @@ __device__ __forceinline__ void phase2_key(const ChunkArgs& a, DictEntry* ep, co
         bool under = false;
 #pragma unroll
         for (int i = 0; i < D; ++i) atomicMin(slim_ptr(s, i, h[i]), bucket_max_cg(s, i, h[i], f[i], &under));
-        if (under) atomicOr(a.ctrl + kCtrlErr, kErrUnderflow);
+        if (under) atomicOr(ctrl + kCtrlErr, kErrUnderflow);
     }
     clear_entry(ep);
 }
 
+// The sketch whose flat slot range holds slot j (runs sorted by flat_base).
+__device__ __forceinline__ uint32_t find_run(const SketchRun* runs, uint32_t n_runs, uint64_t j) {
+    uint32_t lo = 0, hi = n_runs;  // invariant: runs[lo].flat_base <= j, answer in [lo, hi)
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(&runs[mid].flat_base) <= j) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
 template <int D>
-__global__ void __launch_bounds__(kChunkBlock, 1) chunk_update_kernel(const ChunkArgs a) {
-    extern __shared__ uint32_t s_claims[];  // dictionary slots this block claimed in the chunk
+__global__ void __launch_bounds__(kChunkBlock, 1) chunk_update_kernel(const __grid_constant__ BatchArgs a) {
+    extern __shared__ uint2 s_claims[];  // (sketch, dictionary slot) claimed by this block in the round
     __shared__ uint32_t s_nclaims;
     __shared__ uint4 s_stage[kChunkBlock / 32][32];
-    const SketchDesc& s = a.s;
+    const SketchRun* runs = a.runs ? a.runs : &a.one;
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    const uint64_t nchunks = (a.n + a.S - 1) / a.S;
-    const uint64_t total_bytes = a.n * s.key_bytes;
-    // one warp-iteration per chunk: each lane claims at most one slot and keeps it in registers
-    const bool single = 32ull * nwarps >= (uint64_t)a.S;
-    const bool may_ins = a.ops != nullptr || a.op_const > 0;
+    // one warp-iteration per round: each lane claims at most one slot and keeps it in registers
+    const bool single = 32ull * nwarps >= a.flat_len;
     uint4* stage = s_stage[threadIdx.x >> 5];
     unsigned long long target = (a.bar_base + 1ull) * gridDim.x;
+    // the first flat slot of this warp lies in the same sketch every round
+    const uint32_t k_first = gwarp * 32 < a.flat_len ? find_run(runs, a.n_runs, gwarp * 32) : 0u;
 
     LaneWork<D> pre;
     bool have_pre = false;
-    for (uint64_t c = 0; c < nchunks; ++c) {
-        const uint64_t base = c * (uint64_t)a.S;
-        const uint64_t len = min((uint64_t)a.S, a.n - base);
+    for (uint64_t r = 0; r < a.n_rounds; ++r) {
         if (!single) {
             if (threadIdx.x == 0) s_nclaims = 0u;
             __syncthreads();
         }
 
-        // ---- phase 1: Fat updates and the chunk dictionary --------------------------------
-        uint32_t my_slot = kNoSlot;
+        // ---- phase 1: Fat updates and the chunk dictionaries --------------------------------
+        uint32_t my_slot = kNoSlot, my_k = 0;
         uint32_t my_h[D], my_f[D];
-        for (uint64_t j = gwarp * 32; j < len; j += nwarps * 32) {
+        for (uint64_t j = gwarp * 32; j < a.flat_len; j += nwarps * 32) {
+            const uint32_t k = (j == gwarp * 32) ? k_first : find_run(runs, a.n_runs, j);
+            const SketchRun& R = runs[k];
+            const uint64_t o = j - R.flat_base;          // slot offset inside the sketch's chunk
+            const uint64_t base = r * (uint64_t)R.S;     // first update of this round's chunk
+            if (base >= R.n || o >= R.S) continue;       // sketch finished, or padding slots
+            const uint64_t len = min((uint64_t)R.S, R.n - base);
+            if (o >= len) continue;
             LaneWork<D> L;
             if (have_pre && j == gwarp * 32) L = pre;
-            else prepare<D>(a, base, len, j, lane, total_bytes, stage, L);
+            else prepare<D>(R, a.ctrl, base + o, len - o, lane, stage, L);
             have_pre = false;
-            const uint32_t slot = phase1<D>(a, L, lane);
+            const uint32_t slot = phase1<D>(R, a.ctrl, L, lane);
             if (slot != kNoSlot) {
                 if (single) {
                     my_slot = slot;
+                    my_k = k;
 #pragma unroll
                     for (int i = 0; i < D; ++i) {
                         my_h[i] = L.h[i];
@@ -274,51 +291,60 @@ __global__ void __launch_bounds__(kChunkBlock, 1) chunk_update_kernel(const Chun
                     }
                 } else {
                     const uint32_t q = atomicAdd(&s_nclaims, 1u);
-                    if (q < a.claims_cap) s_claims[q] = slot;
+                    if (q < a.claims_cap) s_claims[q] = make_uint2(k, slot);
                     else atomicOr(a.ctrl + kCtrlErr, kErrDictFull);
                 }
             }
         }
+        have_pre = false;
         if (!grid_barrier(a.ctrl, target, a.timeout_ns)) return;
         target += gridDim.x;
 
         // ---- phase 2: Slim raises and clamps, once per distinct key (by its claimer) --------
         if (single) {
             if (my_slot != kNoSlot) {
-                DictEntry* ep = a.dict + my_slot;
+                const SketchRun& R = runs[my_k];
+                DictEntry* ep = R.dict + my_slot;
                 const uint4 cn = __ldcg(reinterpret_cast<const uint4*>(ep) + 1);  // c_ins, c_del, m, mask
                 uint32_t Fv[D];
-                if (may_ins) {
+                if (a.may_ins) {
 #pragma unroll
-                    for (int i = 0; i < D; ++i) Fv[i] = __ldcg(fat_ptr(s, i, my_h[i], my_f[i]));
+                    for (int i = 0; i < D; ++i) Fv[i] = __ldcg(fat_ptr(R.s, i, my_h[i], my_f[i]));
                 }
-                phase2_key<D>(a, ep, my_h, my_f, cn.x, cn.y, cn.z, cn.w, Fv);
+                phase2_key<D>(R.s, a.ctrl, ep, my_h, my_f, cn.x, cn.y, cn.z, cn.w, Fv);
             }
         } else {
             const uint32_t nclaims = min(s_nclaims, a.claims_cap);
             for (uint32_t q = threadIdx.x; q < nclaims; q += blockDim.x) {
-                DictEntry* ep = a.dict + s_claims[q];
+                const uint2 cl = s_claims[q];
+                const SketchRun& R = runs[cl.x];
+                DictEntry* ep = R.dict + cl.y;
                 unsigned long long k0, k1, c01, c23;
                 ld_entry(ep, k0, k1, c01, c23);
-                const Key k{k0, k1 & ~kKeyTag};
+                const Key key{k0, k1 & ~kKeyTag};
                 uint32_t h[D], f[D], probe, Fv[D];
-                key_indices<D>(s, k, h, f, &probe);
+                key_indices<D>(R.s, key, h, f, &probe);
                 const uint32_t c_ins = (uint32_t)c01;
                 if (c_ins) {
 #pragma unroll
-                    for (int i = 0; i < D; ++i) Fv[i] = __ldcg(fat_ptr(s, i, h[i], f[i]));
+                    for (int i = 0; i < D; ++i) Fv[i] = __ldcg(fat_ptr(R.s, i, h[i], f[i]));
                 }
-                phase2_key<D>(a, ep, h, f, c_ins, (uint32_t)(c01 >> 32), (uint32_t)c23, (uint32_t)(c23 >> 32), Fv);
+                phase2_key<D>(R.s, a.ctrl, ep, h, f, c_ins, (uint32_t)(c01 >> 32), (uint32_t)c23,
+                              (uint32_t)(c23 >> 32), Fv);
             }
         }
 
-        // prepare the next chunk's first iteration (keys, ops, hashes) while others finish
-        if (c + 1 < nchunks) {
-            const uint64_t base1 = base + a.S;
-            const uint64_t len1 = min((uint64_t)a.S, a.n - base1);
-            if (gwarp * 32 < len1) {
-                prepare<D>(a, base1, len1, gwarp * 32, lane, total_bytes, stage, pre);
-                have_pre = true;
+        // prepare the next round's first iteration (keys, ops, hashes) while others finish
+        if (r + 1 < a.n_rounds && gwarp * 32 < a.flat_len) {
+            const SketchRun& R = runs[k_first];
+            const uint64_t o = gwarp * 32 - R.flat_base;
+            const uint64_t base = (r + 1) * (uint64_t)R.S;
+            if (base < R.n && o < R.S) {
+                const uint64_t len = min((uint64_t)R.S, R.n - base);
+                if (o < len) {
+                    prepare<D>(R, a.ctrl, base + o, len - o, lane, stage, pre);
+                    have_pre = true;
+                }
             }
         }
         if (!grid_barrier(a.ctrl, target, a.timeout_ns)) return;
@@ -399,8 +425,8 @@ __global__ void __launch_bounds__(kSeqBlock) seq_update_kernel(const SeqArgs a) 
 }  // namespace
 
 template <int D>
-static cudaError_t launch_chunk_d(const ChunkArgs& a, int grid, cudaStream_t st) {
-    const size_t smem = (size_t)a.claims_cap * sizeof(uint32_t);
+static cudaError_t launch_batch_d(const BatchArgs& a, int grid, cudaStream_t st) {
+    const size_t smem = (size_t)a.claims_cap * sizeof(uint2);
     cudaError_t e = cudaFuncSetAttribute(chunk_update_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -420,10 +446,11 @@ static cudaError_t launch_chunk_d(const ChunkArgs& a, int grid, cudaStream_t st)
 template <int D>
 static int blocks_per_sm_d() {
     int nb = 0;
-    // the claim list of the largest chunk fits in 64 KiB of dynamic shared memory per block
-    if (cudaFuncSetAttribute(chunk_update_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536) !=
+    // the claim list of the largest round fits in 96 KiB of dynamic shared memory per block
+    if (cudaFuncSetAttribute(chunk_update_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxClaimSmem) !=
             cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, chunk_update_kernel<D>, kChunkBlock, 65536) != cudaSuccess)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, chunk_update_kernel<D>, kChunkBlock, kMaxClaimSmem) !=
+            cudaSuccess)
         return 0;
     return nb;
 }
@@ -442,25 +469,44 @@ int chunk_update_blocks_per_sm(uint32_t d) {
     }
 }
 
-uint32_t chunk_claims_cap(uint32_t S, int grid) {
-    // a block claims at most one slot per update it handles: iterations per chunk x block size
+uint32_t chunk_claims_cap(uint64_t flat_len, int grid) {
+    // a block claims at most one slot per update it handles: iterations per round x block size
     const uint64_t per_iter = (uint64_t)grid * kChunkBlock;
-    const uint64_t iters = (S + per_iter - 1) / per_iter;
+    const uint64_t iters = (flat_len + per_iter - 1) / per_iter;
     return (uint32_t)(iters * kChunkBlock);
 }
 
-cudaError_t launch_chunk_update(const ChunkArgs& a, int grid, cudaStream_t st) {
-    switch (a.s.d) {
-        case 1: return launch_chunk_d<1>(a, grid, st);
-        case 2: return launch_chunk_d<2>(a, grid, st);
-        case 3: return launch_chunk_d<3>(a, grid, st);
-        case 4: return launch_chunk_d<4>(a, grid, st);
-        case 5: return launch_chunk_d<5>(a, grid, st);
-        case 6: return launch_chunk_d<6>(a, grid, st);
-        case 7: return launch_chunk_d<7>(a, grid, st);
-        case 8: return launch_chunk_d<8>(a, grid, st);
+cudaError_t launch_batch_update(const BatchArgs& a, uint32_t d, int grid, cudaStream_t st) {
+    if ((uint64_t)a.claims_cap * sizeof(uint2) > (uint64_t)kMaxClaimSmem) return cudaErrorInvalidValue;
+    switch (d) {
+        case 1: return launch_batch_d<1>(a, grid, st);
+        case 2: return launch_batch_d<2>(a, grid, st);
+        case 3: return launch_batch_d<3>(a, grid, st);
+        case 4: return launch_batch_d<4>(a, grid, st);
+        case 5: return launch_batch_d<5>(a, grid, st);
+        case 6: return launch_batch_d<6>(a, grid, st);
+        case 7: return launch_batch_d<7>(a, grid, st);
+        case 8: return launch_batch_d<8>(a, grid, st);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_chunk_update(const SketchRun& one, uint32_t* ctrl, uint64_t bar_base, uint32_t claims_cap,
+                                int grid, cudaStream_t st) {
+    BatchArgs a{};
+    a.runs = nullptr;
+    a.one = one;
+    a.one.flat_base = 0;
+    a.n_runs = 1;
+    a.claims_cap = claims_cap;
+    a.flat_len = round_up32(one.S);
+    a.n_rounds = (one.n + one.S - 1) / one.S;
+    a.ctrl = ctrl;
+    a.bar_base = bar_base;
+    a.timeout_ns = kBarrierTimeoutNs;
+    a.may_ins = one.ops != nullptr || one.op_const > 0;
+    a.may_del = one.ops != nullptr || one.op_const < 0;
+    return launch_batch_update(a, one.s.d, grid, st);
 }
 
 cudaError_t launch_seq_update(const SeqArgs& a, cudaStream_t st, int smem_limit) {

@@ -1,0 +1,92 @@
+"""Batched many-sketch update (one persistent cooperative launch, CUDA graph replay): every
+sketch's Fat and Slim equal those of one sf_update_batch call per sketch (bit for bit), and
+sampled sketches equal the CPU oracle's chunked semantics with the same chunk size."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def _plan(n_sketches, seed, w_log2=(6.0, 11.0), n_log10=(2.0, 4.7)):
+    return wl.many_sketch_plan(n_sketches, seed, w_log2=w_log2, n_log10=n_log10)
+
+
+def _streams(plan, device="cuda"):
+    out = []
+    for p in plan:
+        st, ids = wl.mixed_stream(p["n"], p["distinct"], p["s"], 0.1, 4, seed=p["seed"], device=device)
+        out.append((st, ids))
+    return out
+
+
+def _chunk_for(p, rounds):
+    return max(2, -(-p["n"] // rounds))
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_batch_equals_per_sketch_calls(sf, graph):
+    import torch
+    plan = _plan(37, seed=5)
+    streams = _streams(plan)
+    for rounds in (3, 40):
+        batch_sk = [sf.Sketch(4, p["w"], 16, 4, p["seed"], _chunk_for(p, rounds)) for p in plan]
+        plain_sk = [sf.Sketch(4, p["w"], 16, 4, p["seed"], _chunk_for(p, rounds)) for p in plan]
+        b = sf.Batch(len(plan), graph=graph)
+        halves = []
+        for (st, _) in streams:
+            h = st.keys.shape[0] // 2
+            halves.append(((st.keys[:h], st.ops[:h]), (st.keys[h:], st.ops[h:])))
+        for part in (0, 1):  # two calls in a row (graph replay when the shape repeats)
+            b.update([(sk, halves[i][part][0], halves[i][part][1]) for i, sk in enumerate(batch_sk)])
+            for i, sk in enumerate(plain_sk):
+                sk.update(halves[i][part][0], halves[i][part][1])
+        b.sync()
+        for sk in plain_sk:
+            sk.sync()
+        for i in range(len(plan)):
+            assert torch.equal(batch_sk[i].fat, plain_sk[i].fat), (rounds, i)
+            assert torch.equal(batch_sk[i].slim, plain_sk[i].slim), (rounds, i)
+        info = b.info()
+        if graph:
+            assert info["graph_captures"] >= 1 and info["graph_launches"] == 2
+        b.close()
+
+
+def test_batch_matches_oracle_on_sampled_sketches(sf):
+    import torch
+    plan = _plan(24, seed=9, w_log2=(7.0, 12.0), n_log10=(3.0, 5.0))
+    streams = _streams(plan)
+    sks = [sf.Sketch(4, p["w"], 16, 4, p["seed"], _chunk_for(p, 17)) for p in plan]
+    b = sf.Batch(len(plan))
+    b.update([(sk, st.keys, st.ops) for sk, (st, _) in zip(sks, streams)])
+    b.sync()
+    for i in (0, 5, 11, 23):
+        p = plan[i]
+        st, ids = streams[i]
+        o = oracle.Sketch(4, p["w"], 16, 4, p["seed"])
+        o.update(st.keys.cpu().numpy(), st.ops.cpu().numpy(), S=_chunk_for(p, 17))
+        assert np.array_equal(sks[i].fat.cpu().numpy().view(np.uint32).reshape(o.B.shape), o.B)
+        assert np.array_equal(sks[i].slim.cpu().numpy().view(np.uint32).reshape(o.A.shape), o.A)
+
+
+def test_batch_with_13_byte_keys_and_empty_items(sf):
+    import torch
+    sks, items, refs = [], [], []
+    for i, (n, w) in enumerate([(5000, 100), (0, 64), (777, 33), (40_000, 1000)]):
+        ins, dels, flows = wl.flows_with_deletes(max(n, 1), 300, 1.1, 0.1, seed=70 + i, device="cuda")
+        ins = ins[:n]
+        sk = sf.Sketch(4, w, 16, 13, 100 + i, 1000)
+        ref = sf.Sketch(4, w, 16, 13, 100 + i, 1000)
+        sks.append(sk)
+        refs.append(ref)
+        items.append((sk, ins, None))
+        ref.insert(ins)
+    b = sf.Batch(8)
+    b.update(items)
+    b.sync()
+    for sk, ref in zip(sks, refs):
+        ref.sync()
+        assert torch.equal(sk.fat, ref.fat) and torch.equal(sk.slim, ref.slim)
