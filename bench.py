@@ -192,6 +192,10 @@ def main():
     ap.add_argument("--ref-queries", type=int, default=20_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", choices=["all", "flows", "batch", "serve"], default="all",
+                    help="all: the flows line with the batched and serving results embedded")
+    ap.add_argument("--batch-sketches", type=int, default=1024)
+    ap.add_argument("--serve-seconds", type=float, default=8.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_env()
@@ -221,6 +225,38 @@ def main():
     L = sf.load()
     stream = torch.cuda.current_stream(dev)
 
+    ctx = dict(world=world, rank=rank, local=local, dist=dist, dev=dev, L=L, stream=stream)
+    line = None
+    if args.workload in ("all", "flows"):
+        line = run_flows(args, ctx)
+    if args.workload in ("all", "batch"):
+        b = run_batch(args, ctx)
+        if line is None:
+            line = b
+        elif rank == 0:
+            line["batched"] = b
+    if args.workload in ("all", "serve"):
+        v = run_serve(args, ctx)
+        if line is None:
+            line = v
+        elif rank == 0:
+            line["serving"] = v
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_flows(args, ctx):
+    """The 5-tuple workload (the headline): Zipf sweep, inserts, deletes, Slim export, queries."""
+    import numpy as np
+    import torch
+
+    import paper_1701_04148_gb300 as sf
+    import workloads as wl
+    world, rank, local, dist = ctx["world"], ctx["rank"], ctx["local"], ctx["dist"]
+    dev, L, stream = ctx["dev"], ctx["L"], ctx["stream"]
     # ---- inputs, resident in HBM ----------------------------------------------------------
     inputs = []
     for idx, s in enumerate(SWEEP):
@@ -402,10 +438,247 @@ def main():
             "cpu_baseline": cpu, "bit_exact_sample": exact, "e2e": e2e,
             "gpu_launches": args.steps * launches_per_step, "clocks": clk,
         }
-        print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
-    return 0
+        return line
+    return None
+
+
+def run_batch(args, ctx):
+    """Many-node update: --batch-sketches sketches (Slim widths log-uniform 2^10..2^16, Fat 16x, d=4,
+    stream lengths log-uniform 10^4..10^7 u32 keys, Zipf s ~ U(0.5, 1.5), 90/10 insert/delete)
+    in one persistent graph-captured launch per step (batched) versus one sf_update_batch call
+    per sketch (plain), same chunk sizes (picked by the autotuner), same GPU."""
+    import torch
+
+    import paper_1701_04148_gb300 as sf
+    from paper_1701_04148_gb300 import autotune
+    import workloads as wl
+    world, rank, dist, dev, stream = ctx["world"], ctx["rank"], ctx["dist"], ctx["dev"], ctx["stream"]
+    plan = wl.many_sketch_plan(args.batch_sketches, seed=3 + 1000 * rank)
+    t0 = time.time()
+    streams = []
+    for p in plan:
+        st, _ = wl.mixed_stream(p["n"], p["distinct"], p["s"], 0.1, 4, seed=p["seed"], device=dev)
+        streams.append((st.keys, st.ops))
+    torch.cuda.synchronize()
+    gen_s = time.time() - t0
+    ns = [p["n"] for p in plan]
+    ws = [p["w"] for p in plan]
+    total = sum(ns)
+
+    def make(chunks):
+        return [sf.Sketch(4, w, 16, 4, p["seed"], S, stream=stream) for w, p, S in zip(ws, plan, chunks)]
+
+    cache = os.path.join(ROOT, "paper_1701_04148_gb300", "_build", "autotune_cache.json")
+    key = autotune.shape_key(ws, ns, 4, 16, 4) + "-" + torch.cuda.get_device_name(dev).replace(" ", "_")
+    t1 = time.time()
+    tuned = autotune.tune(make, streams, ns, candidates=(64, 256, 1024), cache_path=cache, cache_key=key)
+    tune_s = time.time() - t1
+    chunks = tuned["chunks"]
+    bsk, psk = make(chunks), make(chunks)
+    batch = sf.Batch(len(bsk), graph=True, stream=stream, max_round_slots=tuned["round_slots"])
+    items = [(sk, k, o) for sk, (k, o) in zip(bsk, streams)]
+
+    def batched_step():
+        for sk in bsk:
+            sk.reset()
+        batch.update(items)
+
+    def plain_step():
+        for sk, (k, o) in zip(psk, streams):
+            sk.reset()
+            sk.update(k, o)
+
+    for _ in range(args.warmup):
+        batched_step()
+    plain_step()
+    torch.cuda.synchronize()
+
+    def timed(fn, k):
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / k
+        if dist is not None:
+            t = torch.tensor([ms], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    tb = timed(batched_step, args.steps)
+    tp = timed(plain_step, max(1, args.steps // 2))
+    st_b = batch.sync_status()
+    exact = all(torch.equal(a.fat, b.fat) and torch.equal(a.slim, b.slim) for a, b in zip(bsk, psk))
+    info = batch.info()
+    out = {"workload": "batched-many-sketch", "metric": "M updates/s", "sketches": len(plan),
+           "updates_per_step": total, "value": round(world * total / (tb / 1e3) / 1e6, 2), "unit": "M updates/s",
+           "plain_value": round(world * total / (tp / 1e3) / 1e6, 2), "batched_vs_plain_speedup": round(tp / tb, 3),
+           "ms_per_step_batched": round(tb, 3), "ms_per_step_plain": round(tp, 3), "rounds": tuned["rounds"],
+           "autotune_updates_per_s": tuned["trials"], "graph": info, "status": st_b,
+           "batched_equals_plain": bool(exact), "gen_s": round(gen_s, 1), "autotune_s": round(tune_s, 1),
+           "n_gpus": world, "scaling": "weak"}
+    batch.close()
+    for sk in bsk + psk:
+        sk.close()
+    del streams
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_serve(args, ctx):
+    """Collector serving loop: 4,096 resident Slims (widths log-uniform 2^10..2^18, d=4) filled from
+    u32 Zipf streams, a 40 GB admission budget, open-loop Poisson query batches of round(2^U(0,16))
+    keys (80 % Zipf-hot present, 20 % uniform absent) at ~70 % of the measured capacity, with
+    replace-in-place uploads during the run; then a 1 GB budget where admission binds; and the plain
+    path (one sf_query_batch per request, copies included) for comparison."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    import paper_1701_04148_gb300 as sf
+    import workloads as wl
+    rank, dev, stream = ctx["rank"], ctx["dev"], ctx["stream"]
+    n_sk = 4096
+    g = torch.Generator().manual_seed(4 + 1000 * rank)
+    widths = [wl.log_uniform_int(10.0, 18.0, g) for _ in range(n_sk)]
+    # fill the Slims with the batched update, 256 sketches at a time, keep only the exported Slims
+    slims, hdrs, idtabs = [], [], []
+    t0 = time.time()
+    for g0 in range(0, n_sk, 256):
+        grp = list(range(g0, min(n_sk, g0 + 256)))
+        sks, items = [], []
+        for k in grp:
+            w = widths[k]
+            st, ids = wl.mixed_stream(2 * w, 4 * w, 1.0, 0.1, 4, seed=50_000 + k + 1000 * rank, device=dev)
+            sk = sf.Sketch(4, w, 16, 4, 7 + k, 2048, stream=stream)
+            sks.append(sk)
+            items.append((sk, st.keys, st.ops))
+            idtabs.append(ids.view(torch.int32).reshape(-1).cpu().numpy())
+        b = sf.Batch(len(sks), stream=stream)
+        b.update(items)
+        b.sync()
+        for sk in sks:
+            slim, hdr = sk.export_slim()
+            slims.append(slim)
+            hdrs.append(hdr)
+            sk.close()
+        b.close()
+        del sks, items
+    torch.cuda.synchronize()
+    build_s = time.time() - t0
+    slim_bytes = sum(4 * 4 * w for w in widths)
+
+    # request pool: 1024 pre-generated host key arrays
+    rng = np.random.default_rng(11 + rank)
+    pool = []
+    for q in range(1024):
+        k = int(rng.integers(n_sk))
+        n = int(round(2 ** rng.uniform(0, 16)))
+        ids = idtabs[k]
+        n_hot = int(round(0.8 * n))
+        ranks = np.minimum(rng.zipf(1.1, n_hot) - 1, len(ids) - 1)
+        keys = np.concatenate([ids[ranks], rng.integers(0, 2**31, n - n_hot).astype(np.int32)])
+        rng.shuffle(keys)
+        pool.append((k, np.ascontiguousarray(keys), np.zeros(n, np.uint32)))
+    mean_keys = float(np.mean([len(p[1]) for p in pool]))
+
+    col = sf.Collector(budget_bytes=40 << 30, max_sketches=n_sk, n_streams=4, max_batch_keys=1 << 17,
+                       max_batch_reqs=512, max_wait_us=50)
+    for k in range(n_sk):
+        assert col.upload(k, slims[k], hdrs[k]) == sf.SF_OK
+
+    # capacity: closed loop, as fast as one client thread submits
+    def burst(n_req):
+        ts = []
+        t = time.perf_counter()
+        for q in range(n_req):
+            k, keys, out = pool[q % len(pool)]
+            ts.append(col.submit(k, keys, out))
+        for x in ts:
+            col.wait(x)
+        return time.perf_counter() - t
+
+    burst(256)
+    col.stats(reset=True)
+    dt = burst(4096)
+    cap = col.stats(reset=True)
+    cap_keys_s = cap["keys"] / dt
+
+    # open loop at ~70 % of capacity, Poisson arrivals, replace-in-place uploads at 20/s
+    rate = 0.7 * cap_keys_s / mean_keys
+    gaps = wl.poisson_gaps(int(rate * args.serve_seconds) + 1, rate, torch.Generator().manual_seed(5)).numpy()
+    arrivals = np.cumsum(gaps)
+    stop = threading.Event()
+    uploads = [0]
+
+    def uploader():
+        r2 = np.random.default_rng(99)
+        while not stop.is_set():
+            k = int(r2.integers(n_sk))
+            if col.upload(k, slims[k], hdrs[k]) == sf.SF_OK:
+                uploads[0] += 1
+            time.sleep(0.05)
+
+    th = threading.Thread(target=uploader)
+    th.start()
+    tickets = []
+    t_start = time.perf_counter()
+    for q, at in enumerate(arrivals):
+        while True:
+            now = time.perf_counter() - t_start
+            if now >= at:
+                break
+            if at - now > 2e-4:
+                time.sleep((at - now) - 1e-4)
+        k, keys, out = pool[q % len(pool)]
+        tickets.append(col.submit(k, keys, out))
+    for x in tickets:
+        col.wait(x)
+    stop.set()
+    th.join()
+    open_stats = col.stats(reset=True)
+    offered = len(arrivals) / (time.perf_counter() - t_start)
+
+    # check a sample of answers against sf_query_batch (alone) on the same Slims
+    exact = True
+    for q in range(0, len(pool), 97):
+        k, keys, _ = pool[q]
+        out = np.zeros(len(keys), np.uint32)
+        col.wait(col.submit(k, keys, out))
+        want = sf.query(slims[k], hdrs[k], torch.from_numpy(keys).to(dev)).cpu().numpy().view(np.uint32)
+        exact &= bool(np.array_equal(out, want))
+    col.close()
+
+    # plain path: one sf_query_batch per request with its own copies, one at a time
+    t = time.perf_counter()
+    nk = 0
+    for q in range(1024):
+        k, keys, _ = pool[q]
+        kd = torch.from_numpy(keys).to(dev, non_blocking=True)
+        res = sf.query(slims[k], hdrs[k], kd).cpu()
+        nk += len(keys)
+    plain_keys_s = nk / (time.perf_counter() - t)
+
+    # tight budget: admission binds
+    tight = sf.Collector(budget_bytes=1 << 30, max_sketches=n_sk, n_streams=1)
+    admitted = sum(1 for k in range(n_sk) if tight.upload(k, slims[k], hdrs[k]) == sf.SF_OK)
+    tst = tight.stats()
+    tight.close()
+    return {"workload": "collector-serving", "sketches": n_sk, "slim_bytes": slim_bytes,
+            "p50_ms": round(open_stats["p50_us"] / 1e3, 4), "p99_ms": round(open_stats["p99_us"] / 1e3, 4),
+            "mean_ms": round(open_stats["mean_us"] / 1e3, 4), "queries_per_s": round(open_stats["qps"], 1),
+            "offered_requests_per_s": round(offered, 1), "load_fraction_of_capacity": 0.7,
+            "capacity_keys_per_s": round(cap_keys_s, 1), "capacity_p99_ms": round(cap["p99_us"] / 1e3, 4),
+            "plain_keys_per_s": round(plain_keys_s, 1), "served_vs_plain_speedup": round(cap_keys_s / plain_keys_s, 2),
+            "uploads_during_run": uploads[0], "mean_keys_per_request": round(mean_keys, 1),
+            "answers_equal_alone": exact, "budget_1GB": {"admitted": admitted, "rejected": tst["rejected_uploads"]},
+            "budget_40GB_admitted": n_sk, "build_s": round(build_s, 1)}
 
 
 if __name__ == "__main__":

@@ -191,21 +191,25 @@ typedef struct sf_batch_item {
 
 #define SF_BATCH_GRAPH 1u     /* capture the launch in a CUDA graph and replay it               */
 
-/* Device scratch of a batch of up to max_sketches items: control words + the run table. */
-sf_status sf_batch_required_bytes(uint32_t max_sketches, uint64_t *scratch_bytes);
+/*
+ * Device scratch of a batch of up to max_sketches items whose chunk sizes, each rounded up to a
+ * multiple of 32, sum to at most max_round_slots: control words, the run table and the per-block
+ * lists of dictionary claims of one round.
+ */
+sf_status sf_batch_required_bytes(uint32_t max_sketches, uint64_t max_round_slots, uint64_t *scratch_bytes);
 
 /*
  * Creates a batch bound to cuda_stream and to caller-owned scratch_dev (sf_batch_required_bytes,
  * 16-byte aligned; zeroed here).  The batch allocates a pinned host staging table and a private
  * capture stream, no device memory.  flags: SF_BATCH_GRAPH or 0 (direct launches).
  */
-sf_status sf_batch_create(uint32_t max_sketches, void *scratch_dev, void *cuda_stream, uint32_t flags,
-                          sf_batch **out);
+sf_status sf_batch_create(uint32_t max_sketches, uint64_t max_round_slots, void *scratch_dev, void *cuda_stream,
+                          uint32_t flags, sf_batch **out);
 
 /*
  * Enqueues items[0..n_items) as one launch on the batch's stream.  The sketches' own pending work
- * must be ordered before it (same stream, or synchronised).  A call whose per-round slot count
- * exceeds what one launch can hold returns SF_ERR_INVALID.  Device errors: sf_batch_sync.
+ * must be ordered before it (same stream, or synchronised).  A call whose chunk sizes (rounded up
+ * to multiples of 32) sum above max_round_slots returns SF_ERR_INVALID.  Device errors: sf_batch_sync.
  */
 sf_status sf_batch_update(sf_batch *b, uint32_t n_items, const sf_batch_item *items);
 
@@ -218,6 +222,77 @@ sf_status sf_batch_info(const sf_batch *b, uint32_t *graph_launches, uint32_t *g
                         uint64_t *rounds_last);
 
 sf_status sf_batch_destroy(sf_batch *b);
+
+/*
+ * ---- Collector serving loop --------------------------------------------------------------------
+ * The remote collector receives Slim-subsketches from many monitoring nodes and answers point
+ * queries from them (Abstract; Sec. 1.1; GPU batching and multi-stream pipelining, Sec. 4.2).
+ * sfc_* keeps uploaded Slims resident in a caller-provided device arena -- the memory budget --
+ * and serves queries with continuous batching: a worker thread packs the requests that have
+ * arrived into one multi-request query launch per batch, keeps up to n_streams batches in flight
+ * on separate CUDA streams, and admits new requests into the next batch as soon as a stream frees,
+ * while earlier batches still run.  Each query binds to the sketch version current at submit
+ * (uploads replace in place; an old version's memory returns to the arena when its last query
+ * finishes).  Answers equal sf_query_batch on the same Slim.
+ */
+typedef struct sfc sfc;
+
+typedef struct sfc_config {
+    void *arena_dev;          /* device memory holding resident Slims: the admission budget      */
+    uint64_t arena_bytes;
+    void *staging_dev;        /* device memory for in-flight batches (sfc_required_staging_bytes) */
+    uint64_t staging_bytes;
+    uint32_t max_sketches;    /* sketch ids are 0 .. max_sketches-1                              */
+    uint32_t n_streams;       /* batches in flight at once, 1..16                                */
+    uint32_t max_batch_keys;  /* keys per launched batch; one request may not exceed it          */
+    uint32_t max_batch_reqs;  /* requests per launched batch                                     */
+    uint32_t max_wait_us;     /* a partly filled batch waits at most this long for more requests */
+} sfc_config;
+
+typedef struct sfc_stats {
+    uint64_t requests, keys, batches, uploads, rejected_uploads, evictions;
+    double p50_us, p99_us, mean_us, max_us;  /* submit -> answers in the caller's host buffer   */
+    double qps;                               /* keys answered per second over the stats window  */
+    uint64_t arena_used_bytes;
+} sfc_stats;
+
+/* Device staging bytes for a configuration (keys, answers and request tables of n_streams batches). */
+sf_status sfc_required_staging_bytes(const sfc_config *c, uint64_t *bytes);
+
+/* Starts a collector (and its worker thread) on the current device.  Host staging is pinned
+ * memory allocated here; device memory is only the caller's arena and staging. */
+sf_status sfc_create(const sfc_config *c, sfc **out);
+
+/*
+ * Upload (or replace) the Slim of sketch_id: d*w counters at `counters` (device or host pointer,
+ * e.g. from sf_export_slim) with its header.  Returns after the copy; queries submitted afterwards
+ * see the new version.  SF_ERR_BUDGET: the arena cannot hold it now (nothing changes);
+ * SF_ERR_VERSION: not a Slim header of this library.
+ */
+sf_status sfc_upload(sfc *c, uint32_t sketch_id, const uint32_t *counters, const sf_slim_header *hdr);
+
+/* Drops sketch_id; its memory returns to the arena once queries bound to it finish. */
+sf_status sfc_evict(sfc *c, uint32_t sketch_id);
+
+/*
+ * Submits n point queries (host keys of the sketch's key_bytes) against the current version of
+ * sketch_id; answers are written to out_host (n uint32) before the ticket completes.  Both
+ * buffers must stay valid until then.  n <= max_batch_keys.
+ */
+sf_status sfc_query_submit(sfc *c, uint32_t sketch_id, const void *keys_host, uint64_t n, uint32_t *out_host,
+                           uint64_t *ticket);
+
+/* SF_OK when the ticket finished (the ticket is then released), SF_PENDING otherwise. */
+sf_status sfc_poll(sfc *c, uint64_t ticket);
+
+/* Blocks until the ticket finished; then like sfc_poll. */
+sf_status sfc_wait(sfc *c, uint64_t ticket);
+
+/* Statistics since creation or the last reset (reset != 0 clears them after reading). */
+sf_status sfc_stats_get(sfc *c, sfc_stats *out, int reset);
+
+/* Stops the worker after finishing submitted requests; frees host resources. */
+sf_status sfc_destroy(sfc *c);
 
 /*
  * Update without any caller scratch -- the paper has no counterpart; this is a deployment aid.

@@ -57,6 +57,20 @@ class SlimView(ctypes.Structure):
                 ("n_index_keys", ctypes.c_uint32)]
 
 
+class CollectorConfig(ctypes.Structure):
+    _fields_ = [("arena_dev", ctypes.c_void_p), ("arena_bytes", ctypes.c_uint64), ("staging_dev", ctypes.c_void_p),
+                ("staging_bytes", ctypes.c_uint64), ("max_sketches", ctypes.c_uint32), ("n_streams", ctypes.c_uint32),
+                ("max_batch_keys", ctypes.c_uint32), ("max_batch_reqs", ctypes.c_uint32),
+                ("max_wait_us", ctypes.c_uint32)]
+
+
+class CollectorStats(ctypes.Structure):
+    _fields_ = [("requests", ctypes.c_uint64), ("keys", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+                ("uploads", ctypes.c_uint64), ("rejected_uploads", ctypes.c_uint64), ("evictions", ctypes.c_uint64),
+                ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double), ("mean_us", ctypes.c_double),
+                ("max_us", ctypes.c_double), ("qps", ctypes.c_double), ("arena_used_bytes", ctypes.c_uint64)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -77,14 +91,24 @@ _SIGS = {
     "sf_query_batch": (ctypes.c_int32, [ctypes.POINTER(SlimView), ctypes.c_void_p, ctypes.c_uint64,
                                         ctypes.c_void_p, ctypes.c_void_p]),
     "sf_sync": (ctypes.c_int32, [ctypes.c_void_p]),
-    "sf_batch_required_bytes": (ctypes.c_int32, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64)]),
-    "sf_batch_create": (ctypes.c_int32, [ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32,
-                                         ctypes.POINTER(ctypes.c_void_p)]),
+    "sf_batch_required_bytes": (ctypes.c_int32, [ctypes.c_uint32, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]),
+    "sf_batch_create": (ctypes.c_int32, [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_uint32, ctypes.POINTER(ctypes.c_void_p)]),
     "sf_batch_update": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]),
     "sf_batch_sync": (ctypes.c_int32, [ctypes.c_void_p]),
     "sf_batch_info": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32),
                                        ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint64)]),
     "sf_batch_destroy": (ctypes.c_int32, [ctypes.c_void_p]),
+    "sfc_required_staging_bytes": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
+    "sfc_create": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "sfc_upload": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.POINTER(SlimHeader)]),
+    "sfc_evict": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint32]),
+    "sfc_query_submit": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint64,
+                                          ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
+    "sfc_poll": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64]),
+    "sfc_wait": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64]),
+    "sfc_stats_get": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "sfc_destroy": (ctypes.c_int32, [ctypes.c_void_p]),
     "sf_update_batch_noalloc": (ctypes.c_int32, [ctypes.POINTER(Params), ctypes.c_void_p, ctypes.c_void_p,
                                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
                                                  ctypes.c_void_p]),
@@ -282,16 +306,17 @@ SF_BATCH_GRAPH = 1
 class Batch:
     """Many sketches updated by one persistent launch (sf_batch_*), CUDA graph replay by default."""
 
-    def __init__(self, max_sketches: int, graph: bool = True, stream=None, device=None):
+    def __init__(self, max_sketches: int, graph: bool = True, stream=None, device=None,
+                 max_round_slots: int = 1 << 22):
         torch = _torch()
         L = load()
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         xb = ctypes.c_uint64()
-        check(L.sf_batch_required_bytes(max_sketches, ctypes.byref(xb)), "sf_batch_required_bytes")
+        check(L.sf_batch_required_bytes(max_sketches, max_round_slots, ctypes.byref(xb)), "sf_batch_required_bytes")
         self.scratch = torch.empty(xb.value // 4 + 4, dtype=torch.int32, device=self.device)
         h = ctypes.c_void_p()
-        check(L.sf_batch_create(max_sketches, self.scratch.data_ptr(), _stream_handle(self.stream),
+        check(L.sf_batch_create(max_sketches, max_round_slots, self.scratch.data_ptr(), _stream_handle(self.stream),
                                 SF_BATCH_GRAPH if graph else 0, ctypes.byref(h)), "sf_batch_create")
         self.handle = h
         self.max_sketches = max_sketches
@@ -359,3 +384,73 @@ def update_batch_noalloc(params: Params, fat, slim, keys, ops=None, err=None, st
     check(load().sf_update_batch_noalloc(ctypes.byref(params), _dev_ptr(fat, "fat"), _dev_ptr(slim, "slim"),
                                          _dev_ptr(keys, "keys") if n else 0, _dev_ptr(ops, "ops"), n,
                                          _dev_ptr(err, "err"), _stream_handle(stream)), "sf_update_batch_noalloc")
+
+
+
+class Collector:
+    """The collector serving loop (sfc_*): resident Slims in a device arena of `budget_bytes`,
+    continuous batching of host-side point-query requests over `n_streams` CUDA streams."""
+
+    def __init__(self, budget_bytes: int, max_sketches: int, n_streams: int = 4, max_batch_keys: int = 1 << 17,
+                 max_batch_reqs: int = 1024, max_wait_us: int = 50, device=None):
+        torch = _torch()
+        L = load()
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.arena = torch.empty(max(budget_bytes, 256) // 4, dtype=torch.int32, device=self.device)
+        cfg = CollectorConfig(self.arena.data_ptr(), self.arena.numel() * 4, 0, 0, max_sketches, n_streams,
+                              max_batch_keys, max_batch_reqs, max_wait_us)
+        need = ctypes.c_uint64()
+        check(L.sfc_required_staging_bytes(ctypes.byref(cfg), ctypes.byref(need)), "sfc_required_staging_bytes")
+        self.staging = torch.empty(need.value // 4 + 64, dtype=torch.int32, device=self.device)
+        cfg.staging_dev = self.staging.data_ptr()
+        cfg.staging_bytes = self.staging.numel() * 4
+        self.cfg = cfg
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            check(L.sfc_create(ctypes.byref(cfg), ctypes.byref(h)), "sfc_create")
+        self.handle = h
+        self._live = {}
+
+    def upload(self, sketch_id: int, counters, hdr: SlimHeader) -> int:
+        """Returns the status (SF_OK, SF_ERR_BUDGET, ...); counters: device or host tensor."""
+        ptr = counters.data_ptr()
+        return load().sfc_upload(self.handle, sketch_id, ptr, ctypes.byref(hdr))
+
+    def evict(self, sketch_id: int) -> int:
+        return load().sfc_evict(self.handle, sketch_id)
+
+    def submit(self, sketch_id: int, keys_np, out_np) -> int:
+        """keys_np: contiguous numpy array of packed keys (host); out_np: uint32 numpy array."""
+        t = ctypes.c_uint64()
+        n = len(out_np)
+        check(load().sfc_query_submit(self.handle, sketch_id, keys_np.ctypes.data if n else None, n,
+                                      out_np.ctypes.data if n else None, ctypes.byref(t)), "sfc_query_submit")
+        self._live[t.value] = (keys_np, out_np)
+        return t.value
+
+    def poll(self, ticket: int) -> int:
+        st = load().sfc_poll(self.handle, ticket)
+        if st != SF_PENDING:
+            self._live.pop(ticket, None)
+        return st
+
+    def wait(self, ticket: int) -> int:
+        st = load().sfc_wait(self.handle, ticket)
+        self._live.pop(ticket, None)
+        return st
+
+    def stats(self, reset: bool = False) -> dict:
+        s = CollectorStats()
+        check(load().sfc_stats_get(self.handle, ctypes.byref(s), 1 if reset else 0), "sfc_stats_get")
+        return {f: getattr(s, f) for f, _ in CollectorStats._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().sfc_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

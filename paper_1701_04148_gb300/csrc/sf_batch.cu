@@ -12,6 +12,8 @@
 
 struct sf_batch {
     uint32_t max_sketches;
+    uint64_t max_round_slots;
+    uint2* claims_dev;
     uint8_t* scratch;
     uint32_t* ctrl;
     sfk::SketchRun* table_dev;
@@ -39,7 +41,8 @@ constexpr uint64_t kBatchCtrlBytes = 256;
 
 bool same_shape(const sfk::BatchArgs& x, const sfk::BatchArgs& y) {
     return x.n_runs == y.n_runs && x.claims_cap == y.claims_cap && x.flat_len == y.flat_len &&
-           x.n_rounds == y.n_rounds && x.may_ins == y.may_ins && x.may_del == y.may_del && x.runs == y.runs;
+           x.n_rounds == y.n_rounds && x.may_ins == y.may_ins && x.may_del == y.may_del && x.runs == y.runs &&
+           x.claims_global == y.claims_global;
 }
 
 cudaError_t enqueue(sf_batch* b, const sfk::BatchArgs& a, uint32_t d, int grid, size_t table_bytes,
@@ -55,27 +58,33 @@ cudaError_t enqueue(sf_batch* b, const sfk::BatchArgs& a, uint32_t d, int grid, 
 
 extern "C" {
 
-sf_status sf_batch_required_bytes(uint32_t max_sketches, uint64_t* scratch_bytes) {
-    if (max_sketches == 0 || !scratch_bytes) return SF_ERR_INVALID;
-    *scratch_bytes = kBatchCtrlBytes + (uint64_t)max_sketches * sizeof(sfk::SketchRun);
+static uint64_t table_bytes_of(uint32_t max_sketches) {
+    return ((uint64_t)max_sketches * sizeof(sfk::SketchRun) + 255) / 256 * 256;
+}
+
+sf_status sf_batch_required_bytes(uint32_t max_sketches, uint64_t max_round_slots, uint64_t* scratch_bytes) {
+    if (max_sketches == 0 || max_round_slots == 0 || !scratch_bytes) return SF_ERR_INVALID;
+    *scratch_bytes = kBatchCtrlBytes + table_bytes_of(max_sketches) + sfk::claims_global_bytes(max_round_slots);
     return SF_OK;
 }
 
-sf_status sf_batch_create(uint32_t max_sketches, void* scratch_dev, void* cuda_stream, uint32_t flags,
-                          sf_batch** out) {
-    if (!out || !scratch_dev || max_sketches == 0 || ((uintptr_t)scratch_dev & 15u) || (flags & ~SF_BATCH_GRAPH))
+sf_status sf_batch_create(uint32_t max_sketches, uint64_t max_round_slots, void* scratch_dev, void* cuda_stream,
+                          uint32_t flags, sf_batch** out) {
+    if (!out || !scratch_dev || max_sketches == 0 || max_round_slots == 0 || ((uintptr_t)scratch_dev & 15u) ||
+        (flags & ~SF_BATCH_GRAPH))
         return SF_ERR_INVALID;
     *out = nullptr;
     sf_batch* b = new (std::nothrow) sf_batch();
     if (!b) return SF_ERR_OOM;
     b->max_sketches = max_sketches;
+    b->max_round_slots = max_round_slots;
+    b->claims_dev = (uint2*)((uint8_t*)scratch_dev + kBatchCtrlBytes + table_bytes_of(max_sketches));
     b->scratch = (uint8_t*)scratch_dev;
     b->ctrl = (uint32_t*)scratch_dev;
     b->table_dev = (sfk::SketchRun*)((uint8_t*)scratch_dev + kBatchCtrlBytes);
     b->stream = (cudaStream_t)cuda_stream;
     b->flags = flags;
-    uint64_t xb = 0;
-    sf_batch_required_bytes(max_sketches, &xb);
+    uint64_t xb = kBatchCtrlBytes + table_bytes_of(max_sketches);  // claim lists need no zeroing
     if (cudaGetDevice(&b->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess ||
         cudaHostAlloc((void**)&b->staging, (size_t)max_sketches * sizeof(sfk::SketchRun), cudaHostAllocDefault) !=
@@ -155,7 +164,9 @@ sf_status sf_batch_update(sf_batch* b, uint32_t n_items, const sf_batch_item* it
     a.timeout_ns = sfk::kBarrierTimeoutNs;
     a.may_ins = may_ins;
     a.may_del = may_del;
-    if ((uint64_t)a.claims_cap * sizeof(uint2) > (uint64_t)sfk::kMaxClaimSmem) return SF_ERR_INVALID;
+    if (flat > b->max_round_slots) return SF_ERR_INVALID;
+    // claim lists in shared memory when they fit, else in the batch scratch
+    a.claims_global = ((uint64_t)a.claims_cap * sizeof(uint2) > (uint64_t)sfk::kMaxClaimSmem) ? b->claims_dev : nullptr;
     const size_t table_bytes = (size_t)n_items * sizeof(sfk::SketchRun);
     b->rounds_last = rounds;
 

@@ -35,6 +35,7 @@ struct BatchArgs {
     uint64_t timeout_ns;
     int32_t may_ins;        // some update of the launch may be an insertion
     int32_t may_del;        // ... a deletion
+    uint2* claims_global;   // per-block claim lists in global memory (claims_cap each), or nullptr: shared memory
 };
 
 inline uint64_t round_up32(uint64_t x) { return (x + 31) & ~31ull; }
@@ -56,6 +57,24 @@ struct QueryArgs {
     uint32_t* out;
 };
 
+// One request of a multi-request query launch (the collector's batches): its keys are
+// key_bytes-wide at keys + key_off, its answers go to out[out_off .. out_off + n).
+struct QueryReq {
+    const uint32_t* A;     // Slim counters of the sketch version the request is bound to
+    uint32_t d, w, key_bytes, n;
+    uint64_t rs[kMaxD];
+    uint64_t key_off;      // byte offset of the request's keys in the batch key buffer
+    uint64_t out_off;      // first answer slot (prefix of the n of earlier requests)
+};
+
+struct MultiQueryArgs {
+    const QueryReq* reqs;  // device, sorted by out_off
+    uint32_t n_reqs;
+    uint64_t total;        // sum of n
+    const uint8_t* keys;
+    uint32_t* out;
+};
+
 constexpr int kChunkBlock = 512;
 constexpr int kSeqBlock = 256;
 constexpr int kQueryBlock = 256;
@@ -65,6 +84,10 @@ constexpr int kMaxClaimSmem = 96 * 1024;               // dynamic shared memory 
 // Chunked update: one cooperative persistent launch per call (one sketch or a batch of sketches
 // sharing d); 2 grid barriers per round.
 cudaError_t launch_batch_update(const BatchArgs& a, uint32_t d, int grid, cudaStream_t st);
+// Global claim-list bytes a launch over rounds of up to max_round_slots slots may need (any grid <= 1024 blocks).
+inline uint64_t claims_global_bytes(uint64_t max_round_slots) {
+    return (max_round_slots + 1024ull * kChunkBlock) * 8ull;
+}
 int chunk_update_blocks_per_sm(uint32_t d);
 uint32_t chunk_claims_cap(uint64_t flat_len, int grid);
 // Single sketch: a batch of one.
@@ -74,6 +97,7 @@ cudaError_t launch_chunk_update(const SketchRun& one, uint32_t* ctrl, uint64_t b
 cudaError_t launch_seq_update(const SeqArgs& a, cudaStream_t st, int smem_limit);
 // Point queries.
 cudaError_t launch_query(const QueryArgs& a, int num_sms, cudaStream_t st);
+cudaError_t launch_multi_query(const MultiQueryArgs& a, int num_sms, cudaStream_t st);
 
 // Dictionary capacity: a power of two >= 4 S (load factor <= 1/4 keeps probe chains short).
 inline uint32_t dict_capacity(uint32_t S) {

@@ -25,7 +25,47 @@ __global__ void __launch_bounds__(kQueryBlock) query_kernel(const QueryArgs q) {
     }
 }
 
+// Many requests against many Slims in one launch: thread t answers global slot t, finding its
+// request by binary search over the out_off prefix (requests stay warp-coherent mostly).
+__global__ void __launch_bounds__(kQueryBlock) multi_query_kernel(const MultiQueryArgs q) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < q.total; t += stride) {
+        uint32_t lo = 0, hi = q.n_reqs;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (__ldg(&q.reqs[mid].out_off) <= t) lo = mid;
+            else hi = mid;
+        }
+        const QueryReq& r = q.reqs[lo];
+        SketchDesc s{};
+        s.A = const_cast<uint32_t*>(r.A);
+        s.d = r.d;
+        s.w = r.w;
+        s.z = 0xFFFFFFFFu;
+        s.key_bytes = r.key_bytes;
+#pragma unroll
+        for (int i = 0; i < kMaxD; ++i) s.rs[i] = r.rs[i];
+        const Key k = load_key(q.keys + r.key_off, t - r.out_off, r.key_bytes);
+        uint32_t h[kMaxD], f[kMaxD], probe;
+        key_indices<0>(s, k, h, f, &probe);
+        uint32_t m = 0xFFFFFFFFu;
+#pragma unroll
+        for (int i = 0; i < kMaxD; ++i)
+            if (i < (int)s.d) m = min(m, __ldg(s.A + (uint64_t)i * s.w + h[i]));
+        q.out[t] = m;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_multi_query(const MultiQueryArgs& a, int num_sms, cudaStream_t st) {
+    if (a.total == 0) return cudaSuccess;
+    const uint64_t want = (a.total + kQueryBlock - 1) / kQueryBlock;
+    const uint64_t cap = (uint64_t)num_sms * 8;
+    const unsigned grid = (unsigned)(want < cap ? want : cap);
+    multi_query_kernel<<<grid, kQueryBlock, 0, st>>>(a);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_query(const QueryArgs& a, int num_sms, cudaStream_t st) {
     if (a.n == 0) return cudaSuccess;

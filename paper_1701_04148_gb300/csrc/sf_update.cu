@@ -242,7 +242,8 @@ __device__ __forceinline__ uint32_t find_run(const SketchRun* runs, uint32_t n_r
 
 template <int D>
 __global__ void __launch_bounds__(kChunkBlock, 1) chunk_update_kernel(const __grid_constant__ BatchArgs a) {
-    extern __shared__ uint2 s_claims[];  // (sketch, dictionary slot) claimed by this block in the round
+    extern __shared__ uint2 s_claims_smem[];  // (sketch, dictionary slot) claimed by this block in the round
+    uint2* s_claims = a.claims_global ? a.claims_global + (uint64_t)blockIdx.x * a.claims_cap : s_claims_smem;
     __shared__ uint32_t s_nclaims;
     __shared__ uint4 s_stage[kChunkBlock / 32][32];
     const SketchRun* runs = a.runs ? a.runs : &a.one;
@@ -426,7 +427,7 @@ __global__ void __launch_bounds__(kSeqBlock) seq_update_kernel(const SeqArgs a) 
 
 template <int D>
 static cudaError_t launch_batch_d(const BatchArgs& a, int grid, cudaStream_t st) {
-    const size_t smem = (size_t)a.claims_cap * sizeof(uint2);
+    const size_t smem = a.claims_global ? 0 : (size_t)a.claims_cap * sizeof(uint2);
     cudaError_t e = cudaFuncSetAttribute(chunk_update_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -477,7 +478,7 @@ uint32_t chunk_claims_cap(uint64_t flat_len, int grid) {
 }
 
 cudaError_t launch_batch_update(const BatchArgs& a, uint32_t d, int grid, cudaStream_t st) {
-    if ((uint64_t)a.claims_cap * sizeof(uint2) > (uint64_t)kMaxClaimSmem) return cudaErrorInvalidValue;
+    if (!a.claims_global && (uint64_t)a.claims_cap * sizeof(uint2) > (uint64_t)kMaxClaimSmem) return cudaErrorInvalidValue;
     switch (d) {
         case 1: return launch_batch_d<1>(a, grid, st);
         case 2: return launch_batch_d<2>(a, grid, st);

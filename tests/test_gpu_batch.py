@@ -90,3 +90,27 @@ def test_batch_with_13_byte_keys_and_empty_items(sf):
     for sk, ref in zip(sks, refs):
         ref.sync()
         assert torch.equal(sk.fat, ref.fat) and torch.equal(sk.slim, ref.slim)
+
+
+def test_batch_with_claim_lists_in_global_memory(sf):
+    """Rounds of 2.4 M slots overflow the shared-memory claim lists: the launch keeps them in the
+    batch scratch instead; results still equal one call per sketch."""
+    import torch
+    sks, refs, items = [], [], []
+    for i in range(8):
+        st, _ = wl.mixed_stream(600_000, 200_000, 0.8, 0.1, 4, seed=300 + i, device="cuda")
+        sk = sf.Sketch(4, 1 << 14, 16, 4, 500 + i, 300_000)
+        ref = sf.Sketch(4, 1 << 14, 16, 4, 500 + i, 300_000)
+        ref.update(st.keys, st.ops)
+        sks.append(sk)
+        refs.append(ref)
+        items.append((sk, st.keys, st.ops))
+    b = sf.Batch(8, max_round_slots=8 * 300_032)
+    b.update(items)
+    b.sync()
+    for sk, ref in zip(sks, refs):
+        ref.sync()
+        assert torch.equal(sk.fat, ref.fat) and torch.equal(sk.slim, ref.slim)
+    with pytest.raises(sf.SFError):
+        small = sf.Batch(8, max_round_slots=1000)
+        small.update(items)
