@@ -9,7 +9,7 @@
 
 #include <cuda_runtime.h>
 
-#include "../../include/sf.h"
+#include "sf.h"
 #include "sf_internal.h"
 
 #include "sf_handle.h"

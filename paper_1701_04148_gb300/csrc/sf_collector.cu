@@ -20,7 +20,7 @@
 #include <unordered_map>
 #include <vector>
 
-#include "../../include/sf.h"
+#include "sf.h"
 #include "sf_internal.h"
 
 namespace {

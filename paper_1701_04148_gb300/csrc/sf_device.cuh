@@ -166,10 +166,43 @@ __device__ __forceinline__ void cas128(unsigned long long* addr, unsigned long l
         : "memory");
 }
 
+// Split-phase grid barrier: grid_arrive announces this block (after all its threads' prior memory
+// operations), grid_wait blocks until every block of the grid has arrived `target` times in total.
+// Work placed between the two overlaps the wait.
+__device__ __forceinline__ void grid_arrive(uint32_t* ctrl) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        red_release_gpu_add_u64(reinterpret_cast<unsigned long long*>(ctrl + kCtrlBarrier64), 1ull);
+    }
+}
+
+__device__ __forceinline__ bool grid_wait(uint32_t* ctrl, unsigned long long target, uint64_t timeout_ns) {
+    __shared__ int s_ok_w;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned long long* cnt = reinterpret_cast<const unsigned long long*>(ctrl + kCtrlBarrier64);
+        if (ld_acquire_gpu_u64(cnt) < target) {
+            const uint64_t t0 = globaltimer_ns();
+            while (ld_acquire_gpu_u64(cnt) < target) {
+                if (globaltimer_ns() - t0 > timeout_ns) {
+                    atomicOr(ctrl + kCtrlErr, kErrTimeout);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        s_ok_w = ok;
+    }
+    __syncthreads();
+    return s_ok_w != 0;
+}
+
 // Grid-wide barrier for a co-resident (cooperatively launched) grid.  Every block adds 1 to a
 // monotonic 64-bit counter and waits until it reaches `target` = (barriers passed so far + 1) *
 // gridDim.x.  The wait is bounded: after timeout_ns the block latches kErrTimeout and returns
-// false, and so does every block that finds the flag set, so the kernel leaves instead of hanging.
+// false, so the kernel leaves instead of hanging.
 __device__ __forceinline__ bool grid_barrier(uint32_t* ctrl, unsigned long long target, uint64_t timeout_ns) {
     __shared__ int s_ok;
     __syncthreads();
@@ -182,6 +215,8 @@ __device__ __forceinline__ bool grid_barrier(uint32_t* ctrl, unsigned long long 
             const uint64_t t0 = globaltimer_ns();
             while (ld_acquire_gpu_u64(cnt) < target) {
                 if (globaltimer_ns() - t0 > timeout_ns) {
+                    // give up: latch the error and leave; every other block then misses this one at
+                    // its next barrier, times out the same way, and the launch ends
                     atomicOr(ctrl + kCtrlErr, kErrTimeout);
                     ok = 0;
                     break;
@@ -189,7 +224,6 @@ __device__ __forceinline__ bool grid_barrier(uint32_t* ctrl, unsigned long long 
             }
         }
         __threadfence();
-        if (ld_acquire_gpu(ctrl + kCtrlErr) & kErrTimeout) ok = 0;
         s_ok = ok;
     }
     __syncthreads();

@@ -4,7 +4,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
-#include "../../include/sf.h"
+#include "sf.h"
 #include "sf_internal.h"
 
 struct sf_sketch {

@@ -99,9 +99,11 @@ cudaError_t launch_seq_update(const SeqArgs& a, cudaStream_t st, int smem_limit)
 cudaError_t launch_query(const QueryArgs& a, int num_sms, cudaStream_t st);
 cudaError_t launch_multi_query(const MultiQueryArgs& a, int num_sms, cudaStream_t st);
 
-// Dictionary capacity: a power of two >= 4 S (load factor <= 1/4 keeps probe chains short).
+// Dictionary capacity: a power of two >= 16 S.  Each probe of the open-addressing table is one
+// 128-bit CAS round trip and a chunk waits for its slowest key, so the longest probe chain
+// matters: at load 1/4 it reaches ~11 slots over 65,536 keys, at load 1/16 ~5.
 inline uint32_t dict_capacity(uint32_t S) {
-    uint64_t need = 4ull * (uint64_t)S;
+    uint64_t need = 16ull * (uint64_t)S;
     uint64_t cap = 64;
     while (cap < need) cap <<= 1;
     return (uint32_t)cap;

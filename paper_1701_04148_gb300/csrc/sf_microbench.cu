@@ -1,5 +1,5 @@
 // sf_microbench.cu -- roofline denominators measured on the device (no sketch arithmetic).
-#include "../../include/sf_bench.h"
+#include "sf_bench.h"
 #include "sf_internal.h"
 
 namespace sfk {

@@ -9,7 +9,7 @@
 // this library keeps until the process exits.
 #include <mutex>
 
-#include "../../include/sf.h"
+#include "sf.h"
 #include "sf_internal.h"
 
 namespace {
@@ -17,6 +17,16 @@ namespace {
 constexpr uint64_t kNoAllocCtrlBytes = 256;
 constexpr uint64_t kNoAllocScratchBytes =
     kNoAllocCtrlBytes + (uint64_t)(4u * SF_NOALLOC_MAX_CHUNK) * sizeof(sfk::DictEntry);  // 2 MiB + 256 B
+
+// Dictionary capacity inside the fixed array: a power of two >= 4 S (load factor <= 1/4).
+constexpr uint32_t noalloc_capacity(uint32_t S) {
+    uint32_t cap = 64;
+    while (cap < 4u * S) cap <<= 1;
+    return cap;
+}
+static_assert(kNoAllocCtrlBytes + (uint64_t)noalloc_capacity(SF_NOALLOC_MAX_CHUNK) * sizeof(sfk::DictEntry) <=
+                  kNoAllocScratchBytes,
+              "the largest dictionary must fit the fixed scratch array");
 
 // The shared scratch: control words (error bits, barrier counter) then the key dictionary.
 static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
@@ -75,7 +85,7 @@ extern "C" sf_status sf_update_batch_noalloc(const sf_params* p, uint32_t* fat_d
 
     // The array keeps whatever the previous call left: zero the control words and the dictionary
     // (a call that stopped early may leave claimed entries behind).
-    const uint32_t cap = sfk::dict_capacity(p->chunk);
+    const uint32_t cap = noalloc_capacity(p->chunk);
     if (cudaMemsetAsync(scratch, 0, kNoAllocCtrlBytes + (uint64_t)cap * sizeof(sfk::DictEntry), stream) != cudaSuccess)
         return SF_ERR_CUDA;
 

@@ -140,21 +140,50 @@ __device__ __forceinline__ void prepare(const SketchRun& R, uint32_t* ctrl, uint
     }
 }
 
-// Phase 1 for one warp-iteration: warp aggregation, Fat RED, dictionary claim/lookup and counts.
-// Returns the dictionary slot this lane claimed, or kNoSlot.
+// Warp aggregation: equal keys of one warp-iteration collapse onto their lowest lane (the warp
+// leader), which carries the group's insert and delete counts.
+struct WarpGroup {
+    bool leader;
+    uint32_t ci, cd;
+};
+
 template <int D>
-__device__ __forceinline__ uint32_t phase1(const SketchRun& R, uint32_t* ctrl, const LaneWork<D>& L,
-                                           uint32_t lane) {
-    const SketchDesc& s = R.s;
+__device__ __forceinline__ WarpGroup warp_group(const LaneWork<D>& L, uint32_t key_bytes, uint32_t lane) {
+    WarpGroup g{false, 0u, 0u};
     const unsigned act = __ballot_sync(kFull, L.op != 0);
-    if (act == 0u) return kNoSlot;
+    if (act == 0u) return g;
     const unsigned ins = __ballot_sync(kFull, L.op > 0);
     unsigned grp = __match_any_sync(kFull, L.k.x0);
-    if (s.key_bytes > 8) grp &= __match_any_sync(kFull, L.k.x1);
+    if (key_bytes > 8) grp &= __match_any_sync(kFull, L.k.x1);
     grp &= act;
-    if (L.op == 0 || lane != (uint32_t)(__ffs(grp) - 1)) return kNoSlot;
+    if (L.op != 0 && lane == (uint32_t)(__ffs(grp) - 1)) {
+        g.leader = true;
+        g.ci = __popc(grp & ins);
+        g.cd = __popc(grp & ~ins);
+    }
+    return g;
+}
 
-    const uint32_t ci = __popc(grp & ins), cd = __popc(grp & ~ins);
+// Block-level merge table: warp leaders of one block-iteration with equal keys merge onto one
+// owner, so a key hot across the block touches the Fat and the dictionary once per block.
+// Indexed by a 32-bit key fingerprint; keys are compared in full, and a fingerprint shared by
+// two different keys just leaves the second one unmerged.
+constexpr int kMergeSlots = 2 * kChunkBlock;
+struct MergeTable {
+    uint32_t tag[kMergeSlots];
+    uint32_t run[kMergeSlots];  // sketch of the key (keys of different sketches never merge)
+    uint32_t ci[kMergeSlots];
+    uint32_t cd[kMergeSlots];
+    ulonglong2 key[kMergeSlots];
+};
+
+// Global part of phase 1 for one (block- or warp-) leader: Fat RED of the net count, dictionary
+// claim/lookup (one 128-bit CAS per probe), counts, chunk-start Slim minimum.  Returns the slot
+// this thread claimed, or kNoSlot.
+template <int D>
+__device__ __forceinline__ uint32_t phase1_global(const SketchRun& R, uint32_t* ctrl, const LaneWork<D>& L,
+                                                  uint32_t ci, uint32_t cd) {
+    const SketchDesc& s = R.s;
     const int32_t net = (int32_t)ci - (int32_t)cd;
     if (net != 0) {
 #pragma unroll
@@ -257,43 +286,133 @@ __global__ void __launch_bounds__(kChunkBlock, 1) chunk_update_kernel(const __gr
     // the first flat slot of this warp lies in the same sketch every round
     const uint32_t k_first = gwarp * 32 < a.flat_len ? find_run(runs, a.n_runs, gwarp * 32) : 0u;
 
+    __shared__ MergeTable s_merge;
+    for (int i = threadIdx.x; i < kMergeSlots; i += blockDim.x) s_merge.tag[i] = 0u;
+    // every block runs the same number of warp-iterations per round (block merges need __syncthreads)
+    const uint64_t iters = (a.flat_len + 32 * nwarps - 1) / (32 * nwarps);
+
+    // The block merge pays three __syncthreads per warp-iteration; a block uses it only when its
+    // warps saw duplicate keys in the previous round (>= 1/16 of their updates).
+    __shared__ uint32_t s_act, s_lead;
+    __shared__ int s_use_merge;
+    if (threadIdx.x == 0) {
+        s_act = 0u;
+        s_lead = 0u;
+        s_use_merge = 1;
+    }
+
     LaneWork<D> pre;
     bool have_pre = false;
     for (uint64_t r = 0; r < a.n_rounds; ++r) {
-        if (!single) {
-            if (threadIdx.x == 0) s_nclaims = 0u;
-            __syncthreads();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (!single) s_nclaims = 0u;
+            if (r > 0) s_use_merge = (s_act > 0u) && (16u * (s_act - s_lead) >= s_act);
+            s_act = 0u;
+            s_lead = 0u;
         }
+        __syncthreads();
+        const bool use_merge = s_use_merge != 0;
 
         // ---- phase 1: Fat updates and the chunk dictionaries --------------------------------
         uint32_t my_slot = kNoSlot, my_k = 0;
         uint32_t my_h[D], my_f[D];
-        for (uint64_t j = gwarp * 32; j < a.flat_len; j += nwarps * 32) {
-            const uint32_t k = (j == gwarp * 32) ? k_first : find_run(runs, a.n_runs, j);
-            const SketchRun& R = runs[k];
-            const uint64_t o = j - R.flat_base;          // slot offset inside the sketch's chunk
-            const uint64_t base = r * (uint64_t)R.S;     // first update of this round's chunk
-            if (base >= R.n || o >= R.S) continue;       // sketch finished, or padding slots
-            const uint64_t len = min((uint64_t)R.S, R.n - base);
-            if (o >= len) continue;
+        for (uint64_t it = 0; it < iters; ++it) {
+            const uint64_t j = gwarp * 32 + it * nwarps * 32;
             LaneWork<D> L;
-            if (have_pre && j == gwarp * 32) L = pre;
-            else prepare<D>(R, a.ctrl, base + o, len - o, lane, stage, L);
-            have_pre = false;
-            const uint32_t slot = phase1<D>(R, a.ctrl, L, lane);
-            if (slot != kNoSlot) {
-                if (single) {
-                    my_slot = slot;
-                    my_k = k;
-#pragma unroll
-                    for (int i = 0; i < D; ++i) {
-                        my_h[i] = L.h[i];
-                        my_f[i] = L.f[i];
+            L.op = 0;
+            L.k = Key{0ull, 0ull};
+            L.probe = 0;
+            uint32_t k = 0;
+            bool live = false;
+            if (j < a.flat_len) {
+                k = (it == 0) ? k_first : find_run(runs, a.n_runs, j);
+                const SketchRun& R = runs[k];
+                const uint64_t o = j - R.flat_base;       // slot offset inside the sketch's chunk
+                const uint64_t base = r * (uint64_t)R.S;  // first update of this round's chunk
+                if (base < R.n && o < R.S) {
+                    const uint64_t len = min((uint64_t)R.S, R.n - base);
+                    if (o < len) {
+                        live = true;
+                        if (have_pre && it == 0) L = pre;
+                        else prepare<D>(R, a.ctrl, base + o, len - o, lane, stage, L);
                     }
+                }
+            }
+            have_pre = false;
+            const SketchRun& R = runs[k];
+            WarpGroup wg{false, 0u, 0u};
+            if (live) wg = warp_group<D>(L, R.s.key_bytes, lane);
+
+            {
+                const unsigned act_b = __ballot_sync(kFull, L.op != 0);
+                const unsigned lead_b = __ballot_sync(kFull, wg.leader);
+                if (lane == 0 && act_b) {
+                    atomicAdd(&s_act, (uint32_t)__popc(act_b));
+                    atomicAdd(&s_lead, (uint32_t)__popc(lead_b));
+                }
+            }
+
+            // block-level merge of equal keys across the block's warps
+            bool do_global = wg.leader;
+            uint32_t ci = wg.ci, cd = wg.cd;
+            int role = 0;  // 1: owner of a merge slot, 2: merged into an owner, 3: unmerged
+            uint32_t ms = 0;
+            const uint32_t ftag = (L.probe ^ (k * 0x9E3779B9u)) | 1u;
+            if (use_merge) __syncthreads();
+            if (use_merge && wg.leader) {
+                ms = (ftag >> 5) & (kMergeSlots - 1);
+                role = 3;
+                for (int p = 0; p < kMergeSlots; ++p) {
+                    const uint32_t old = atomicCAS(&s_merge.tag[ms], 0u, ftag);
+                    if (old == 0u) {
+                        role = 1;
+                        s_merge.key[ms] = make_ulonglong2(L.k.x0, L.k.x1);
+                        s_merge.run[ms] = k;
+                        s_merge.ci[ms] = ci;
+                        s_merge.cd[ms] = cd;
+                        break;
+                    }
+                    if (old == ftag) {
+                        role = 2;
+                        break;
+                    }
+                    ms = (ms + 1) & (kMergeSlots - 1);
+                }
+            }
+            if (use_merge) __syncthreads();
+            if (role == 2) {
+                const ulonglong2 o = s_merge.key[ms];
+                if (o.x == L.k.x0 && o.y == L.k.x1 && s_merge.run[ms] == k) {
+                    atomicAdd(&s_merge.ci[ms], ci);
+                    atomicAdd(&s_merge.cd[ms], cd);
+                    do_global = false;
                 } else {
-                    const uint32_t q = atomicAdd(&s_nclaims, 1u);
-                    if (q < a.claims_cap) s_claims[q] = make_uint2(k, slot);
-                    else atomicOr(a.ctrl + kCtrlErr, kErrDictFull);
+                    role = 3;
+                }
+            }
+            if (use_merge) __syncthreads();
+            if (role == 1) {
+                ci = s_merge.ci[ms];
+                cd = s_merge.cd[ms];
+                s_merge.tag[ms] = 0u;  // free for the next block-iteration (after its __syncthreads)
+            }
+            if (do_global) {
+                const uint32_t slot = phase1_global<D>(R, a.ctrl, L, ci, cd);
+                if (slot != kNoSlot) {
+                    if (single) {
+                        my_slot = slot;
+                        my_k = k;
+#pragma unroll
+                        for (int i = 0; i < D; ++i) {
+                            my_h[i] = L.h[i];
+                            my_f[i] = L.f[i];
+                        }
+                    } else {
+                        const uint32_t q = atomicAdd(&s_nclaims, 1u);
+                        if (q < a.claims_cap) s_claims[q] = make_uint2(k, slot);
+                        else atomicOr(a.ctrl + kCtrlErr, kErrDictFull);
+                    }
                 }
             }
         }
@@ -335,7 +454,9 @@ __global__ void __launch_bounds__(kChunkBlock, 1) chunk_update_kernel(const __gr
             }
         }
 
-        // prepare the next round's first iteration (keys, ops, hashes) while others finish
+        // arrive, then prepare the next round's first iteration (keys, ops, hashes) while the
+        // other blocks finish, then wait
+        grid_arrive(a.ctrl);
         if (r + 1 < a.n_rounds && gwarp * 32 < a.flat_len) {
             const SketchRun& R = runs[k_first];
             const uint64_t o = gwarp * 32 - R.flat_base;
@@ -348,7 +469,7 @@ __global__ void __launch_bounds__(kChunkBlock, 1) chunk_update_kernel(const __gr
                 }
             }
         }
-        if (!grid_barrier(a.ctrl, target, a.timeout_ns)) return;
+        if (!grid_wait(a.ctrl, target, a.timeout_ns)) return;
         target += gridDim.x;
     }
 }

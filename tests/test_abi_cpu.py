@@ -61,7 +61,7 @@ def test_argument_checks_need_no_gpu(lib_path):
     good = sf.make_params(4, 1 << 18, 16, 13, 2, 65536)
     fb, sb, xb = sf.required_bytes(good)
     assert fb == 4 * (1 << 18) * 16 * 4 and sb == 4 * (1 << 18) * 4
-    assert xb >= 256 + 2 * 65536 * 16
+    assert xb >= 256 + 16 * 65536 * 32
     h = ctypes.c_void_p()
     assert L.sf_create(ctypes.byref(good), None, None, None, None, ctypes.byref(h)) == sf.SF_ERR_INVALID
     assert L.sf_insert_batch(None, None, 5) == sf.SF_ERR_INVALID
