@@ -490,7 +490,20 @@ __device__ __forceinline__ bool row_index(const SketchDesc& s, const Key& k, uin
     return true;
 }
 
-__global__ void __launch_bounds__(kSeqBlock) seq_update_kernel(const SeqArgs a) {
+// S = 1: the paper's one-at-a-time rule, exactly.  One warp takes 32 consecutive updates per
+// window; an update depends on an earlier one only if they share a bucket (i, h_i) in some row
+// (Slim counter (i, j) and Fat bucket (i, j) go together).  In each step every pending update with
+// no pending earlier dependency runs in parallel -- updates on disjoint counters commute, so the
+// result equals stream order.
+//
+// Inserts run as r copies of one key at once: an insert of a key e with r >= 1 copies makes the Fat
+// counters B_i[h_i][f_i] += r, and then raises every Slim counter of e to T = min(m0 + r, F), where m0
+// is the smallest of e's Slim counters before and F the smallest of its Fat counters after.  For
+// r = 1 this is the paper's rule (the minimal counters rise by one when below F).  For r > 1 it is
+// the paper's rule applied r times in a row: the minimal counters rise by one per insertion, in
+// lockstep, while they stay below the Fat estimate, which itself grows by one per insertion.  So a
+// run of same-key insertions with no other update of its buckets in between collapses into one.
+__global__ void __launch_bounds__(kSeqBlock, 1) seq_update_kernel(const SeqArgs a) {
     extern __shared__ uint32_t sA[];
     const SketchDesc& s = a.s;
     const uint64_t slim_n = (uint64_t)s.d * s.w;
@@ -498,43 +511,89 @@ __global__ void __launch_bounds__(kSeqBlock) seq_update_kernel(const SeqArgs a) 
         for (uint64_t i = threadIdx.x; i < slim_n; i += blockDim.x) sA[i] = __ldcg(s.A + i);
         __syncthreads();
     }
-    uint32_t* A = a.slim_in_smem ? sA : s.A;
+    volatile uint32_t* A = a.slim_in_smem ? sA : s.A;
     if (threadIdx.x < 32) {
         const uint32_t lane = threadIdx.x;
-        const bool row = lane < s.d;
+        const unsigned lt = (1u << lane) - 1u;
         bool under = false;
-        for (uint64_t t = 0; t < a.n; ++t) {
-            const int op = a.ops ? (int)a.ops[t] : a.op_const;
-            if (op == 0) continue;
-            const Key k = load_key(a.keys, t, s.key_bytes);
-            uint32_t h = 0, f = 0;
-            bool ok = true;
-            if (row) ok = row_index(s, k, lane, &h, &f);
-            if (!__all_sync(kFull, ok)) {
-                if (lane == 0) atomicOr(a.ctrl + kCtrlErr, kErrBadKey);
-                continue;
+        for (uint64_t t0 = 0; t0 < a.n; t0 += 32) {
+            const uint64_t t = t0 + lane;
+            int op = 0;
+            Key k{0ull, 0ull};
+            uint32_t h[kMaxD], f[kMaxD];
+            if (t < a.n) {
+                op = a.ops ? (int)a.ops[t] : a.op_const;
+                if (op != 0) {
+                    k = load_key(a.keys, t, s.key_bytes);
+                    bool ok = true;
+#pragma unroll
+                    for (int i = 0; i < kMaxD; ++i)
+                        if (i < (int)s.d) ok &= row_index(s, k, (uint32_t)i, &h[i], &f[i]);
+                    if (!ok) {
+                        atomicOr(a.ctrl + kCtrlErr, kErrBadKey);
+                        op = 0;
+                    }
+                }
             }
-            uint32_t* bp = row ? fat_ptr(s, lane, h, f) : nullptr;
-            volatile uint32_t* ap = row ? A + (uint64_t)lane * s.w + h : nullptr;
+            // lanes of this window sharing a bucket with this lane, in any row
+            unsigned conf = 0u;
+#pragma unroll
+            for (int i = 0; i < kMaxD; ++i) {
+                if (i < (int)s.d) {
+                    const unsigned long long b = op != 0 ? (((unsigned long long)i << 40) | h[i])
+                                                         : (0xFFFFFFFF00000000ull | lane);  // idle lanes: unique
+                    conf |= __match_any_sync(kFull, b);
+                }
+            }
+            // collapse a run of inserts of one key when no other update of its buckets lies in between
+            unsigned same = __match_any_sync(kFull, k.x0);
+            if (s.key_bytes > 8) same &= __match_any_sync(kFull, k.x1);
+            const unsigned insm = __ballot_sync(kFull, op > 0);
+            uint32_t r = 1;
             if (op > 0) {
-                uint32_t nv = 0xFFFFFFFFu, av = 0xFFFFFFFFu;
-                if (row) {
-                    nv = atomicAdd(bp, 1u) + 1u;
-                    av = *ap;
-                }
-                const uint32_t F = __reduce_min_sync(kFull, nv);
-                const uint32_t m = __reduce_min_sync(kFull, av);
-                if (row && m < F && av == m) *ap = m + 1u;
-            } else {
-                if (row) {
-                    const uint32_t old = atomicAdd(bp, 0xFFFFFFFFu);
-                    if (old == 0u) under = true;
-                    bool dummy = false;
-                    const uint32_t M = bucket_max_cg(s, lane, h, f, &dummy);
-                    if (*ap > M) *ap = M;
+                const unsigned G = same & insm;
+                const int first = __ffs(G) - 1, last = 31 - __clz(G);
+                const unsigned between = (last > first + 1) ? (((1u << last) - 1u) & ~((2u << first) - 1u)) : 0u;
+                if ((conf & ~G & between) == 0u) {
+                    if (lane == (uint32_t)first) r = (uint32_t)__popc(G);
+                    else op = 0;  // folded into the first insert of the run
                 }
             }
-            __syncwarp();
+            unsigned pending = __ballot_sync(kFull, op != 0);
+            const unsigned dep = conf & lt;
+            while (pending) {
+                const bool ready = ((pending >> lane) & 1u) && (dep & pending) == 0u;
+                if (ready) {
+                    if (op > 0) {
+                        uint32_t F = 0xFFFFFFFFu, m = 0xFFFFFFFFu;
+#pragma unroll
+                        for (int i = 0; i < kMaxD; ++i)
+                            if (i < (int)s.d) F = min(F, atomicAdd(fat_ptr(s, i, h[i], f[i]), r) + r);
+#pragma unroll
+                        for (int i = 0; i < kMaxD; ++i)
+                            if (i < (int)s.d) m = min(m, A[(uint64_t)i * s.w + h[i]]);
+                        const uint64_t mr = (uint64_t)m + r;
+                        const uint32_t T = mr < (uint64_t)F ? (uint32_t)mr : F;
+#pragma unroll
+                        for (int i = 0; i < kMaxD; ++i)
+                            if (i < (int)s.d && A[(uint64_t)i * s.w + h[i]] < T) A[(uint64_t)i * s.w + h[i]] = T;
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < kMaxD; ++i)
+                            if (i < (int)s.d && atomicAdd(fat_ptr(s, i, h[i], f[i]), 0xFFFFFFFFu) == 0u) under = true;
+#pragma unroll
+                        for (int i = 0; i < kMaxD; ++i) {
+                            if (i < (int)s.d) {
+                                bool dummy = false;
+                                const uint32_t M = bucket_max_cg(s, i, h[i], f[i], &dummy);
+                                if (A[(uint64_t)i * s.w + h[i]] > M) A[(uint64_t)i * s.w + h[i]] = M;
+                            }
+                        }
+                    }
+                }
+                __syncwarp();
+                pending &= ~__ballot_sync(kFull, ready);
+            }
         }
         if (under) atomicOr(a.ctrl + kCtrlErr, kErrUnderflow);
     }
