@@ -192,7 +192,7 @@ def main():
     ap.add_argument("--ref-queries", type=int, default=20_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["all", "flows", "batch", "serve"], default="all",
+    ap.add_argument("--workload", choices=["all", "flows", "batch", "serve", "accuracy"], default="all",
                     help="all: the flows line with the batched and serving results embedded")
     ap.add_argument("--batch-sketches", type=int, default=1024)
     ap.add_argument("--serve-seconds", type=float, default=8.0)
@@ -235,6 +235,8 @@ def main():
             line = b
         elif rank == 0:
             line["batched"] = b
+    if args.workload == "accuracy":
+        line = run_accuracy(args, ctx)
     if args.workload in ("all", "serve"):
         v = run_serve(args, ctx)
         if line is None:
@@ -422,6 +424,7 @@ def run_flows(args, ctx):
             g.sync()
             exact &= bool(np.array_equal(got.cpu().numpy().view(np.uint32), want[idx]))
 
+    accuracy = accuracy_report(inputs, dev, stream) if rank == 0 else None
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 2), "unit": "M ops/s", "n_gpus": world, "steps": args.steps,
@@ -435,11 +438,111 @@ def run_flows(args, ctx):
                           "delete_mops": round(args.steps * len(SWEEP) * n_del / t_del / 1e3, 1),
                           "export_query_mops": round(args.steps * len(SWEEP) * N_FLOWS / t_qry / 1e3, 1)},
             "roofline": roofline, "roofline_hbm": roofline_hbm,
-            "cpu_baseline": cpu, "bit_exact_sample": exact, "e2e": e2e,
+            "cpu_baseline": cpu, "bit_exact_sample": exact, "e2e": e2e, "accuracy": accuracy,
             "gpu_launches": args.steps * launches_per_step, "clocks": clk,
         }
         return line
     return None
+
+
+def accuracy_report(inputs, dev, stream, n_sample=8_000_000):
+    """ARE / AAE of the chunked semantics (chunk 65,536) and of the paper's sequential semantics
+    (chunk 1) against exact counts, per Zipf exponent, on the first n_sample inserts of each
+    stream plus deletes of 10 % of those occurrences; all 1,000,000 flows are queried.
+    RE = |f_hat - f| / f (Sec. 5.2); ARE averages it over flows with f > 0; AAE averages
+    |f_hat - f| over all queried flows."""
+    import torch
+
+    import paper_1701_04148_gb300 as sf
+    out = {}
+    g_cpu = torch.Generator(device=dev)
+    g_cpu.manual_seed(SEED0)
+    for idx, s in enumerate(SWEEP):
+        ins, _, flows = inputs[idx]
+        head = ins[:n_sample]
+        victims = torch.randperm(n_sample, generator=g_cpu, device=dev)[: int(n_sample * DEL_FRAC)]
+        dels = head[victims].contiguous()
+        # exact net counts of every flow (rows compared byte for byte)
+        allk = torch.cat([flows, head, dels])
+        _, inv = torch.unique(allk, dim=0, return_inverse=True)
+        nf, nh, nd = flows.shape[0], head.shape[0], dels.shape[0]
+        wts = torch.cat([torch.zeros(nf, dtype=torch.int64, device=dev), torch.ones(nh, dtype=torch.int64, device=dev),
+                         -torch.ones(nd, dtype=torch.int64, device=dev)])
+        cnt = torch.zeros(int(inv.max()) + 1, dtype=torch.int64, device=dev).index_add_(0, inv, wts)
+        f = cnt[inv[:nf]]
+        row = {}
+        for name, S_ in (("chunk", S), ("seq", 1)):
+            g = sf.Sketch(D, W, Z, KB, SEED0, S_, stream=stream)
+            g.insert(head)
+            g.delete(dels)
+            slim, hdr = g.export_slim()
+            est = sf.query(slim, hdr, flows, stream=stream).to(torch.int64) & 0xFFFFFFFF
+            g.sync()
+            err = (est - f).abs().to(torch.float64)
+            present = f > 0
+            row[f"are_{name}"] = float((err[present] / f[present].to(torch.float64)).mean())
+            row[f"aae_{name}"] = float(err.mean())
+            row[f"exact_frac_{name}"] = float((err[present] == 0).to(torch.float64).mean())
+            assert bool((est >= f).all()), "under-estimation"
+            g.close()
+        out[str(s)] = {k: round(v, 5) for k, v in row.items()}
+    return {"sample": f"first {n_sample} inserts of each s plus deletes of 10% of them; all {N_FLOWS} flows queried",
+            "per_s": out}
+
+
+def run_accuracy(args, ctx):
+    """Accuracy experiments of Sec. 5.2 (uniform and skewed workloads) on synthetic stand-ins for
+    the YCSB traces: d=5, w=40,000, z=3, 100,000 distinct items, 10,000,000 insertions drawn
+    uniformly or Zipf(0.99), then deletion of the same insertions in reverse order.  Reports the
+    fraction of items with RE < 1 % after the insertions (Fig. CDF-RE), ARE after every 1,000,000
+    insertions and after every 1,000,000 deletions, for the paper's one-at-a-time semantics
+    (chunk 1) and the chunked semantics (chunk 65,536).  The paper reports 74.51 % (uniform) and
+    74.30 % (skewed) of items below 1 % RE for SF-sketch (Sec. 5.2.1, 5.2.2)."""
+    import torch
+
+    import paper_1701_04148_gb300 as sf
+    import workloads as wl
+    dev, stream = ctx["dev"], ctx["stream"]
+    d, w, z, n_items, n_ins, step = 5, 40_000, 3, 100_000, 10_000_000, 1_000_000
+    out = {"workload": "accuracy-sec5.2", "d": d, "w": w, "z": z, "items": n_items, "insertions": n_ins,
+           "paper_re_below_1pct": {"uniform": 0.7451, "skewed": 0.7430}}
+    for name, s_ in (("uniform", 0.0), ("skewed", 0.99)):
+        keys, ids = wl.insert_only_u32(n_ins, n_items, s_, seed=7 if s_ == 0 else 8, device=dev)
+        kid = keys.view(torch.int32).reshape(-1)
+        idv = ids.view(torch.int32).reshape(-1)
+        sid, order = torch.sort(idv)
+        pos = order[torch.searchsorted(sid, kid)]           # item index of every insertion
+        res = {}
+        for sem, S_ in (("seq", 1), ("chunk", 65536)):
+            g = sf.Sketch(d, w, z, 4, 11, S_, stream=stream)
+            f = torch.zeros(n_items, dtype=torch.int64, device=dev)
+            are_ins, are_del = [], []
+
+            def score():
+                slim, hdr = g.export_slim()
+                est = sf.query(slim, hdr, ids, stream=stream).to(torch.int64) & 0xFFFFFFFF
+                present = f > 0
+                re = (est - f).abs().to(torch.float64)[present] / f[present].to(torch.float64)
+                assert bool((est >= f).all())
+                return float(re.mean()), float((re < 0.01).to(torch.float64).mean())
+
+            for b0 in range(0, n_ins, step):
+                g.insert(keys[b0:b0 + step])
+                f.index_add_(0, pos[b0:b0 + step], torch.ones(step, dtype=torch.int64, device=dev))
+                are_ins.append(round(score()[0], 5))
+            below = score()[1]
+            for b1 in range(n_ins, 0, -step):                     # reverse order of the insertions
+                b0 = b1 - step
+                g.delete(keys[b0:b1].flip(0).contiguous())
+                f.index_add_(0, pos[b0:b1], -torch.ones(step, dtype=torch.int64, device=dev))
+                if b0 > 0:
+                    are_del.append(round(score()[0], 5))
+            g.sync()
+            res[sem] = {"re_below_1pct": round(below, 4), "are_after_each_1M_insertions": are_ins,
+                        "are_during_reverse_deletion": are_del}
+            g.close()
+        out[name] = res
+    return out
 
 
 def run_batch(args, ctx):

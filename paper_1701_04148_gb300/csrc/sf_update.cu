@@ -177,12 +177,21 @@ struct MergeTable {
     ulonglong2 key[kMergeSlots];
 };
 
+// What a claiming leader keeps in registers across the barrier (single-iteration rounds): its own
+// counts and the chunk-start minimum m of the key's Slim counters with its minimal-row mask.  Every
+// leader of a key reads the same chunk-start values, so other leaders only add their counts to the
+// dictionary entry (and store m and the mask when they insert).
+struct OwnCounts {
+    uint32_t ci, cd, m, mask;
+};
+
 // Global part of phase 1 for one (block- or warp-) leader: Fat RED of the net count, dictionary
 // claim/lookup (one 128-bit CAS per probe), counts, chunk-start Slim minimum.  Returns the slot
-// this thread claimed, or kNoSlot.
+// this thread claimed, or kNoSlot.  With keep_own, a claimer leaves its counts, m and mask in *own
+// instead of writing them to the entry.
 template <int D>
 __device__ __forceinline__ uint32_t phase1_global(const SketchRun& R, uint32_t* ctrl, const LaneWork<D>& L,
-                                                  uint32_t ci, uint32_t cd) {
+                                                  uint32_t ci, uint32_t cd, bool keep_own, OwnCounts* own) {
     const SketchDesc& s = R.s;
     const int32_t net = (int32_t)ci - (int32_t)cd;
     if (net != 0) {
@@ -214,14 +223,20 @@ __device__ __forceinline__ uint32_t phase1_global(const SketchRun& R, uint32_t* 
         atomicOr(ctrl + kCtrlErr, kErrDictFull);
         return kNoSlot;
     }
+    uint32_t m = 0xFFFFFFFFu, mask = 0u;
     if (ci) {
-        atomicAdd(&R.dict[slot].c_ins, ci);
-        uint32_t m = 0xFFFFFFFFu, mask = 0u;
 #pragma unroll
         for (int i = 0; i < D; ++i) m = min(m, av[i]);
 #pragma unroll
         for (int i = 0; i < D; ++i) mask |= (av[i] == m ? 1u : 0u) << i;
-        // every leader of this key stores the same chunk-start minimum and minimal-row mask
+    }
+    if (claimed && keep_own) {
+        *own = OwnCounts{ci, cd, m, mask};
+        return slot;
+    }
+    if (ci) {
+        atomicAdd(&R.dict[slot].c_ins, ci);
+        // every such leader of this key stores the same chunk-start minimum and minimal-row mask
         asm volatile("st.global.cg.v2.u32 [%0], {%1, %2};" ::"l"(&R.dict[slot].m), "r"(m), "r"(mask) : "memory");
     }
     if (cd) atomicAdd(&R.dict[slot].c_del, cd);
@@ -317,6 +332,7 @@ __global__ void __launch_bounds__(kChunkBlock, 1) chunk_update_kernel(const __gr
         // ---- phase 1: Fat updates and the chunk dictionaries --------------------------------
         uint32_t my_slot = kNoSlot, my_k = 0;
         uint32_t my_h[D], my_f[D];
+        OwnCounts my_own{0u, 0u, 0u, 0u};
         for (uint64_t it = 0; it < iters; ++it) {
             const uint64_t j = gwarp * 32 + it * nwarps * 32;
             LaneWork<D> L;
@@ -398,11 +414,13 @@ __global__ void __launch_bounds__(kChunkBlock, 1) chunk_update_kernel(const __gr
                 s_merge.tag[ms] = 0u;  // free for the next block-iteration (after its __syncthreads)
             }
             if (do_global) {
-                const uint32_t slot = phase1_global<D>(R, a.ctrl, L, ci, cd);
+                OwnCounts own;
+                const uint32_t slot = phase1_global<D>(R, a.ctrl, L, ci, cd, single, &own);
                 if (slot != kNoSlot) {
                     if (single) {
                         my_slot = slot;
                         my_k = k;
+                        my_own = own;
 #pragma unroll
                         for (int i = 0; i < D; ++i) {
                             my_h[i] = L.h[i];
@@ -425,13 +443,16 @@ __global__ void __launch_bounds__(kChunkBlock, 1) chunk_update_kernel(const __gr
             if (my_slot != kNoSlot) {
                 const SketchRun& R = runs[my_k];
                 DictEntry* ep = R.dict + my_slot;
-                const uint4 cn = __ldcg(reinterpret_cast<const uint4*>(ep) + 1);  // c_ins, c_del, m, mask
+                // other leaders' contributions (c_ins, c_del, m, mask); the claimer's own are in my_own
+                const uint4 cn = __ldcg(reinterpret_cast<const uint4*>(ep) + 1);
                 uint32_t Fv[D];
                 if (a.may_ins) {
 #pragma unroll
                     for (int i = 0; i < D; ++i) Fv[i] = __ldcg(fat_ptr(R.s, i, my_h[i], my_f[i]));
                 }
-                phase2_key<D>(R.s, a.ctrl, ep, my_h, my_f, cn.x, cn.y, cn.z, cn.w, Fv);
+                const bool mine = my_own.ci != 0u;  // the claimer read the chunk-start Slim itself
+                phase2_key<D>(R.s, a.ctrl, ep, my_h, my_f, my_own.ci + cn.x, my_own.cd + cn.y, mine ? my_own.m : cn.z,
+                              mine ? my_own.mask : cn.w, Fv);
             }
         } else {
             const uint32_t nclaims = min(s_nclaims, a.claims_cap);
