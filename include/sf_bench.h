@@ -39,6 +39,14 @@ sf_status sf_bench_random_access(uint32_t *buf_dev, uint64_t n_words, uint64_t t
  */
 sf_status sf_bench_grid_barrier(void *scratch_dev, uint32_t n_barriers, void *cuda_stream);
 
+/*
+ * Failure-detection check of the bounded device waits: the same barrier loop, but
+ * `missing_blocks` blocks of the grid never arrive, so every other block's wait runs out after
+ * timeout_ns (at most 1 s here) and the call returns SF_ERR_TIMEOUT with the context still usable.
+ * missing_blocks = 0 is a normal run.  No fault and no unbounded wait is involved.
+ */
+sf_status sf_bench_wait_timeout(void *scratch_dev, uint32_t missing_blocks, uint64_t timeout_ns, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -168,9 +168,6 @@ struct sfc {
     void complete(Slot& s) {  // caller holds mu; the slot's event has fired
         const auto now = Clock::now();
         for (auto& r : s.members) {
-            if (r->status == SF_OK && r->n) {
-                // answers were placed contiguously in request order
-            }
             lat_us.push_back(std::chrono::duration<double, std::micro>(now - r->t_submit).count());
             unref(r->v);
             r->v = nullptr;

@@ -32,6 +32,13 @@ __global__ void __launch_bounds__(kChunkBlock) barrier_kernel(uint32_t* ctrl, ui
         if (!grid_barrier(ctrl, (unsigned long long)(i + 1) * gridDim.x, kBarrierTimeoutNs)) return;
 }
 
+// Blocks >= gridDim.x - missing skip the barrier; the others wait for them until timeout_ns.
+__global__ void __launch_bounds__(kChunkBlock) missing_arrival_kernel(uint32_t* ctrl, uint32_t missing,
+                                                                      uint64_t timeout_ns) {
+    if (blockIdx.x >= gridDim.x - missing) return;
+    grid_barrier(ctrl, (unsigned long long)gridDim.x, timeout_ns);
+}
+
 }  // namespace
 
 }  // namespace sfk
@@ -73,6 +80,34 @@ sf_status sf_bench_grid_barrier(void* scratch_dev, uint32_t n_barriers, void* cu
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     if (cudaLaunchKernelEx(&cfg, sfk::barrier_kernel, (uint32_t*)scratch_dev, n_barriers) != cudaSuccess)
+        return SF_ERR_CUDA;
+    uint32_t err = 0;
+    if (cudaMemcpyAsync(&err, scratch_dev, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return SF_ERR_CUDA;
+    return (err & sfk::kErrTimeout) ? SF_ERR_TIMEOUT : SF_OK;
+}
+
+sf_status sf_bench_wait_timeout(void* scratch_dev, uint32_t missing_blocks, uint64_t timeout_ns, void* cuda_stream) {
+    if (!scratch_dev || timeout_ns > 1000000000ull) return SF_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return SF_ERR_CUDA;
+    if (missing_blocks >= (uint32_t)sms) return SF_ERR_INVALID;
+    if (cudaMemsetAsync(scratch_dev, 0, 256, st) != cudaSuccess) return SF_ERR_CUDA;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)sms);
+    cfg.blockDim = dim3(sfk::kChunkBlock);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, sfk::missing_arrival_kernel, (uint32_t*)scratch_dev, missing_blocks, timeout_ns) !=
+        cudaSuccess)
         return SF_ERR_CUDA;
     uint32_t err = 0;
     if (cudaMemcpyAsync(&err, scratch_dev, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
