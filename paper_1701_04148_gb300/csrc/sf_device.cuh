@@ -150,6 +150,47 @@ __device__ __forceinline__ void red_release_gpu_add_u64(unsigned long long* p, u
     asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+// L2 eviction-priority policies.  The Fat and the Slim are reused across chunks and should stay in
+// L2 (evict_last); the chunk dictionary and the key stream are touched once or twice per chunk
+// (evict_first), so they should not push counters out.
+__device__ __forceinline__ unsigned long long l2_policy_keep() {
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ unsigned long long l2_policy_stream() {
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ uint32_t ld_cg_pol(const uint32_t* p, unsigned long long pol) {
+    uint32_t v;
+    asm volatile("ld.global.cg.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
+__device__ __forceinline__ uint4 ld_cg_v4_pol(const void* p, unsigned long long pol) {
+    uint4 v;
+    asm volatile("ld.global.cg.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p), "l"(pol));
+    return v;
+}
+
+__device__ __forceinline__ void red_add_pol(uint32_t* p, uint32_t v, unsigned long long pol) {
+    asm volatile("red.global.add.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(pol) : "memory");
+}
+
+__device__ __forceinline__ void red_max_pol(uint32_t* p, uint32_t v, unsigned long long pol) {
+    asm volatile("red.global.max.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(pol) : "memory");
+}
+
+__device__ __forceinline__ void red_min_pol(uint32_t* p, uint32_t v, unsigned long long pol) {
+    asm volatile("red.global.min.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(pol) : "memory");
+}
+
 // 128-bit compare-and-swap in global memory (atom.cas.b128, sm_90 and later).
 __device__ __forceinline__ void cas128(unsigned long long* addr, unsigned long long cmp_lo,
                                        unsigned long long cmp_hi, unsigned long long new_lo,

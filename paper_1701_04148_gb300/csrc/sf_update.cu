@@ -39,19 +39,20 @@ __device__ __forceinline__ uint32_t* slim_ptr(const SketchDesc& s, uint32_t i, u
 
 // max_k B_i[h][k] and whether B_i[h][f] went negative (strict-turnstile violation).
 __device__ __forceinline__ uint32_t bucket_max_cg(const SketchDesc& s, uint32_t i, uint32_t h,
-                                                  uint32_t f, bool* underflow) {
+                                                  uint32_t f, bool* underflow,
+                                                  unsigned long long pol = 0ull, bool hinted = false) {
     const uint32_t* bk = s.B + ((uint64_t)i * s.w + h) * s.z;
     uint32_t mx = 0;
     if ((s.z & 3u) == 0u) {
         const uint4* b4 = reinterpret_cast<const uint4*>(bk);
         for (uint32_t q = 0; q < (s.z >> 2); ++q) {
-            const uint4 v = __ldcg(b4 + q);
+            const uint4 v = hinted ? ld_cg_v4_pol(b4 + q, pol) : __ldcg(b4 + q);
             mx = max(max(mx, v.x), max(v.y, max(v.z, v.w)));
         }
     } else {
-        for (uint32_t k = 0; k < s.z; ++k) mx = max(mx, __ldcg(bk + k));
+        for (uint32_t k = 0; k < s.z; ++k) mx = max(mx, hinted ? ld_cg_pol(bk + k, pol) : __ldcg(bk + k));
     }
-    if ((int32_t)__ldcg(bk + f) < 0) *underflow = true;
+    if ((int32_t)(hinted ? ld_cg_pol(bk + f, pol) : __ldcg(bk + f)) < 0) *underflow = true;
     return mx;
 }
 
@@ -100,10 +101,6 @@ __device__ __forceinline__ void ld_entry(const DictEntry* ep, unsigned long long
     asm volatile("ld.global.cg.v4.u64 {%0, %1, %2, %3}, [%4];"
                  : "=l"(k0), "=l"(k1), "=l"(c01), "=l"(c23)
                  : "l"(ep));
-}
-
-__device__ __forceinline__ void clear_entry(DictEntry* ep) {
-    asm volatile("st.global.cg.v4.u64 [%0], {%1, %1, %1, %1};" ::"l"(ep), "l"(0ull) : "memory");
 }
 
 // One lane's update of the current warp-iteration, loaded and hashed (independent of the
@@ -191,17 +188,18 @@ struct OwnCounts {
 // instead of writing them to the entry.
 template <int D>
 __device__ __forceinline__ uint32_t phase1_global(const SketchRun& R, uint32_t* ctrl, const LaneWork<D>& L,
-                                                  uint32_t ci, uint32_t cd, bool keep_own, OwnCounts* own) {
+                                                  uint32_t ci, uint32_t cd, bool keep_own, OwnCounts* own,
+                                                  unsigned long long keep, unsigned long long stream) {
     const SketchDesc& s = R.s;
     const int32_t net = (int32_t)ci - (int32_t)cd;
     if (net != 0) {
 #pragma unroll
-        for (int i = 0; i < D; ++i) atomicAdd(fat_ptr(s, i, L.h[i], L.f[i]), (uint32_t)net);
+        for (int i = 0; i < D; ++i) red_add_pol(fat_ptr(s, i, L.h[i], L.f[i]), (uint32_t)net, keep);
     }
     uint32_t av[D];
     if (ci) {  // chunk-start Slim values, issued before the CAS so the latencies overlap
 #pragma unroll
-        for (int i = 0; i < D; ++i) av[i] = __ldcg(slim_ptr(s, i, L.h[i]));
+        for (int i = 0; i < D; ++i) av[i] = ld_cg_pol(slim_ptr(s, i, L.h[i]), keep);
     }
     const unsigned long long tag = L.k.x1 | kKeyTag;
     uint32_t slot = L.probe & R.cap_mask;
@@ -235,11 +233,13 @@ __device__ __forceinline__ uint32_t phase1_global(const SketchRun& R, uint32_t* 
         return slot;
     }
     if (ci) {
-        atomicAdd(&R.dict[slot].c_ins, ci);
+        red_add_pol(&R.dict[slot].c_ins, ci, stream);
         // every such leader of this key stores the same chunk-start minimum and minimal-row mask
-        asm volatile("st.global.cg.v2.u32 [%0], {%1, %2};" ::"l"(&R.dict[slot].m), "r"(m), "r"(mask) : "memory");
+        asm volatile("st.global.cg.L2::cache_hint.v2.u32 [%0], {%1, %2}, %3;" ::"l"(&R.dict[slot].m), "r"(m),
+                     "r"(mask), "l"(stream)
+                     : "memory");
     }
-    if (cd) atomicAdd(&R.dict[slot].c_del, cd);
+    if (cd) red_add_pol(&R.dict[slot].c_del, cd, stream);
     return claimed ? slot : kNoSlot;
 }
 
@@ -251,7 +251,8 @@ __device__ __forceinline__ uint32_t phase1_global(const SketchRun& R, uint32_t* 
 template <int D>
 __device__ __forceinline__ void phase2_key(const SketchDesc& s, uint32_t* ctrl, DictEntry* ep, const uint32_t* h,
                                            const uint32_t* f, uint32_t c_ins, uint32_t c_del, uint32_t m,
-                                           uint32_t mask, const uint32_t* Fv) {
+                                           uint32_t mask, const uint32_t* Fv, unsigned long long keep,
+                                           unsigned long long stream) {
     if (c_ins) {
         uint32_t F = 0xFFFFFFFFu;
 #pragma unroll
@@ -261,16 +262,18 @@ __device__ __forceinline__ void phase2_key(const SketchDesc& s, uint32_t* ctrl, 
         if (T > m) {
 #pragma unroll
             for (int i = 0; i < D; ++i)
-                if (((mask >> i) & 1u) || c_ins > 1u) atomicMax(slim_ptr(s, i, h[i]), T);
+                if (((mask >> i) & 1u) || c_ins > 1u) red_max_pol(slim_ptr(s, i, h[i]), T, keep);
         }
     }
     if (c_del) {
         bool under = false;
 #pragma unroll
-        for (int i = 0; i < D; ++i) atomicMin(slim_ptr(s, i, h[i]), bucket_max_cg(s, i, h[i], f[i], &under));
+        for (int i = 0; i < D; ++i)
+            red_min_pol(slim_ptr(s, i, h[i]), bucket_max_cg(s, i, h[i], f[i], &under, keep, true), keep);
         if (under) atomicOr(ctrl + kCtrlErr, kErrUnderflow);
     }
-    clear_entry(ep);
+    asm volatile("st.global.cg.L2::cache_hint.v4.u64 [%0], {%1, %1, %1, %1}, %2;" ::"l"(ep), "l"(0ull), "l"(stream)
+                 : "memory");
 }
 
 // The sketch whose flat slot range holds slot j (runs sorted by flat_base).
@@ -291,6 +294,7 @@ __global__ void __launch_bounds__(kChunkBlock, 1) chunk_update_kernel(const __gr
     __shared__ uint32_t s_nclaims;
     __shared__ uint4 s_stage[kChunkBlock / 32][32];
     const SketchRun* runs = a.runs ? a.runs : &a.one;
+    const unsigned long long pol_keep = l2_policy_keep(), pol_stream = l2_policy_stream();
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -415,7 +419,7 @@ __global__ void __launch_bounds__(kChunkBlock, 1) chunk_update_kernel(const __gr
             }
             if (do_global) {
                 OwnCounts own;
-                const uint32_t slot = phase1_global<D>(R, a.ctrl, L, ci, cd, single, &own);
+                const uint32_t slot = phase1_global<D>(R, a.ctrl, L, ci, cd, single, &own, pol_keep, pol_stream);
                 if (slot != kNoSlot) {
                     if (single) {
                         my_slot = slot;
@@ -444,15 +448,15 @@ __global__ void __launch_bounds__(kChunkBlock, 1) chunk_update_kernel(const __gr
                 const SketchRun& R = runs[my_k];
                 DictEntry* ep = R.dict + my_slot;
                 // other leaders' contributions (c_ins, c_del, m, mask); the claimer's own are in my_own
-                const uint4 cn = __ldcg(reinterpret_cast<const uint4*>(ep) + 1);
+                const uint4 cn = ld_cg_v4_pol(reinterpret_cast<const uint4*>(ep) + 1, pol_stream);
                 uint32_t Fv[D];
                 if (a.may_ins) {
 #pragma unroll
-                    for (int i = 0; i < D; ++i) Fv[i] = __ldcg(fat_ptr(R.s, i, my_h[i], my_f[i]));
+                    for (int i = 0; i < D; ++i) Fv[i] = ld_cg_pol(fat_ptr(R.s, i, my_h[i], my_f[i]), pol_keep);
                 }
                 const bool mine = my_own.ci != 0u;  // the claimer read the chunk-start Slim itself
                 phase2_key<D>(R.s, a.ctrl, ep, my_h, my_f, my_own.ci + cn.x, my_own.cd + cn.y, mine ? my_own.m : cn.z,
-                              mine ? my_own.mask : cn.w, Fv);
+                              mine ? my_own.mask : cn.w, Fv, pol_keep, pol_stream);
             }
         } else {
             const uint32_t nclaims = min(s_nclaims, a.claims_cap);
@@ -468,10 +472,10 @@ __global__ void __launch_bounds__(kChunkBlock, 1) chunk_update_kernel(const __gr
                 const uint32_t c_ins = (uint32_t)c01;
                 if (c_ins) {
 #pragma unroll
-                    for (int i = 0; i < D; ++i) Fv[i] = __ldcg(fat_ptr(R.s, i, h[i], f[i]));
+                    for (int i = 0; i < D; ++i) Fv[i] = ld_cg_pol(fat_ptr(R.s, i, h[i], f[i]), pol_keep);
                 }
                 phase2_key<D>(R.s, a.ctrl, ep, h, f, c_ins, (uint32_t)(c01 >> 32), (uint32_t)c23,
-                              (uint32_t)(c23 >> 32), Fv);
+                              (uint32_t)(c23 >> 32), Fv, pol_keep, pol_stream);
             }
         }
 
