@@ -192,7 +192,7 @@ def main():
     ap.add_argument("--ref-queries", type=int, default=20_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["all", "flows", "batch", "serve", "accuracy"], default="all",
+    ap.add_argument("--workload", choices=["all", "flows", "batch", "serve", "accuracy", "pipeline"], default="all",
                     help="all: the flows line with the batched and serving results embedded")
     ap.add_argument("--batch-sketches", type=int, default=1024)
     ap.add_argument("--serve-seconds", type=float, default=8.0)
@@ -237,6 +237,8 @@ def main():
             line["batched"] = b
     if args.workload == "accuracy":
         line = run_accuracy(args, ctx)
+    if args.workload == "pipeline":
+        line = run_pipeline(args, ctx)
     if args.workload in ("all", "serve"):
         v = run_serve(args, ctx)
         if line is None:
@@ -270,32 +272,39 @@ def run_flows(args, ctx):
     answers = [torch.empty(N_FLOWS, dtype=torch.int32, device=dev) for _ in SWEEP]
     n_del = inputs[0][1].shape[0]
     ops_per_step = len(SWEEP) * (N_INS + n_del + N_FLOWS)
-    launches_per_step = len(SWEEP) * 3  # insert + delete chunk-kernel launches, one query launch
+    # the sketches of the sweep are independent: each update call is one batched launch over all
+    # of them (same per-sketch semantics as one call per sketch; see the batched-update tests)
+    del_ops = [torch.full((n_del,), -1, dtype=torch.int8, device=dev) for _ in SWEEP]
+    slots = len(SWEEP) * ((S + 31) // 32 * 32)
+    b_ins = sf.Batch(len(SWEEP), graph=True, stream=stream, max_round_slots=slots)
+    b_del = sf.Batch(len(SWEEP), graph=True, stream=stream, max_round_slots=slots)
+    launches_per_step = 2 + len(SWEEP)  # one batched insert and one batched delete launch, a query per sketch
 
     def step(evs=None, host=None):
-        for idx in range(len(SWEEP)):
-            if host is not None:
+        if host is not None:
+            for idx in range(len(SWEEP)):
                 ins_h, dels_h, flows_h, _ = host[idx]
                 ins_d, dels_d, flows_d = inputs[idx]
                 ins_d.copy_(ins_h, non_blocking=True)
                 dels_d.copy_(dels_h, non_blocking=True)
                 flows_d.copy_(flows_h, non_blocking=True)
-            ins, dels, flows = inputs[idx]
-            sk = sketches[idx]
+        for sk in sketches:
             sk.reset()
-            if evs is not None:
-                evs[idx][0].record(stream)
-            sk.insert(ins)
-            if evs is not None:
-                evs[idx][1].record(stream)
-            sk.delete(dels)
-            if evs is not None:
-                evs[idx][2].record(stream)
-            slim, hdr = sk.export_slim(slims[idx])
-            sf.query(slim, hdr, flows, out=answers[idx], stream=stream)
-            if evs is not None:
-                evs[idx][3].record(stream)
-            if host is not None:
+        if evs is not None:
+            evs[0].record(stream)
+        b_ins.update([(sk, inp[0], None) for sk, inp in zip(sketches, inputs)])
+        if evs is not None:
+            evs[1].record(stream)
+        b_del.update([(sk, inp[1], o) for sk, inp, o in zip(sketches, inputs, del_ops)])
+        if evs is not None:
+            evs[2].record(stream)
+        for idx in range(len(SWEEP)):
+            slim, hdr = sketches[idx].export_slim(slims[idx])
+            sf.query(slim, hdr, inputs[idx][2], out=answers[idx], stream=stream)
+        if evs is not None:
+            evs[3].record(stream)
+        if host is not None:
+            for idx in range(len(SWEEP)):
                 host[idx][3].copy_(answers[idx], non_blocking=True)
 
     for _ in range(args.warmup):
@@ -303,9 +312,10 @@ def run_flows(args, ctx):
     torch.cuda.synchronize()
     for sk in sketches:
         sk.sync()
+    assert b_ins.sync_status() == sf.SF_OK and b_del.sync_status() == sf.SF_OK
 
     # ---- timed region (device-resident inputs) --------------------------------------------
-    evs_all = [[[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in SWEEP] for _ in range(args.steps)]
+    evs_all = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(gpu_index_for(local))
     clocks.start()
@@ -324,9 +334,9 @@ def run_flows(args, ctx):
     ms = e0.elapsed_time(e1) / args.steps
     for sk in sketches:
         sk.sync()
-    t_ins = sum(evs_all[k][i][0].elapsed_time(evs_all[k][i][1]) for k in range(args.steps) for i in range(len(SWEEP)))
-    t_del = sum(evs_all[k][i][1].elapsed_time(evs_all[k][i][2]) for k in range(args.steps) for i in range(len(SWEEP)))
-    t_qry = sum(evs_all[k][i][2].elapsed_time(evs_all[k][i][3]) for k in range(args.steps) for i in range(len(SWEEP)))
+    t_ins = sum(evs_all[k][0].elapsed_time(evs_all[k][1]) for k in range(args.steps))
+    t_del = sum(evs_all[k][1].elapsed_time(evs_all[k][2]) for k in range(args.steps))
+    t_qry = sum(evs_all[k][2].elapsed_time(evs_all[k][3]) for k in range(args.steps))
     ms_max = ms
     if dist is not None:
         t = torch.tensor([ms], dtype=torch.float64, device=dev)
@@ -349,7 +359,7 @@ def run_flows(args, ctx):
     del buf
     upd_timed = args.steps * len(SWEEP) * (N_INS + n_del)
     chunk_ms = t_ins + t_del
-    launches_chunk = args.steps * len(SWEEP) * 2
+    launches_chunk = args.steps * 2
     achieved = upd_timed * L2_OPS_PER_UPDATE / (chunk_ms / 1e3) / 1e9
     tr = traffic_record()
     traffic = None
@@ -396,6 +406,30 @@ def run_flows(args, ctx):
         for sk in sketches:
             sk.sync()
 
+    # ---- the single-sketch path (one call per sketch), measured after the timed region ------
+    single = None
+    if rank == 0:
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in SWEEP]
+        for idx, sk in enumerate(sketches):
+            sk.reset()
+            ev[idx][0].record(stream)
+            sk.insert(inputs[idx][0])
+            ev[idx][1].record(stream)
+            sk.delete(inputs[idx][1])
+            ev[idx][2].record(stream)
+        torch.cuda.synchronize()
+        ti = sum(e[0].elapsed_time(e[1]) for e in ev)
+        td = sum(e[1].elapsed_time(e[2]) for e in ev)
+        single = {"insert_mops": round(len(SWEEP) * N_INS / ti / 1e3, 1),
+                  "delete_mops": round(len(SWEEP) * n_del / td / 1e3, 1),
+                  "insert_mops_per_zipf_s": {str(x): round(N_INS / ev[i][0].elapsed_time(ev[i][1]) / 1e3, 1)
+                                             for i, x in enumerate(SWEEP)},
+                  "roofline_frac": round(len(SWEEP) * (N_INS + n_del) * L2_OPS_PER_UPDATE / ((ti + td) / 1e3) / 1e9
+                                         / best, 4),
+                  "note": "one sf_insert_batch / sf_delete_batch call per sketch, same inputs"}
+        for sk in sketches:
+            sk.sync()
+
     # ---- CPU baseline (the oracle) and a bit-exact check on the same bounded sample -------
     cpu = None
     exact = None
@@ -434,10 +468,11 @@ def run_flows(args, ctx):
                        "chunk": S, "inserts_per_s": N_INS, "deletes_per_s": n_del, "flows": N_FLOWS,
                        "zipf_s": list(SWEEP), "l2": "inputs larger than L2 (2.7 GB of keys per step)",
                        "parallelism": f"replicas x{world}"},
-            "breakdown": {"insert_mops": round(args.steps * len(SWEEP) * N_INS / t_ins / 1e3, 1),
+            "breakdown": {"mode": "the six sweep sketches updated by one batched launch per call",
+                          "insert_mops": round(args.steps * len(SWEEP) * N_INS / t_ins / 1e3, 1),
                           "delete_mops": round(args.steps * len(SWEEP) * n_del / t_del / 1e3, 1),
                           "export_query_mops": round(args.steps * len(SWEEP) * N_FLOWS / t_qry / 1e3, 1)},
-            "roofline": roofline, "roofline_hbm": roofline_hbm,
+            "roofline": roofline, "roofline_hbm": roofline_hbm, "single_sketch": single,
             "cpu_baseline": cpu, "bit_exact_sample": exact, "e2e": e2e, "accuracy": accuracy,
             "gpu_launches": args.steps * launches_per_step, "clocks": clk,
         }
@@ -543,6 +578,57 @@ def run_accuracy(args, ctx):
             g.close()
         out[name] = res
     return out
+
+
+def run_pipeline(args, ctx):
+    """The paper's GPU query experiment (Sec. 4.2, 5.4) on this GPU: batches of b host keys go
+    through sf_query_pipelined (split over n streams, copy in, query, copy out), b from 1 K to
+    64 K.  Throughput: many batches back to back; latency: one batch alone, submit to answers in
+    host memory.  The Slim is the Zipf(1.0) 5-tuple sketch (d=4, w=2^18).  Paper (Tesla C2075):
+    ~50 Mqps at 20 K, >110 Mqps at 64 K, mean latency < 410 us up to 28 K."""
+    import numpy as np
+    import torch
+
+    import paper_1701_04148_gb300 as sf
+    import workloads as wl
+    dev, stream = ctx["dev"], ctx["stream"]
+    ins, dels, flows = wl.flows_with_deletes(N_INS, N_FLOWS, 1.0, DEL_FRAC, seed=SEED0 + 2, device=dev)
+    g = sf.Sketch(D, W, Z, KB, SEED0, S, stream=stream)
+    g.insert(ins)
+    g.delete(dels)
+    slim, hdr = g.export_slim()
+    g.sync()
+    del ins, dels
+    n_streams = 4
+    streams = [torch.cuda.Stream(device=dev) for _ in range(n_streams)]
+    rows = []
+    for b in (1024, 4096, 8192, 16384, 20000, 28000, 32768, 65536):
+        kh = flows[:b].cpu().pin_memory()
+        oh = torch.zeros(b, dtype=torch.int32).pin_memory()
+        kd = torch.empty((b, KB), dtype=torch.uint8, device=dev)
+        od = torch.empty(b, dtype=torch.int32, device=dev)
+        for _ in range(5):
+            sf.query_pipelined(slim, hdr, kh, oh, kd, od, streams)
+        torch.cuda.synchronize()
+        lat = []
+        for _ in range(50):
+            t = time.perf_counter()
+            sf.query_pipelined(slim, hdr, kh, oh, kd, od, streams)
+            for s_ in streams:
+                s_.synchronize()
+            lat.append(time.perf_counter() - t)
+        reps = max(20, int(4_000_000 // b))
+        t = time.perf_counter()
+        for _ in range(reps):
+            sf.query_pipelined(slim, hdr, kh, oh, kd, od, streams)
+        for s_ in streams:
+            s_.synchronize()
+        dt = time.perf_counter() - t
+        rows.append({"batch": b, "mqps": round(b * reps / dt / 1e6, 1),
+                     "mean_latency_us": round(1e6 * float(np.mean(lat)), 1),
+                     "p99_latency_us": round(1e6 * float(np.percentile(lat, 99)), 1)})
+    return {"workload": "query-pipeline-sec4.2", "streams": n_streams, "key_bytes": KB, "rows": rows,
+            "paper_tesla_c2075": {"mqps_at_20K": 50, "mqps_at_64K": 110, "mean_latency_us_upto_28K": 410}}
 
 
 def run_batch(args, ctx):

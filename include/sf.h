@@ -172,6 +172,17 @@ sf_status sf_query_batch(const sf_slim_view *slim, const void *keys_dev, uint64_
 sf_status sf_sync(sf_sketch *s);
 
 /*
+ * Multi-stream query pipeline (Sec. 4.2.2): a batch of n host keys is split over n_streams CUDA
+ * streams in parts of nearly equal size (the first n % n_streams parts take one key more); on each
+ * stream its part is copied to the device, queried (Sec. 3.1) and its answers copied back, so the
+ * copies of one part overlap the kernels of another.  keys_host / out_host: host buffers (pinned
+ * for the copies to overlap); keys_dev / out_dev: device staging of n keys / n answers;
+ * streams: n_streams cudaStream_t.  Asynchronous: synchronise the streams before reading out_host.
+ */
+sf_status sf_query_pipelined(const sf_slim_view *slim, const void *keys_host, uint64_t n, uint32_t *out_host,
+                             void *keys_dev, uint32_t *out_dev, uint32_t n_streams, void *const *streams);
+
+/*
  * ---- Batched many-sketch update --------------------------------------------------------------
  * Monitoring nodes each fill their own sketch (Sec. 1.1); a collector-side or node-side host may
  * hold thousands of them.  The paper updates one sketch at a time; a batch applies one call's

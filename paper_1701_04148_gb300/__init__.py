@@ -91,6 +91,9 @@ _SIGS = {
     "sf_query_batch": (ctypes.c_int32, [ctypes.POINTER(SlimView), ctypes.c_void_p, ctypes.c_uint64,
                                         ctypes.c_void_p, ctypes.c_void_p]),
     "sf_sync": (ctypes.c_int32, [ctypes.c_void_p]),
+    "sf_query_pipelined": (ctypes.c_int32, [ctypes.POINTER(SlimView), ctypes.c_void_p, ctypes.c_uint64,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32,
+                                            ctypes.c_void_p]),
     "sf_batch_required_bytes": (ctypes.c_int32, [ctypes.c_uint32, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]),
     "sf_batch_create": (ctypes.c_int32, [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_uint32, ctypes.POINTER(ctypes.c_void_p)]),
@@ -455,3 +458,14 @@ class Collector:
             self.close()
         except Exception:
             pass
+
+
+def query_pipelined(slim, hdr: SlimHeader, keys_host, out_host, keys_dev, out_dev, streams) -> None:
+    """sf_query_pipelined: the batch split over len(streams) CUDA streams (copy in, query, copy out
+    per part).  keys_host/out_host: pinned CPU tensors; keys_dev/out_dev: device staging tensors."""
+    n = out_host.numel()
+    arr = (ctypes.c_void_p * len(streams))(*[int(s.cuda_stream) for s in streams])
+    v = SlimView(_dev_ptr(slim, "slim"), hdr, 0, 0)
+    check(load().sf_query_pipelined(ctypes.byref(v), keys_host.data_ptr(), n, out_host.data_ptr(),
+                                    _dev_ptr(keys_dev, "keys_dev"), _dev_ptr(out_dev, "out_dev"), len(streams),
+                                    ctypes.cast(arr, ctypes.c_void_p)), "sf_query_pipelined")

@@ -245,6 +245,30 @@ sf_status sf_query_batch(const sf_slim_view* v, const void* keys_dev, uint64_t n
     return sfk::launch_query(q, sms, (cudaStream_t)cuda_stream) == cudaSuccess ? SF_OK : SF_ERR_CUDA;
 }
 
+sf_status sf_query_pipelined(const sf_slim_view* v, const void* keys_host, uint64_t n, uint32_t* out_host,
+                             void* keys_dev, uint32_t* out_dev, uint32_t n_streams, void* const* streams) {
+    if (!v || n_streams == 0 || !streams) return SF_ERR_INVALID;
+    if (n == 0) return SF_OK;
+    if (!keys_host || !out_host || !keys_dev || !out_dev) return SF_ERR_INVALID;
+    const uint64_t kb = v->hdr.key_bytes;
+    const uint64_t base = n / n_streams, extra = n % n_streams;
+    uint64_t off = 0;
+    for (uint32_t q = 0; q < n_streams; ++q) {
+        const uint64_t len = base + (q < extra ? 1 : 0);  // the first n % n_streams parts take one more
+        if (len == 0) continue;
+        cudaStream_t st = (cudaStream_t)streams[q];
+        const uint8_t* kh = (const uint8_t*)keys_host + off * kb;
+        uint8_t* kd = (uint8_t*)keys_dev + off * kb;
+        if (cudaMemcpyAsync(kd, kh, len * kb, cudaMemcpyHostToDevice, st) != cudaSuccess) return SF_ERR_CUDA;
+        const sf_status qs = sf_query_batch(v, kd, len, out_dev + off, st);
+        if (qs != SF_OK) return qs;
+        if (cudaMemcpyAsync(out_host + off, out_dev + off, len * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            return SF_ERR_CUDA;
+        off += len;
+    }
+    return SF_OK;
+}
+
 sf_status sf_sync(sf_sketch* s) {
     if (!s) return SF_ERR_INVALID;
     uint32_t err = 0;

@@ -196,3 +196,26 @@ def test_flows_zipf_sweep_mid_size(sf):
         g, o = _run_both(sf, 4, 1 << 12, 16, 13, 2, 65536, [(ins, None), (dels, "del")])
         _assert_same(g, o)
         _queries_match(sf, g, o, flows)
+
+
+def test_query_pipeline_splits_like_the_paper_and_matches(sf):
+    """Sec. 4.2.2 multi-stream pipeline: parts of nearly equal size over n streams (the first
+    b % n take one more); answers equal one sf_query_batch over the whole batch."""
+    import torch
+    st, ids = wl.mixed_stream(50_000, 8_000, 1.0, 0.2, 4, seed=91)
+    g = sf.Sketch(4, 2048, 16, 4, 3, 1000)
+    g.update(st.keys.cuda(), st.ops.cuda())
+    slim, hdr = g.export_slim()
+    g.sync()
+    keys = torch.cat([ids, ids[:1234]]).contiguous()
+    want = _np_u32(sf.query(slim, hdr, keys.cuda()))
+    for n_streams in (1, 3, 7, 16):
+        streams = [torch.cuda.Stream() for _ in range(n_streams)]
+        kh = keys.pin_memory()
+        oh = torch.zeros(keys.shape[0], dtype=torch.int32).pin_memory()
+        kd = torch.empty_like(keys, device="cuda")
+        od = torch.empty(keys.shape[0], dtype=torch.int32, device="cuda")
+        sf.query_pipelined(slim, hdr, kh, oh, kd, od, streams)
+        for s_ in streams:
+            s_.synchronize()
+        assert np.array_equal(oh.numpy().view(np.uint32), want), n_streams
