@@ -192,8 +192,12 @@ def main():
     ap.add_argument("--ref-queries", type=int, default=20_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["all", "flows", "batch", "serve", "accuracy", "pipeline"], default="all",
-                    help="all: the flows line with the batched and serving results embedded")
+    ap.add_argument("--workload", choices=["all", "flows", "batch", "serve", "accuracy", "pipeline", "profile"],
+                    default="all",
+                    help="all: the flows line with the batched and serving results embedded; profile: the small "
+                         "fixed case the committed ncu summaries capture (two insert launches, the second profiled)")
+    ap.add_argument("--profile-zipf", type=float, default=0.0)
+    ap.add_argument("--profile-inserts", type=int, default=2_000_000)
     ap.add_argument("--batch-sketches", type=int, default=1024)
     ap.add_argument("--serve-seconds", type=float, default=8.0)
     args = ap.parse_args()
@@ -239,6 +243,8 @@ def main():
         line = run_accuracy(args, ctx)
     if args.workload == "pipeline":
         line = run_pipeline(args, ctx)
+    if args.workload == "profile":
+        line = run_profile(args, ctx)
     if args.workload in ("all", "serve"):
         v = run_serve(args, ctx)
         if line is None:
@@ -523,6 +529,37 @@ def accuracy_report(inputs, dev, stream, n_sample=8_000_000):
         out[str(s)] = {k: round(v, 5) for k, v in row.items()}
     return {"sample": f"first {n_sample} inserts of each s plus deletes of 10% of them; all {N_FLOWS} flows queried",
             "per_s": out}
+
+
+def run_profile(args, ctx):
+    """The small case of the chunk kernel that ncu captures: one sketch of the flows shape
+    (d=4, w=2^18, z=16, 13-byte keys, chunk 65,536), `--profile-inserts` keys drawn with Zipf
+    `--profile-zipf` over 10^6 flows; a warm-up insert launch, the profiled insert launch
+    (launch index 1 of the chunk kernel), then deletes, export and queries.  Prints the
+    CUDA-event time of the second insert launch."""
+    import torch
+    import paper_1701_04148_gb300 as sf
+    import workloads as wl
+    ins, dels, flows = wl.flows_with_deletes(args.profile_inserts, N_FLOWS, args.profile_zipf, DEL_FRAC,
+                                             seed=2, device=ctx["dev"])
+    g = sf.Sketch(D, W, Z, KB, 2, S)
+    g.insert(ins)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(ctx["stream"])
+    g.insert(ins)
+    e1.record(ctx["stream"])
+    g.delete(dels)
+    slim, hdr = g.export_slim()
+    q = sf.query(slim, hdr, flows)
+    st = g.sync_status()
+    torch.cuda.synchronize()
+    if st != sf.SF_OK:
+        raise SystemExit(f"profile case failed: status {st}")
+    ms = e0.elapsed_time(e1)
+    g.close()
+    return {"workload": "profile", "inserts": int(ins.shape[0]), "zipf": args.profile_zipf,
+            "insert_ms": round(ms, 4), "M_inserts_per_s": round(ins.shape[0] / ms / 1e3, 1),
+            "query_mean": float(q.to(torch.float64).mean())}
 
 
 def run_accuracy(args, ctx):

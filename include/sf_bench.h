@@ -22,11 +22,15 @@ extern "C" {
 #define SF_BENCH_LOAD_CG   2u  /* 32-bit load bypassing L1               */
 #define SF_BENCH_RED_MAX   3u  /* atomicMax, result unused               */
 #define SF_BENCH_CAS       4u  /* atomicCAS, result used                 */
+#define SF_BENCH_MIX_RED_LD 5u /* even warps atomicAdd (result unused), odd warps 32-bit load bypassing
+                                  L1: the 1:1 read-modify-write / load mix of the sketch update (on a
+                                  GB300 this schedule measured above alternating the two in one thread) */
 
 /*
  * Issues total_ops random 32-bit operations of `kind` on buf_dev[0 .. n_words) (device,
- * n_words a power of two, caller-owned, contents overwritten) on cuda_stream.  Addresses come
- * from a 64-bit LCG per thread (uniform over the buffer).  grid_blocks = 0 picks 8 blocks of
+ * caller-owned, contents overwritten; n_words a power of two or at most 2^32, else
+ * SF_ERR_INVALID) on cuda_stream.  Addresses come from a 64-bit LCG per thread (uniform over the
+ * buffer).  grid_blocks = 0 picks 8 blocks of
  * 256 threads per SM.  The caller times the call with CUDA events.
  */
 sf_status sf_bench_random_access(uint32_t *buf_dev, uint64_t n_words, uint64_t total_ops, uint32_t kind,

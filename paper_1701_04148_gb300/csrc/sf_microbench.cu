@@ -6,21 +6,29 @@ namespace sfk {
 
 namespace {
 
-__global__ void __launch_bounds__(256) random_access_kernel(uint32_t* __restrict__ buf, uint64_t mask,
+// n_words a power of two: index = 40 LCG bits masked; otherwise (n_words <= 2^32) the top 32 bits
+// scaled to [0, n_words) by a multiply-shift.
+__global__ void __launch_bounds__(256) random_access_kernel(uint32_t* __restrict__ buf, uint64_t n_words,
                                                             uint64_t ops_per_thread, uint32_t kind,
                                                             uint32_t* __restrict__ sink) {
+    const bool pow2 = (n_words & (n_words - 1)) == 0;
+    const uint64_t mask = n_words - 1;
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     uint64_t x = tid * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
     uint32_t acc = 0;
 #pragma unroll 8
     for (uint64_t i = 0; i < ops_per_thread; ++i) {
         x = x * 6364136223846793005ull + 1442695040888963407ull;  // Knuth's MMIX LCG
-        const uint64_t idx = (x >> 24) & mask;
+        const uint64_t idx = pow2 ? ((x >> 24) & mask) : (((x >> 32) * n_words) >> 32);
         switch (kind) {
             case SF_BENCH_RED_ADD: atomicAdd(buf + idx, 1u); break;
             case SF_BENCH_ATOM_ADD: acc += atomicAdd(buf + idx, 1u); break;
             case SF_BENCH_LOAD_CG: acc += __ldcg(buf + idx); break;
             case SF_BENCH_RED_MAX: atomicMax(buf + idx, (uint32_t)(x >> 40)); break;
+            case SF_BENCH_MIX_RED_LD:  // odd warps load, even warps reduce
+                if (threadIdx.x & 32u) acc += __ldcg(buf + idx);
+                else atomicAdd(buf + idx, 1u);
+                break;
             default: acc += atomicCAS(buf + idx, 0u, (uint32_t)tid); break;
         }
     }
@@ -47,7 +55,8 @@ extern "C" {
 
 sf_status sf_bench_random_access(uint32_t* buf_dev, uint64_t n_words, uint64_t total_ops, uint32_t kind,
                                  uint32_t grid_blocks, void* cuda_stream) {
-    if (!buf_dev || n_words == 0 || (n_words & (n_words - 1)) != 0 || kind > SF_BENCH_CAS) return SF_ERR_INVALID;
+    if (!buf_dev || n_words == 0 || kind > SF_BENCH_MIX_RED_LD) return SF_ERR_INVALID;
+    if ((n_words & (n_words - 1)) != 0 && n_words > (1ull << 32)) return SF_ERR_INVALID;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -55,7 +64,7 @@ sf_status sf_bench_random_access(uint32_t* buf_dev, uint64_t n_words, uint64_t t
     const uint32_t grid = grid_blocks ? grid_blocks : (uint32_t)sms * 8u;
     const uint64_t threads = (uint64_t)grid * 256u;
     const uint64_t per = (total_ops + threads - 1) / threads;
-    sfk::random_access_kernel<<<grid, 256, 0, (cudaStream_t)cuda_stream>>>(buf_dev, n_words - 1, per, kind,
+    sfk::random_access_kernel<<<grid, 256, 0, (cudaStream_t)cuda_stream>>>(buf_dev, n_words, per, kind,
                                                                           buf_dev);
     return cudaGetLastError() == cudaSuccess ? SF_OK : SF_ERR_CUDA;
 }

@@ -175,24 +175,45 @@ struct MergeTable {
 };
 
 // What a claiming leader keeps in registers across the barrier (single-iteration rounds): its own
-// counts and the chunk-start minimum m of the key's Slim counters with its minimal-row mask.  Every
-// leader of a key reads the same chunk-start values, so other leaders only add their counts to the
-// dictionary entry (and store m and the mask when they insert).
+// counts and the chunk-start minimum m of the key's Slim counters with its minimal-row mask (and,
+// in insertion-only launches, its slack).  Every leader of a key reads the same chunk-start
+// values, so other leaders only add their counts to the dictionary entry (and store m, mask and
+// their own slack when they insert).
 struct OwnCounts {
-    uint32_t ci, cd, m, mask;
+    uint32_t ci, cd, m, mask_slack;
 };
 
-// Global part of phase 1 for one (block- or warp-) leader: Fat RED of the net count, dictionary
-// claim/lookup (one 128-bit CAS per probe), counts, chunk-start Slim minimum.  Returns the slot
-// this thread claimed, or kNoSlot.  With keep_own, a claimer leaves its counts, m and mask in *own
-// instead of writing them to the entry.
+// Slack of one leader in an insertion-only launch.  Its returning increments saw old_i on the
+// key's Fat counters and added ci, and counters only grow until the chunk ends, so
+// Fl = min_i (old_i + ci) <= F_e.  With sl = Fl - m (0 if negative, clipped to 24 bits),
+// c_ins <= sl implies m + c_ins <= F_e, i.e. T_e = m + c_ins without reading the Fat again.
+__device__ __forceinline__ uint32_t slack_of(uint32_t Fl, uint32_t m) {
+    if (Fl <= m) return 0u;
+    const uint32_t sl = Fl - m;
+    return sl < kSlackMax ? sl : kSlackMax;
+}
+
+// Global part of phase 1 for one (block- or warp-) leader: Fat increments of the net count,
+// dictionary claim/lookup (one 128-bit CAS per probe), counts, chunk-start Slim minimum.  Returns
+// the slot this thread claimed, or kNoSlot.  With keep_own, a claimer leaves its counts, m and
+// mask in *own instead of writing them to the entry.  In insertion-only launches (ins_only) the
+// Fat increments return the old values, which give the leader's slack.
 template <int D>
 __device__ __forceinline__ uint32_t phase1_global(const SketchRun& R, uint32_t* ctrl, const LaneWork<D>& L,
-                                                  uint32_t ci, uint32_t cd, bool keep_own, OwnCounts* own,
-                                                  unsigned long long keep, unsigned long long stream) {
+                                                  uint32_t ci, uint32_t cd, bool keep_own, bool ins_only,
+                                                  OwnCounts* own, unsigned long long keep,
+                                                  unsigned long long stream) {
     const SketchDesc& s = R.s;
     const int32_t net = (int32_t)ci - (int32_t)cd;
-    if (net != 0) {
+    // A single insertion takes the returning increment (it is the common leader of spread-out
+    // streams, whose claimer can then skip the chunk-end Fat read); a merged group of a hot key
+    // keeps the non-returning one, so the leader never waits on a serialised hot counter.
+    uint32_t Fl = 0u;  // 0: no slack
+    if (ins_only && ci == 1u) {
+        Fl = 0xFFFFFFFFu;
+#pragma unroll
+        for (int i = 0; i < D; ++i) Fl = min(Fl, atom_add_pol(fat_ptr(s, i, L.h[i], L.f[i]), 1u, keep) + 1u);
+    } else if (net != 0) {
 #pragma unroll
         for (int i = 0; i < D; ++i) red_add_pol(fat_ptr(s, i, L.h[i], L.f[i]), (uint32_t)net, keep);
     }
@@ -221,29 +242,50 @@ __device__ __forceinline__ uint32_t phase1_global(const SketchRun& R, uint32_t* 
         atomicOr(ctrl + kCtrlErr, kErrDictFull);
         return kNoSlot;
     }
-    uint32_t m = 0xFFFFFFFFu, mask = 0u;
+    uint32_t m = 0xFFFFFFFFu, ms = 0u;
     if (ci) {
 #pragma unroll
         for (int i = 0; i < D; ++i) m = min(m, av[i]);
 #pragma unroll
-        for (int i = 0; i < D; ++i) mask |= (av[i] == m ? 1u : 0u) << i;
+        for (int i = 0; i < D; ++i) ms |= (av[i] == m ? 1u : 0u) << i;
+        if (ins_only) ms |= slack_of(Fl, m) << 8;
     }
     if (claimed && keep_own) {
-        *own = OwnCounts{ci, cd, m, mask};
+        *own = OwnCounts{ci, cd, m, ms};
         return slot;
     }
     if (ci) {
         red_add_pol(&R.dict[slot].c_ins, ci, stream);
         // every such leader of this key stores the same chunk-start minimum and minimal-row mask
+        // (and a valid slack of its own)
         asm volatile("st.global.cg.L2::cache_hint.v2.u32 [%0], {%1, %2}, %3;" ::"l"(&R.dict[slot].m), "r"(m),
-                     "r"(mask), "l"(stream)
+                     "r"(ms), "l"(stream)
                      : "memory");
     }
     if (cd) red_add_pol(&R.dict[slot].c_del, cd, stream);
     return claimed ? slot : kNoSlot;
 }
 
-// Phase 2 for one distinct key of the chunk (its entry ep, indices h/f).
+// Fat estimate F_e = min_i B_i[h_i][f_i] of the chunk-end Fat.
+template <int D>
+__device__ __forceinline__ uint32_t fat_min(const SketchDesc& s, const uint32_t* h, const uint32_t* f,
+                                            unsigned long long keep) {
+    uint32_t F = 0xFFFFFFFFu;
+#pragma unroll
+    for (int i = 0; i < D; ++i) F = min(F, ld_cg_pol(fat_ptr(s, i, h[i], f[i]), keep));
+    return F;
+}
+
+// F_e, read only when the slack does not already settle T_e (c_ins > slack); otherwise F_e is
+// not needed and the maximum stands in for it (min(m + c_ins, max) = m + c_ins = T_e).
+template <int D>
+__device__ __forceinline__ uint32_t fat_estimate(const SketchDesc& s, const uint32_t* h, const uint32_t* f,
+                                                 uint32_t c_ins, uint32_t slack, unsigned long long keep) {
+    return c_ins > slack ? fat_min<D>(s, h, f, keep) : 0xFFFFFFFFu;
+}
+
+// Phase 2 for one distinct key of the chunk (its entry ep, indices h/f, Fat estimate F when it
+// inserts).
 //   raise: T = min(m + c_ins, F); a row whose chunk-start value A0_i >= T needs no atomicMax
 //          (its final value is >= T anyway because T <= the bucket maximum).  Rows with
 //          A0_i == m are known from the mask; when c_ins == 1 every other row has A0_i >= m + 1 >= T.
@@ -251,12 +293,9 @@ __device__ __forceinline__ uint32_t phase1_global(const SketchRun& R, uint32_t* 
 template <int D>
 __device__ __forceinline__ void phase2_key(const SketchDesc& s, uint32_t* ctrl, DictEntry* ep, const uint32_t* h,
                                            const uint32_t* f, uint32_t c_ins, uint32_t c_del, uint32_t m,
-                                           uint32_t mask, const uint32_t* Fv, unsigned long long keep,
+                                           uint32_t mask, uint32_t F, unsigned long long keep,
                                            unsigned long long stream) {
     if (c_ins) {
-        uint32_t F = 0xFFFFFFFFu;
-#pragma unroll
-        for (int i = 0; i < D; ++i) F = min(F, Fv[i]);
         const uint64_t mc = (uint64_t)m + c_ins;
         const uint32_t T = mc < (uint64_t)F ? (uint32_t)mc : F;
         if (T > m) {
@@ -296,10 +335,13 @@ __global__ void __launch_bounds__(kChunkBlock, 1) chunk_update_kernel(const __gr
     const SketchRun* runs = a.runs ? a.runs : &a.one;
     const unsigned long long pol_keep = l2_policy_keep(), pol_stream = l2_policy_stream();
     const uint32_t lane = threadIdx.x & 31u;
-    const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    // warps are numbered across blocks first, so a round shorter than the grid spreads over every SM
+    const uint64_t gwarp = (uint64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     // one warp-iteration per round: each lane claims at most one slot and keeps it in registers
     const bool single = 32ull * nwarps >= a.flat_len;
+    // every update of the launch is an insertion: Fat counters only grow within a chunk
+    const bool ins_only = a.may_ins && !a.may_del;
     uint4* stage = s_stage[threadIdx.x >> 5];
     unsigned long long target = (a.bar_base + 1ull) * gridDim.x;
     // the first flat slot of this warp lies in the same sketch every round
@@ -419,7 +461,8 @@ __global__ void __launch_bounds__(kChunkBlock, 1) chunk_update_kernel(const __gr
             }
             if (do_global) {
                 OwnCounts own;
-                const uint32_t slot = phase1_global<D>(R, a.ctrl, L, ci, cd, single, &own, pol_keep, pol_stream);
+                const uint32_t slot =
+                    phase1_global<D>(R, a.ctrl, L, ci, cd, single, ins_only, &own, pol_keep, pol_stream);
                 if (slot != kNoSlot) {
                     if (single) {
                         my_slot = slot;
@@ -447,16 +490,21 @@ __global__ void __launch_bounds__(kChunkBlock, 1) chunk_update_kernel(const __gr
             if (my_slot != kNoSlot) {
                 const SketchRun& R = runs[my_k];
                 DictEntry* ep = R.dict + my_slot;
-                // other leaders' contributions (c_ins, c_del, m, mask); the claimer's own are in my_own
+                // other leaders' contributions (c_ins, c_del, m, mask | slack); the claimer's own are
+                // in my_own
                 const uint4 cn = ld_cg_v4_pol(reinterpret_cast<const uint4*>(ep) + 1, pol_stream);
-                uint32_t Fv[D];
-                if (a.may_ins) {
-#pragma unroll
-                    for (int i = 0; i < D; ++i) Fv[i] = ld_cg_pol(fat_ptr(R.s, i, my_h[i], my_f[i]), pol_keep);
-                }
+                // The Fat reads overlap the entry read unless the claimer's own slack already
+                // settles T (insertion-only launches, no other leader of the key in the chunk: the
+                // common case); if other leaders' inserts exceed the combined slack, read it after.
+                const uint32_t own_sl = ins_only ? (my_own.mask_slack >> 8) : 0u;
+                const bool early = a.may_ins && (!ins_only || my_own.ci > own_sl);
+                uint32_t F = early ? fat_min<D>(R.s, my_h, my_f, pol_keep) : 0xFFFFFFFFu;
+                const uint32_t c_ins = my_own.ci + cn.x;
+                const uint32_t sl = ins_only ? max(own_sl, cn.w >> 8) : 0u;
+                if (!early && c_ins > sl) F = fat_estimate<D>(R.s, my_h, my_f, c_ins, sl, pol_keep);
                 const bool mine = my_own.ci != 0u;  // the claimer read the chunk-start Slim itself
-                phase2_key<D>(R.s, a.ctrl, ep, my_h, my_f, my_own.ci + cn.x, my_own.cd + cn.y, mine ? my_own.m : cn.z,
-                              mine ? my_own.mask : cn.w, Fv, pol_keep, pol_stream);
+                phase2_key<D>(R.s, a.ctrl, ep, my_h, my_f, c_ins, my_own.cd + cn.y, mine ? my_own.m : cn.z,
+                              (mine ? my_own.mask_slack : cn.w) & 0xFFu, F, pol_keep, pol_stream);
             }
         } else {
             const uint32_t nclaims = min(s_nclaims, a.claims_cap);
@@ -467,15 +515,13 @@ __global__ void __launch_bounds__(kChunkBlock, 1) chunk_update_kernel(const __gr
                 unsigned long long k0, k1, c01, c23;
                 ld_entry(ep, k0, k1, c01, c23);
                 const Key key{k0, k1 & ~kKeyTag};
-                uint32_t h[D], f[D], probe, Fv[D];
+                uint32_t h[D], f[D], probe;
                 key_indices<D>(R.s, key, h, f, &probe);
-                const uint32_t c_ins = (uint32_t)c01;
-                if (c_ins) {
-#pragma unroll
-                    for (int i = 0; i < D; ++i) Fv[i] = ld_cg_pol(fat_ptr(R.s, i, h[i], f[i]), pol_keep);
-                }
-                phase2_key<D>(R.s, a.ctrl, ep, h, f, c_ins, (uint32_t)(c01 >> 32), (uint32_t)c23,
-                              (uint32_t)(c23 >> 32), Fv, pol_keep, pol_stream);
+                const uint32_t c_ins = (uint32_t)c01, ms = (uint32_t)(c23 >> 32);
+                const uint32_t F = c_ins ? fat_estimate<D>(R.s, h, f, c_ins, ins_only ? (ms >> 8) : 0u, pol_keep)
+                                         : 0xFFFFFFFFu;
+                phase2_key<D>(R.s, a.ctrl, ep, h, f, c_ins, (uint32_t)(c01 >> 32), (uint32_t)c23, ms & 0xFFu, F,
+                              pol_keep, pol_stream);
             }
         }
 
