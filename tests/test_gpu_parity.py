@@ -86,6 +86,27 @@ def test_mixed_stream_u32(sf, S):
     _queries_match(sf, g, o, ids)
 
 
+@pytest.mark.parametrize("del_frac", [0.0, 0.02])
+@pytest.mark.parametrize("d,w,z", [(4, 97, 16), (3, 1 << 16, 8)])
+def test_one_at_a_time_windows(sf, del_frac, d, w, z):
+    """S = 1 on streams whose windows mostly hold no deletion (the precomputed-Fat path), with
+    deletion windows in between (the in-step path) and hot keys (several lanes on one counter).
+    w = 2^16 puts the Slim (768 KiB) beyond shared memory, so the steps run on global memory."""
+    st, ids = wl.mixed_stream(40_000, 1_500, 1.2, del_frac, 4, seed=int(del_frac * 100) + w)
+    g, o = _run_both(sf, d, w, z, 4, 9, 1, [(st.keys, st.ops)])
+    _assert_same(g, o)
+    _queries_match(sf, g, o, ids)
+
+
+@pytest.mark.parametrize("n", [1, 31, 32, 33, 64, 65, 97])
+def test_one_at_a_time_short_streams(sf, n):
+    """S = 1 on lengths around the 32-update window and the two-window key prefetch."""
+    st, ids = wl.mixed_stream(n, 7, 1.5, 0.0, 4, seed=n)
+    g, o = _run_both(sf, 4, 5, 3, 4, 1, 1, [(st.keys, st.ops), (st.keys[: n // 2 + 1], None)])
+    _assert_same(g, o)
+    _queries_match(sf, g, o, ids)
+
+
 @pytest.mark.parametrize("kb", [1, 3, 8, 13, 15])
 def test_key_widths(sf, kb):
     import torch
