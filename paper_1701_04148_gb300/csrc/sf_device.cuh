@@ -287,4 +287,51 @@ __device__ __forceinline__ uint32_t warp_min_u32(uint32_t v, uint32_t mask) {
     return __reduce_min_sync(mask, v);
 }
 
+// ---- counter addressing shared by the update kernels ---------------------------------------
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+__device__ __forceinline__ uint32_t* fat_ptr(const SketchDesc& s, uint32_t i, uint32_t h, uint32_t f) {
+    return s.B + ((uint64_t)i * s.w + h) * s.z + f;
+}
+
+__device__ __forceinline__ uint32_t* slim_ptr(const SketchDesc& s, uint32_t i, uint32_t h) {
+    return s.A + (uint64_t)i * s.w + h;
+}
+
+// max_k B_i[h][k] and whether B_i[h][f] went negative (strict-turnstile violation).
+__device__ __forceinline__ uint32_t bucket_max_cg(const SketchDesc& s, uint32_t i, uint32_t h,
+                                                  uint32_t f, bool* underflow,
+                                                  unsigned long long pol = 0ull, bool hinted = false) {
+    const uint32_t* bk = s.B + ((uint64_t)i * s.w + h) * s.z;
+    uint32_t mx = 0;
+    if ((s.z & 3u) == 0u) {
+        const uint4* b4 = reinterpret_cast<const uint4*>(bk);
+        for (uint32_t q = 0; q < (s.z >> 2); ++q) {
+            const uint4 v = hinted ? ld_cg_v4_pol(b4 + q, pol) : __ldcg(b4 + q);
+            mx = max(max(mx, v.x), max(v.y, max(v.z, v.w)));
+        }
+    } else {
+        for (uint32_t k = 0; k < s.z; ++k) mx = max(mx, hinted ? ld_cg_pol(bk + k, pol) : __ldcg(bk + k));
+    }
+    if ((int32_t)(hinted ? ld_cg_pol(bk + f, pol) : __ldcg(bk + f)) < 0) *underflow = true;
+    return mx;
+}
+
+// Indices of row i only (the sequential kernels take rows one at a time).
+__device__ __forceinline__ bool row_index(const SketchDesc& s, const Key& k, uint32_t i, uint32_t* h,
+                                          uint32_t* f) {
+    if (s.idx_table) {
+        if (k.x0 >= s.n_ids) return false;
+        const uint32_t* row = s.idx_table + (k.x0 * s.d + i) * 2;
+        *h = __ldg(row);
+        *f = __ldg(row + 1);
+        return *h < s.w && *f < s.z;
+    }
+    const uint64_t H = row_hash(k, s.key_bytes, s.rs[i]);
+    *h = reduce_hi(H, s.w);
+    *f = reduce_lo(H, s.z);
+    return true;
+}
+
 }  // namespace sfk
