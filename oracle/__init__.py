@@ -6,7 +6,9 @@ ctypes and shares no code with the CUDA library.
 
 Semantics (see ``sf_oracle.c`` for the full statement):
   * ``seq_apply``   -- the paper's one-update-at-a-time insertion (Sec. 3.4, SF_4 = SF_F
-                       insertion) and SF_F deletion (Sec. 3.5), literal or clamp form.
+                       insertion) and SF_F deletion (Sec. 3.5), literal or clamp form; or, with
+                       ``delete_rule="sf4"``, the SF_4 deletion (Sec. 3.4: decrement by 1 above
+                       the bucket sum), kept for the ablation against SF_F.
   * ``chunk_apply`` -- the chunked schedule CHUNK(S), stream order inside each chunk.
   * ``query``       -- min over the d hashed Slim counters (Sec. 3.1 "Query").
 """
@@ -81,6 +83,10 @@ def _configure(L):
     L.osf_seq_apply.restype = None
     L.osf_seq_apply.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, u32p, u32p,
                                 u32p, u32p, i8p, ctypes.c_uint64, ctypes.c_int]
+    L.osf_chunk_apply_rule.restype = ctypes.c_int
+    L.osf_chunk_apply_rule.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, u32p, u32p,
+                                       u32p, u32p, i8p, ctypes.c_uint64, ctypes.c_uint64,
+                                       u8p, ctypes.c_uint32, ctypes.c_int]
     L.osf_chunk_apply.restype = ctypes.c_int
     L.osf_chunk_apply.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, u32p, u32p,
                                   u32p, u32p, i8p, ctypes.c_uint64, ctypes.c_uint64,
@@ -123,25 +129,31 @@ def index_keys(keys: np.ndarray, seed: int, d: int, w: int, z: int):
 
 
 class Sketch:
-    """Oracle state: Slim A (d, w) and Fat B (d, w, z), uint32, all zero at init (Sec. 3.1)."""
+    """Oracle state: Slim A (d, w) and Fat B (d, w, z), uint32, all zero at init (Sec. 3.1).
+    delete_rule: "sff" (Sec. 3.5, the final design) or "sf4" (Sec. 3.4)."""
 
-    def __init__(self, d: int, w: int, z: int, key_bytes: int = 4, seed: int = 0):
+    def __init__(self, d: int, w: int, z: int, key_bytes: int = 4, seed: int = 0, delete_rule: str = "sff"):
+        if delete_rule not in ("sff", "sf4"):
+            raise ValueError("delete_rule must be 'sff' or 'sf4'")
         self.d, self.w, self.z, self.key_bytes, self.seed = d, w, z, key_bytes, seed
+        self.delete_rule = delete_rule
         self.A = np.zeros((d, w), dtype=np.uint32)
         self.B = np.zeros((d, w, z), dtype=np.uint32)
 
     def copy(self) -> "Sketch":
-        s = Sketch(self.d, self.w, self.z, self.key_bytes, self.seed)
+        s = Sketch(self.d, self.w, self.z, self.key_bytes, self.seed, self.delete_rule)
         s.A[...] = self.A
         s.B[...] = self.B
         return s
 
     # -- index-level calls -------------------------------------------------------
     def seq_apply(self, h, f, ops, literal: bool = True) -> None:
+        """SEQ semantics.  SF_F deletes: literal rule or the clamp form; SF_4: its literal rule."""
         h, f, ops = _prep(h, f, ops, self.d)
+        rule = 2 if self.delete_rule == "sf4" else (1 if literal else 0)
         lib().osf_seq_apply(self.d, self.w, self.z, _p(self.A, ctypes.c_uint32), _p(self.B, ctypes.c_uint32),
                             _p(h, ctypes.c_uint32), _p(f, ctypes.c_uint32), _p(ops, ctypes.c_int8),
-                            len(ops), 1 if literal else 0)
+                            len(ops), rule)
 
     def chunk_apply(self, h, f, ops, S: int, ident: np.ndarray) -> None:
         h, f, ops = _prep(h, f, ops, self.d)
@@ -149,10 +161,11 @@ class Sketch:
             return
         ident = np.ascontiguousarray(ident).view(np.uint8).reshape(len(ops), -1)
         ident = np.ascontiguousarray(ident)
-        rc = lib().osf_chunk_apply(self.d, self.w, self.z, _p(self.A, ctypes.c_uint32),
-                                   _p(self.B, ctypes.c_uint32), _p(h, ctypes.c_uint32), _p(f, ctypes.c_uint32),
-                                   _p(ops, ctypes.c_int8), len(ops), S,
-                                   _p(ident, ctypes.c_uint8), ident.shape[1] if len(ops) else 1)
+        rc = lib().osf_chunk_apply_rule(self.d, self.w, self.z, _p(self.A, ctypes.c_uint32),
+                                        _p(self.B, ctypes.c_uint32), _p(h, ctypes.c_uint32),
+                                        _p(f, ctypes.c_uint32), _p(ops, ctypes.c_int8), len(ops), S,
+                                        _p(ident, ctypes.c_uint8), ident.shape[1] if len(ops) else 1,
+                                        1 if self.delete_rule == "sf4" else 0)
         if rc != 0:
             raise ValueError("osf_chunk_apply failed (bad arguments or out of memory)")
 

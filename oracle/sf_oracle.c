@@ -17,6 +17,9 @@
  *   - deletion (SF_F, Sec. 3.5 "Deletion"):
  *       B_i[h_i(e)][f_i(e)] -= 1; for each row i, if max_k B_i[h_i(e)][k] changed, then
  *       A_i[h_i(e)] is lowered to that maximum when it is larger; otherwise unchanged.
+ *   - deletion, SF_4 variant (Sec. 3.4 "Deletion", kept for the ablation against SF_F):
+ *       B_i[h_i(e)][f_i(e)] -= 1 for all i; then for each row i, A_i[h_i(e)] is decremented by 1
+ *       when it is larger than the bucket sum sum_k B_i[h_i(e)][k].
  *   - query (Sec. 3.1 "Query"): min_i A_i[h_i(e)], Slim only.
  *
  * Indices are 0-based here (the paper is 1-based).  Counters are uint32 and wrap on
@@ -40,6 +43,9 @@
  *               With S = 1 this reduces to SEQ (the raise max(A, min(m+1, F)) increments exactly
  *               the minimal rows when m < F; the clamp equals the literal delete rule because
  *               A_i[j] <= max_k B_i[j][k] always holds, Appendix I).
+ *               SF_4 variant: step 3 takes the chunk-end bucket sum SUM_i = sum_k B1_i[h_i(e)][k]
+ *               and step 4's delete does A_i[h_i(e)] -= 1 when A_i[h_i(e)] > SUM_i; with S = 1
+ *               this is the SF_4 rule itself.
  *
  * Hash functions (the paper only asks for independent uniform h_i, f_i; this is a reading):
  *   row seeds s_0..s_{d-1} are the first d outputs of SplitMix64 started at the sketch seed
@@ -124,6 +130,14 @@ static inline uint32_t *fat_at(uint32_t *B, uint32_t w, uint32_t z, uint32_t i, 
     return &B[((uint64_t)i * w + j) * z + k];
 }
 
+/* Sum of a bucket's z counters (64-bit: z counters of 32 bits each). */
+static uint64_t bucket_sum(uint32_t *B, uint32_t w, uint32_t z, uint32_t i, uint32_t j)
+{
+    uint64_t s = 0;
+    for (uint32_t k = 0; k < z; k++) s += *fat_at(B, w, z, i, j, k);
+    return s;
+}
+
 static uint32_t bucket_max(uint32_t *B, uint32_t w, uint32_t z, uint32_t i, uint32_t j)
 {
     uint32_t mx = 0;
@@ -137,8 +151,9 @@ static uint32_t bucket_max(uint32_t *B, uint32_t w, uint32_t z, uint32_t i, uint
 /*
  * SEQ semantics, one update at a time, in stream order.
  * h, f: n*d indices; ops: +1 insert, -1 delete.
- * literal_delete != 0: the paper's delete rule with its "if the maximum changed" test;
- * literal_delete == 0: unconditional clamp A_i = min(A_i, max_k B_i[h][k]).
+ * literal_delete == 1: the paper's SF_F delete rule with its "if the maximum changed" test;
+ * literal_delete == 0: unconditional clamp A_i = min(A_i, max_k B_i[h][k]);
+ * literal_delete == 2: the SF_4 delete rule (decrement by 1 above the bucket sum).
  */
 void osf_seq_apply(uint32_t d, uint32_t w, uint32_t z, uint32_t *A, uint32_t *B,
                    const uint32_t *h, const uint32_t *f, const int8_t *ops, uint64_t n,
@@ -168,6 +183,13 @@ void osf_seq_apply(uint32_t d, uint32_t w, uint32_t z, uint32_t *A, uint32_t *B,
                     uint32_t *a = slim_at(A, w, i, ht[i]);
                     if (*a == m) *a = m + 1u;
                 }
+            }
+        } else if (ops[t] < 0 && literal_delete == 2) {
+            for (uint32_t i = 0; i < d; i++)
+                *fat_at(B, w, z, i, ht[i], ft[i]) -= 1u;
+            for (uint32_t i = 0; i < d; i++) {
+                uint32_t *a = slim_at(A, w, i, ht[i]);
+                if ((uint64_t)*a > bucket_sum(B, w, z, i, ht[i])) *a -= 1u;
             }
         } else if (ops[t] < 0) {
             if (literal_delete) {
@@ -213,12 +235,14 @@ static int cmp_ident(const void *pa, const void *pb)
 /*
  * CHUNK(S) semantics (defined in the header comment).  ident: the key identity of every
  * update (the key bytes themselves, or a key id in explicit-index mode), used to find the
- * distinct keys of a chunk and their insert counts c_e.  Returns 0, or -1 on bad arguments
- * or allocation failure.
+ * distinct keys of a chunk and their insert counts c_e.  delete_rule 0: SF_F (a delete
+ * clamps to the chunk-end bucket maximum M_i); delete_rule 1: SF_4 (a delete decrements by 1
+ * when above the chunk-end bucket sum, read as a 32-bit bound: a sum of 2^32 or more is never
+ * exceeded).  Returns 0, or -1 on bad arguments or allocation failure.
  */
-int osf_chunk_apply(uint32_t d, uint32_t w, uint32_t z, uint32_t *A, uint32_t *B,
-                    const uint32_t *h, const uint32_t *f, const int8_t *ops, uint64_t n,
-                    uint64_t S, const uint8_t *ident, uint32_t ident_bytes)
+int osf_chunk_apply_rule(uint32_t d, uint32_t w, uint32_t z, uint32_t *A, uint32_t *B,
+                         const uint32_t *h, const uint32_t *f, const int8_t *ops, uint64_t n,
+                         uint64_t S, const uint8_t *ident, uint32_t ident_bytes, int delete_rule)
 {
     if (S == 0 || d == 0 || w == 0 || z == 0) return -1;
     if (n == 0) return 0;
@@ -271,11 +295,18 @@ int osf_chunk_apply(uint32_t d, uint32_t w, uint32_t z, uint32_t *A, uint32_t *B
             g0 = g1;
         }
 
-        /* 3. Clamp bounds of the delete occurrences, from the chunk-end Fat. */
+        /* 3. Bounds of the delete occurrences, from the chunk-end Fat. */
         for (uint64_t t = c0; t < c0 + len; t++)
             if (ops[t] < 0)
                 for (uint32_t i = 0; i < d; i++)
                     M[(t - c0) * d + i] = bucket_max(B, w, z, i, h[t * d + i]);
+        if (delete_rule == 1)
+            for (uint64_t t = c0; t < c0 + len; t++)
+                if (ops[t] < 0)
+                    for (uint32_t i = 0; i < d; i++) {
+                        uint64_t sb = bucket_sum(B, w, z, i, h[t * d + i]);
+                        M[(t - c0) * d + i] = sb > UINT32_MAX ? UINT32_MAX : (uint32_t)sb;
+                    }
 
         /* 4. Slim ops per counter in stream order. */
         for (uint64_t t = c0; t < c0 + len; t++) {
@@ -285,13 +316,25 @@ int osf_chunk_apply(uint32_t d, uint32_t w, uint32_t z, uint32_t *A, uint32_t *B
                     if (*a < T[t - c0]) *a = T[t - c0];
                 } else if (ops[t] < 0) {
                     uint32_t mb = M[(t - c0) * d + i];
-                    if (*a > mb) *a = mb;
+                    if (delete_rule == 1) {
+                        if (*a > mb) *a -= 1u;
+                    } else if (*a > mb) {
+                        *a = mb;
+                    }
                 }
             }
         }
     }
     free(order); free(T); free(M); free(A0);
     return 0;
+}
+
+/* CHUNK(S) with the SF_F delete rule. */
+int osf_chunk_apply(uint32_t d, uint32_t w, uint32_t z, uint32_t *A, uint32_t *B,
+                    const uint32_t *h, const uint32_t *f, const int8_t *ops, uint64_t n,
+                    uint64_t S, const uint8_t *ident, uint32_t ident_bytes)
+{
+    return osf_chunk_apply_rule(d, w, z, A, B, h, f, ops, n, S, ident, ident_bytes, 0);
 }
 
 /* Point query on a Slim-subsketch: out[t] = min_i A_i[h_i]. */

@@ -30,6 +30,15 @@ MUTATIONS = [
     ("mix-wrong-shift", "z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;", "z = (z ^ (z >> 28)) * 0x94D049BB133111EBULL;"),
     ("query-max", "if (v < m) m = v;\n        }\n        out[t] = m;", "if (m == UINT32_MAX || v > m) m = v;\n        }\n        out[t] = m;"),
     ("fat-transposed-index", "return &B[((uint64_t)i * w + j) * z + k];", "return &B[((uint64_t)i * z + k) * w + j];"),
+    ("sf4-decrement-at-equality", "if ((uint64_t)*a > bucket_sum(B, w, z, i, ht[i])) *a -= 1u;",
+     "if ((uint64_t)*a >= bucket_sum(B, w, z, i, ht[i])) *a -= 1u;"),
+    ("sf4-bound-is-max", "if ((uint64_t)*a > bucket_sum(B, w, z, i, ht[i])) *a -= 1u;",
+     "if (*a > bucket_max(B, w, z, i, ht[i])) *a -= 1u;"),
+    ("sf4-sum-drops-a-slot", "for (uint32_t k = 0; k < z; k++) s += *fat_at(B, w, z, i, j, k);",
+     "for (uint32_t k = 1; k < z; k++) s += *fat_at(B, w, z, i, j, k);"),
+    ("sf4-chunk-bound-is-max", "uint64_t sb = bucket_sum(B, w, z, i, h[t * d + i]);",
+     "uint64_t sb = bucket_max(B, w, z, i, h[t * d + i]);"),
+    ("sf4-chunk-clamps-to-zero", "if (*a > mb) *a -= 1u;", "if (*a > mb) *a = 0u;"),
 ]
 
 
@@ -51,6 +60,10 @@ def _pins_pass() -> bool:
         lambda: pins.test_chunk_equals_its_order_free_closed_form(0),
         pins.test_zero_length_and_edge_shapes,
         pins.test_chunk_hand_derived_single_counter,
+        pins.test_sf4_hand_derived_bucket,
+        lambda: pins.test_sf4_chunk_size_one_is_sequential(0),
+        lambda: pins.test_sf4_slim_below_bucket_sum_and_no_underestimation(7),
+        lambda: pins.test_sf4_decrement_is_a_clamp_to_the_bucket_sum(13),
     ]
     for c in checks:
         try:

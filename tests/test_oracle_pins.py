@@ -470,3 +470,114 @@ def test_chunk_hand_derived_single_counter():
     for keys, ops, S, want_a, want_b in steps:
         sk.update(_key_bytes(np.array(keys, np.uint32)), np.array(ops, np.int8), S=S)
         assert int(sk.A[0, 0]) == want_a and int(sk.B[0, 0, 0]) == want_b, (keys, ops)
+
+
+# ---------------------------------------------------------------------------------------
+# SF_4 delete rule (Sec. 3.4), the ablation next to SF_F: decrement A_i[h_i(e)] by 1 when it
+# is above the bucket sum after the Fat decrement
+# ---------------------------------------------------------------------------------------
+
+def _bucket_sum(sk):
+    return sk.B.astype(np.uint64).sum(axis=2)
+
+
+def test_sf4_hand_derived_bucket():
+    """d = w = 1, z = 2; e1 lives in slot 0, e2 in slot 1.  Values worked out by hand from the
+    Sec. 3.4 rules: ins e1 (A 1), ins e1 (A 2), ins e2 (Bmin 1 <= m 2: no raise), del e1 (bucket
+    sum 2, A = 2 is not above it: stays 2; SF_F clamps to the maximum 1), del e1 (sum 1: A 2 -> 1)."""
+    h = np.zeros((5, 1), np.uint32)
+    f = np.array([[0], [0], [1], [0], [0]], np.uint32)
+    ops = np.array([1, 1, 1, -1, -1], np.int8)
+    for rule, want in (("sf4", [1, 2, 2, 2, 1]), ("sff", [1, 2, 2, 1, 1])):
+        sk = Sketch(1, 1, 2, 4, 0, delete_rule=rule)
+        got = []
+        for t in range(5):
+            sk.seq_apply(h[t:t + 1], f[t:t + 1], ops[t:t + 1])
+            got.append(int(sk.A[0, 0]))
+        assert got == want, (rule, got)
+        assert sk.B[0, 0].tolist() == [0, 1]
+    # CHUNK(2) on the same stream: chunks {ins e1, ins e1}, {ins e2, del e1}, {del e1}.
+    #   chunk 1: B1 = [2, 0], T(e1) = min(0 + 2, 2) = 2 -> A 2
+    #   chunk 2: B1 = [1, 1], T(e2) = min(2 + 1, 1) = 1; delete bound: SF_4 sum 2 (A stays 2),
+    #            SF_F max 1 (A -> 1)
+    #   chunk 3: B1 = [0, 1], bound 1 for both: A -> 1
+    ident = np.array([1, 1, 2, 1, 1], np.uint32).view(np.uint8).reshape(-1, 4)
+    for rule, want in (("sf4", [2, 2, 1]), ("sff", [2, 1, 1])):
+        sk = Sketch(1, 1, 2, 4, 0, delete_rule=rule)
+        got = []
+        for c0, c1 in ((0, 2), (2, 4), (4, 5)):
+            sk.chunk_apply(h[c0:c1], f[c0:c1], ops[c0:c1], 2, ident[c0:c1])
+            got.append(int(sk.A[0, 0]))
+        assert got == want, (rule, got)
+
+
+@pytest.mark.parametrize("S", [None, 1, 64])
+def test_sf4_without_deletions_equals_sff(S):
+    """SF_4 and SF_F share the insertion rule (Sec. 3.4, 3.5): with no deletion they agree."""
+    rng = np.random.default_rng(7)
+    ids, ops, _ = _turnstile(rng, 4000, 400, 0.0, zipf_a=1.2)
+    keys = _key_bytes(ids)
+    a = Sketch(4, 40, 4, 4, 3, delete_rule="sf4")
+    b = Sketch(4, 40, 4, 4, 3, delete_rule="sff")
+    a.update(keys, ops, S=S)
+    b.update(keys, ops, S=S)
+    assert np.array_equal(a.A, b.A) and np.array_equal(a.B, b.B)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_sf4_chunk_size_one_is_sequential(seed):
+    rng = np.random.default_rng(40 + seed)
+    ids, ops, _ = _turnstile(rng, 3000, 300, 0.3, zipf_a=1.3)
+    keys = _key_bytes(ids)
+    a = Sketch(4, 64, 4, 4, seed, delete_rule="sf4")
+    b = a.copy()
+    a.update(keys, ops, S=None)
+    b.update(keys, ops, S=1)
+    assert np.array_equal(a.A, b.A) and np.array_equal(a.B, b.B)
+
+
+@pytest.mark.parametrize("S", [None, 1, 7, 256])
+def test_sf4_slim_below_bucket_sum_and_no_underestimation(S):
+    """Sec. 3.4 states that a Slim counter never exceeds the sum of its Fat bucket; the SF_F
+    no-under-estimation proof (Appendix II) carries over with the bucket sum in place of the
+    bucket maximum (sum >= max >= every item's Fat counter).  Checked after every chunk."""
+    rng = np.random.default_rng(55)
+    ids, ops, _ = _turnstile(rng, 4000, 600, 0.35, zipf_a=1.1)
+    keys = _key_bytes(ids)
+    sk = Sketch(3, 30, 4, 4, 11, delete_rule="sf4")
+    step = S or 1
+    live = np.zeros(600, np.int64)
+    for c0 in range(0, len(ops), step if S else 1):
+        c1 = min(len(ops), c0 + step)
+        sk.update(keys[c0:c1], ops[c0:c1], S=S)
+        np.add.at(live, ids[c0:c1].astype(np.int64), ops[c0:c1].astype(np.int64))
+        assert (sk.A.astype(np.uint64) <= _bucket_sum(sk)).all()
+    q = sk.query(_key_bytes(np.arange(600, dtype=np.uint32))).astype(np.int64)
+    assert (q >= live).all()
+
+
+@pytest.mark.parametrize("S", [None, 1, 13, 500])
+def test_sf4_decrement_is_a_clamp_to_the_bucket_sum(S):
+    """Because A <= bucket sum holds before every deletion (Sec. 3.4), "decrement by 1 when
+    above the sum after the Fat decrement" lowers A exactly to that sum: the SF_4 deletion is
+    the SF_F clamp with the bucket sum in place of the bucket maximum.  Checked after each
+    chunk: every Slim counter that went down equals its bucket sum, and only counters that a
+    deletion in the chunk hashed to went down."""
+    rng = np.random.default_rng(77)
+    ids, ops, _ = _turnstile(rng, 3000, 300, 0.4, zipf_a=1.3)
+    keys = _key_bytes(ids)
+    sk = Sketch(2, 16, 3, 4, 5, delete_rule="sf4")
+    h, _ = sk.index(keys)
+    step = S or 1
+    for c0 in range(0, len(ops), step):
+        c1 = min(len(ops), c0 + step)
+        before = sk.A.copy()
+        sk.update(keys[c0:c1], ops[c0:c1], S=S)
+        lowered = sk.A < before
+        assert (sk.A[lowered].astype(np.uint64) == _bucket_sum(sk)[lowered]).all()
+        # a counter can only go down through a deletion of a key hashed to it in this chunk
+        touched = np.zeros_like(lowered)
+        for t in range(c0, c1):
+            if ops[t] < 0:
+                touched[np.arange(sk.d), h[t]] = True
+        assert not (lowered & ~touched).any()
