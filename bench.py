@@ -132,16 +132,25 @@ def l2_random_peaks(L, dev, stream):
     return out
 
 
+CHUNK_KERNEL_SOURCES = ("sf_update.cu", "sf_device.cuh", "sf_internal.h")
+
+
+def chunk_kernel_source_sha256():
+    """sha256 over the files the chunk kernel is compiled from, in CHUNK_KERNEL_SOURCES order."""
+    h = hashlib.sha256()
+    for name in CHUNK_KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_1701_04148_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()
+
+
 def traffic_record():
     """DRAM bytes per update of the chunk kernel from the committed ncu summary, if the kernel
-    source has not changed since the counters were taken."""
+    sources have not changed since the counters were taken."""
     p = os.path.join(ROOT, "profiles", "chunk_update_kernel_traffic.json")
     if not os.path.exists(p):
         return None
     rec = json.load(open(p))
-    src = os.path.join(ROOT, "paper_1701_04148_gb300", "csrc", "sf_update.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    return rec if rec.get("kernel_source_sha256") == sha else None
+    return rec if rec.get("kernel_source_sha256") == chunk_kernel_source_sha256() else None
 
 
 # ------------------------------------------------------------------------------------------
@@ -219,10 +228,15 @@ def main():
                     help="all: the flows line with the batched and serving results embedded; profile: the small "
                          "fixed case the committed ncu summaries capture (two insert launches, the second profiled)")
     ap.add_argument("--profile-zipf", type=float, default=0.0)
+    ap.add_argument("--print-kernel-sha", action="store_true",
+                    help="print the chunk kernel's source hash (the key of the committed traffic record) and exit")
     ap.add_argument("--profile-inserts", type=int, default=2_000_000)
     ap.add_argument("--batch-sketches", type=int, default=1024)
     ap.add_argument("--serve-seconds", type=float, default=8.0)
     args = ap.parse_args()
+    if args.print_kernel_sha:
+        print(chunk_kernel_source_sha256())
+        return 0
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_env()
 
@@ -591,7 +605,10 @@ def run_accuracy(args, ctx):
     fraction of items with RE < 1 % after the insertions (Fig. CDF-RE), ARE after every 1,000,000
     insertions and after every 1,000,000 deletions, for the paper's one-at-a-time semantics
     (chunk 1) and the chunked semantics (chunk 65,536).  The paper reports 74.51 % (uniform) and
-    74.30 % (skewed) of items below 1 % RE for SF-sketch (Sec. 5.2.1, 5.2.2)."""
+    74.30 % (skewed) of items below 1 % RE for SF-sketch (Sec. 5.2.1, 5.2.2).  The same runs with
+    the SF_4 deletion rule (Sec. 3.4: clamp to the bucket sum, not the maximum) give the ablation
+    against SF_F: the insertion phase is identical, the deletion phase shows what SF_F's tighter
+    bound buys."""
     import torch
 
     import paper_1701_04148_gb300 as sf
@@ -607,8 +624,9 @@ def run_accuracy(args, ctx):
         sid, order = torch.sort(idv)
         pos = order[torch.searchsorted(sid, kid)]           # item index of every insertion
         res = {}
-        for sem, S_ in (("seq", 1), ("chunk", 65536)):
-            g = sf.Sketch(d, w, z, 4, 11, S_, stream=stream)
+        for sem, S_, rule in (("seq", 1, "sff"), ("chunk", 65536, "sff"), ("sf4_seq", 1, "sf4"),
+                              ("sf4_chunk", 65536, "sf4")):
+            g = sf.Sketch(d, w, z, 4, 11, S_, stream=stream, delete_rule=rule)
             f = torch.zeros(n_items, dtype=torch.int64, device=dev)
             are_ins, are_del = [], []
 

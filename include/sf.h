@@ -69,6 +69,13 @@ typedef int32_t sf_status;
 
 /* params.flags */
 #define SF_FLAG_EXPLICIT_INDEX 1u    /* keys are uint32 ids into a table of (h_i, f_i)    */
+#define SF_FLAG_SF4_DELETE     2u    /* deletions follow the SF_4 rule (Sec. 3.4): A_i[h_i] is
+                                        decremented by 1 when above the bucket SUM
+                                        sum_k B_i[h_i][k] after the Fat decrement, instead of
+                                        SF_F's clamp to the bucket maximum (Sec. 3.5).  Kept for
+                                        the ablation against SF_F; insertions and queries are
+                                        the same.  Chunked updates apply it as a clamp to the
+                                        chunk-end bucket sum (equal, since A <= sum holds)   */
 
 typedef struct sf_params {
     uint32_t d;          /* rows, 1..SF_MAX_D                                   (Table 1: d) */
@@ -318,7 +325,8 @@ sf_status sfc_destroy(sfc *c);
  * The per-chunk dictionary and control words live in one fixed device array of this library
  * (2 MiB + 256 B), which every GPU that loads the library keeps until the process exits.  Hence:
  *   - params->chunk must be 2..SF_NOALLOC_MAX_CHUNK; larger chunks return SF_ERR_INVALID (the
- *     array is sized for that maximum), as do explicit-index flags;
+ *     array is sized for that maximum), as do explicit-index flags (SF_FLAG_SF4_DELETE is
+ *     accepted);
  *   - all calls share the array, so calls that may overlap on the GPU (different streams,
  *     different threads) race and corrupt each other's result: serialise them;
  *   - the call zeroes the array's control words and dictionary itself before its kernel runs;

@@ -29,6 +29,7 @@ SF_ERR_BUDGET = -6
 SF_ERR_VERSION = -7
 SF_PENDING = 1
 SF_FLAG_EXPLICIT_INDEX = 1
+SF_FLAG_SF4_DELETE = 2
 SF_SLIM_MAGIC = 0x4D494C53
 SF_HASH_SPLITMIX_LEMIRE = 1
 SF_HASH_EXPLICIT = 2
@@ -194,13 +195,17 @@ class Sketch:
     """One SF-sketch on the current CUDA device, buffers owned by torch tensors."""
 
     def __init__(self, d: int, w: int, z: int, key_bytes: int = 4, seed: int = 0, chunk: int = 1,
-                 explicit_index: bool = False, stream=None, device=None):
+                 explicit_index: bool = False, stream=None, device=None, delete_rule: str = "sff"):
+        """delete_rule: "sff" (Sec. 3.5, the final design) or "sf4" (Sec. 3.4, the ablation)."""
         torch = _torch()
         L = load()
+        if delete_rule not in ("sff", "sf4"):
+            raise ValueError("delete_rule must be 'sff' or 'sf4'")
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device: the SF-sketch library has no CPU path")
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
-        self.params = make_params(d, w, z, key_bytes, seed, chunk, SF_FLAG_EXPLICIT_INDEX if explicit_index else 0)
+        flags = (SF_FLAG_EXPLICIT_INDEX if explicit_index else 0) | (SF_FLAG_SF4_DELETE if delete_rule == "sf4" else 0)
+        self.params = make_params(d, w, z, key_bytes, seed, chunk, flags)
         fb, sb, xb = required_bytes(self.params)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         with torch.cuda.device(self.device):

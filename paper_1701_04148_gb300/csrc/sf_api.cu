@@ -32,7 +32,7 @@ bool params_ok(const sf_params* p) {
     if (p->z < 1 || p->z > SF_MAX_Z) return false;
     if (p->key_bytes < 1 || p->key_bytes > SF_MAX_KEY_BYTES) return false;
     if (p->chunk < 1 || p->chunk > SF_MAX_CHUNK) return false;
-    if ((p->flags & ~SF_FLAG_EXPLICIT_INDEX) != 0) return false;
+    if ((p->flags & ~(SF_FLAG_EXPLICIT_INDEX | SF_FLAG_SF4_DELETE)) != 0) return false;
     if ((p->flags & SF_FLAG_EXPLICIT_INDEX) && p->key_bytes != 4) return false;
     if ((uint64_t)p->d * p->w * p->z > (1ull << 40)) return false;
     return true;
@@ -51,6 +51,7 @@ sfk::SketchDesc desc_of(const sf_sketch* s) {
     for (int i = 0; i < SF_MAX_D; ++i) d.rs[i] = s->rs[i];
     d.idx_table = s->idx_table;
     d.n_ids = s->n_ids;
+    d.sf4_delete = (s->p.flags & SF_FLAG_SF4_DELETE) ? 1u : 0u;
     return d;
 }
 

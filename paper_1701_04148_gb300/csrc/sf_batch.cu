@@ -133,6 +133,7 @@ sf_status sf_batch_update(sf_batch* b, uint32_t n_items, const sf_batch_item* it
         R.s.z = s->p.z;
         R.s.key_bytes = s->p.key_bytes;
         for (int r = 0; r < SF_MAX_D; ++r) R.s.rs[r] = s->rs[r];
+        R.s.sf4_delete = (s->p.flags & SF_FLAG_SF4_DELETE) ? 1u : 0u;
         R.keys = (const uint8_t*)items[i].keys_dev;
         R.ops = items[i].ops_dev;
         R.op_const = 1;

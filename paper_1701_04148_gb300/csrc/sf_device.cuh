@@ -48,6 +48,7 @@ struct SketchDesc {
     uint64_t rs[kMaxD];      // row seeds
     const uint32_t* idx_table;  // explicit-index mode table, else nullptr
     uint32_t n_ids;
+    uint32_t sf4_delete;     // nonzero: deletions clamp to the bucket sum (SF_4), else to the maximum (SF_F)
 };
 
 __device__ __forceinline__ uint64_t mix64(uint64_t x) {
@@ -299,22 +300,32 @@ __device__ __forceinline__ uint32_t* slim_ptr(const SketchDesc& s, uint32_t i, u
     return s.A + (uint64_t)i * s.w + h;
 }
 
-// max_k B_i[h][k] and whether B_i[h][f] went negative (strict-turnstile violation).
-__device__ __forceinline__ uint32_t bucket_max_cg(const SketchDesc& s, uint32_t i, uint32_t h,
-                                                  uint32_t f, bool* underflow,
-                                                  unsigned long long pol = 0ull, bool hinted = false) {
+// The bound a deletion clamps Slim counter A_i[h] to, from the Fat bucket B_i[h][.]: its maximum
+// max_k B_i[h][k] (SF_F, Sec. 3.5), or with s.sf4_delete its sum sum_k B_i[h][k] (SF_4, Sec. 3.4;
+// a sum of 2^32 or more is returned as the 32-bit maximum, which no counter exceeds).  Also
+// reports whether B_i[h][f] went negative (strict-turnstile violation).
+__device__ __forceinline__ uint32_t bucket_bound_cg(const SketchDesc& s, uint32_t i, uint32_t h,
+                                                    uint32_t f, bool* underflow,
+                                                    unsigned long long pol = 0ull, bool hinted = false) {
     const uint32_t* bk = s.B + ((uint64_t)i * s.w + h) * s.z;
     uint32_t mx = 0;
+    uint64_t sum = 0;
     if ((s.z & 3u) == 0u) {
         const uint4* b4 = reinterpret_cast<const uint4*>(bk);
         for (uint32_t q = 0; q < (s.z >> 2); ++q) {
             const uint4 v = hinted ? ld_cg_v4_pol(b4 + q, pol) : __ldcg(b4 + q);
             mx = max(max(mx, v.x), max(v.y, max(v.z, v.w)));
+            sum += (uint64_t)v.x + v.y + v.z + v.w;
         }
     } else {
-        for (uint32_t k = 0; k < s.z; ++k) mx = max(mx, hinted ? ld_cg_pol(bk + k, pol) : __ldcg(bk + k));
+        for (uint32_t k = 0; k < s.z; ++k) {
+            const uint32_t v = hinted ? ld_cg_pol(bk + k, pol) : __ldcg(bk + k);
+            mx = max(mx, v);
+            sum += v;
+        }
     }
     if ((int32_t)(hinted ? ld_cg_pol(bk + f, pol) : __ldcg(bk + f)) < 0) *underflow = true;
+    if (s.sf4_delete) return sum < 0xFFFFFFFFull ? (uint32_t)sum : 0xFFFFFFFFu;
     return mx;
 }
 

@@ -63,7 +63,7 @@ extern "C" sf_status sf_update_batch_noalloc(const sf_params* p, uint32_t* fat_d
                                              uint32_t* err_dev, void* cuda_stream) {
     if (!p || !fat_dev || !slim_dev) return SF_ERR_INVALID;
     if (p->d < 1 || p->d > SF_MAX_D || p->w < 1 || p->w > 0x7FFFFFFFu || p->z < 1 || p->z > SF_MAX_Z ||
-        p->key_bytes < 1 || p->key_bytes > SF_MAX_KEY_BYTES || p->flags != 0)
+        p->key_bytes < 1 || p->key_bytes > SF_MAX_KEY_BYTES || (p->flags & ~SF_FLAG_SF4_DELETE) != 0)
         return SF_ERR_INVALID;
     if (p->chunk < 2 || p->chunk > SF_NOALLOC_MAX_CHUNK) return SF_ERR_INVALID;  // beyond the fixed scratch
     if (((uintptr_t)fat_dev & 15u) || ((uintptr_t)slim_dev & 15u)) return SF_ERR_INVALID;
@@ -100,6 +100,7 @@ extern "C" sf_status sf_update_batch_noalloc(const sf_params* p, uint32_t* fat_d
     for (uint32_t i = 0; i < SF_MAX_D; ++i) one.s.rs[i] = i < p->d ? splitmix64_step(&seed) : 0;
     one.s.idx_table = nullptr;
     one.s.n_ids = 0;
+    one.s.sf4_delete = (p->flags & SF_FLAG_SF4_DELETE) ? 1u : 0u;
     one.keys = (const uint8_t*)keys_dev;
     one.ops = ops_dev;
     one.op_const = 1;

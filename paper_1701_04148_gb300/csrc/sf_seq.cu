@@ -310,7 +310,7 @@ __device__ __forceinline__ void seq_mixed_window(const SketchDesc& s, volatile u
                 for (int i = 0; i < kMaxD; ++i) {
                     if (i < (int)s.d) {
                         bool dummy = false;
-                        const uint32_t M = bucket_max_cg(s, i, W.h[i], W.f[i], &dummy);
+                        const uint32_t M = bucket_bound_cg(s, i, W.h[i], W.f[i], &dummy);
                         if (A[(uint64_t)i * s.w + W.h[i]] > M) A[(uint64_t)i * s.w + W.h[i]] = M;
                     }
                 }

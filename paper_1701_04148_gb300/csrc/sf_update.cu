@@ -17,7 +17,9 @@
 //            the dictionary slot is cleared for the next chunk
 //   barrier
 // All clamps of one Slim counter in a chunk share the bound max_k B_i[j][k] of the chunk-end
-// Fat, and every raise target satisfies T_e <= F_e <= that bound, so the raises and clamps of a
+// Fat (sum_k B_i[j][k] under the SF_4 rule of Sec. 3.4, whose decrement-above-the-sum equals a
+// clamp to the sum because A <= sum holds), and every raise target satisfies
+// T_e <= F_e <= that bound, so the raises and clamps of a
 // counter commute: applying them with atomics in any order gives the stream-order result.
 //
 // The S = 1 path (the paper's one-at-a-time rule) is seq_update_kernel in sf_seq.cu.
@@ -260,7 +262,7 @@ __device__ __forceinline__ uint32_t fat_estimate(const SketchDesc& s, const uint
 //   raise: T = min(m + c_ins, F); a row whose chunk-start value A0_i >= T needs no atomicMax
 //          (its final value is >= T anyway because T <= the bucket maximum).  Rows with
 //          A0_i == m are known from the mask; when c_ins == 1 every other row has A0_i >= m + 1 >= T.
-//   clamp: atomicMin of the bucket maximum for every row of a deleted key.
+//   clamp: atomicMin of the bucket bound (maximum, or sum for SF_4) for every row of a deleted key.
 template <int D>
 __device__ __forceinline__ void phase2_key(const SketchDesc& s, uint32_t* ctrl, DictEntry* ep, const uint32_t* h,
                                            const uint32_t* f, uint32_t c_ins, uint32_t c_del, uint32_t m,
@@ -279,7 +281,7 @@ __device__ __forceinline__ void phase2_key(const SketchDesc& s, uint32_t* ctrl, 
         bool under = false;
 #pragma unroll
         for (int i = 0; i < D; ++i)
-            red_min_pol(slim_ptr(s, i, h[i]), bucket_max_cg(s, i, h[i], f[i], &under, keep, true), keep);
+            red_min_pol(slim_ptr(s, i, h[i]), bucket_bound_cg(s, i, h[i], f[i], &under, keep, true), keep);
         if (under) atomicOr(ctrl + kCtrlErr, kErrUnderflow);
     }
     asm volatile("st.global.cg.L2::cache_hint.v4.u64 [%0], {%1, %1, %1, %1}, %2;" ::"l"(ep), "l"(0ull), "l"(stream)

@@ -114,3 +114,28 @@ def test_batch_with_claim_lists_in_global_memory(sf):
     with pytest.raises(sf.SFError):
         small = sf.Batch(8, max_round_slots=1000)
         small.update(items)
+
+
+def test_batch_mixes_sf4_and_sff_sketches(sf):
+    """Sketches of both delete rules in one batched launch: each equals its own per-sketch call
+    and the oracle with its rule (Sec. 3.4 SF_4, Sec. 3.5 SF_F)."""
+    import torch
+    plan = _plan(10, seed=21, w_log2=(6.0, 9.0), n_log10=(3.0, 4.3))
+    streams = [wl.mixed_stream(p["n"], p["distinct"], p["s"], 0.3, 4, seed=p["seed"], device="cuda")[0]
+               for p in plan]
+    rules = ["sf4" if i % 2 else "sff" for i in range(len(plan))]
+    chunks = [_chunk_for(p, 5) for p in plan]
+    bsk = [sf.Sketch(4, p["w"], 16, 4, p["seed"], S, delete_rule=r) for p, S, r in zip(plan, chunks, rules)]
+    b = sf.Batch(len(plan))
+    b.update([(sk, st.keys, st.ops) for sk, st in zip(bsk, streams)])
+    assert b.sync_status() == sf.SF_OK
+    for i, (p, S, r, st) in enumerate(zip(plan, chunks, rules, streams)):
+        ref = sf.Sketch(4, p["w"], 16, 4, p["seed"], S, delete_rule=r)
+        ref.update(st.keys, st.ops)
+        ref.sync()
+        assert torch.equal(ref.fat, bsk[i].fat) and torch.equal(ref.slim, bsk[i].slim), i
+        o = oracle.Sketch(4, p["w"], 16, 4, p["seed"], delete_rule=r)
+        o.update(st.keys.cpu().numpy(), st.ops.cpu().numpy(), S=S)
+        assert np.array_equal(bsk[i].slim.cpu().numpy().view(np.uint32).reshape(o.A.shape), o.A), (i, r)
+        ref.close()
+    b.close()
