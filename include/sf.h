@@ -33,6 +33,14 @@
  * CUDA stream; sf_sync waits and reports errors raised on the device.  A handle is used
  * by one host thread at a time.
  *
+ * Where the key, operation and answer buffers may live.  The arguments named *_dev that carry
+ * keys (sf_insert_batch, sf_delete_batch, sf_update_batch, sf_batch_item, sf_query_batch,
+ * sf_update_batch_noalloc), operations, and query answers (sf_query_batch out_dev) may be device
+ * or managed memory, or page-locked host memory (cudaHostAlloc / cudaHostRegister): the kernels
+ * then read the keys and write the answers over the host link themselves, with no staging
+ * copy.  Each pointer is checked with cudaPointerGetAttributes before any launch; pageable host
+ * memory returns SF_ERR_INVALID.  Fat, Slim and scratch buffers are device memory.
+ *
  * Errors.  No exception crosses the ABI.  Argument errors return immediately; errors found
  * on the device are latched in the scratch buffer and returned by the next sf_sync.
  */

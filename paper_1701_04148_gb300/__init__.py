@@ -180,6 +180,18 @@ def _dev_ptr(t, what: str) -> int:
     return int(t.data_ptr())
 
 
+def _io_ptr(t, what: str) -> int:
+    """Keys, operations and query answers: a CUDA tensor, or a pinned (page-locked) CPU tensor
+    that the kernels read or write over the host link themselves (the library checks it)."""
+    if t is None:
+        return 0
+    if not t.is_cuda and not t.is_pinned():
+        raise ValueError(f"{what} must be a CUDA tensor or a pinned CPU tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    return int(t.data_ptr())
+
+
 def make_params(d, w, z, key_bytes, seed, chunk, flags=0) -> Params:
     return Params(d, w, z, key_bytes, seed & (2**64 - 1), chunk, flags)
 
@@ -264,17 +276,17 @@ class Sketch:
 
     def insert(self, keys):
         k, n = self._keys(keys)
-        check(load().sf_insert_batch(self.handle, _dev_ptr(k, "keys"), n), "sf_insert_batch")
+        check(load().sf_insert_batch(self.handle, _io_ptr(k, "keys"), n), "sf_insert_batch")
 
     def delete(self, keys):
         k, n = self._keys(keys)
-        check(load().sf_delete_batch(self.handle, _dev_ptr(k, "keys"), n), "sf_delete_batch")
+        check(load().sf_delete_batch(self.handle, _io_ptr(k, "keys"), n), "sf_delete_batch")
 
     def update(self, keys, ops):
         k, n = self._keys(keys)
         if ops.numel() != n:
             raise ValueError("ops must have one entry per key")
-        check(load().sf_update_batch(self.handle, _dev_ptr(k, "keys"), _dev_ptr(ops, "ops"), n), "sf_update_batch")
+        check(load().sf_update_batch(self.handle, _io_ptr(k, "keys"), _io_ptr(ops, "ops"), n), "sf_update_batch")
 
     def sync(self) -> int:
         return check(load().sf_sync(self.handle), "sf_sync")
@@ -337,7 +349,7 @@ class Batch:
         keep = []
         for i, (sk, keys, ops) in enumerate(items):
             k, n = sk._keys(keys)
-            arr[i] = BatchItem(sk.handle.value, _dev_ptr(k, "keys") if n else 0, _dev_ptr(ops, "ops"), n)
+            arr[i] = BatchItem(sk.handle.value, _io_ptr(k, "keys") if n else 0, _io_ptr(ops, "ops"), n)
             keep.append((k, ops))
         self._keep = keep
         check(load().sf_batch_update(self.handle, len(items), ctypes.cast(arr, ctypes.c_void_p)), "sf_batch_update")
@@ -366,16 +378,18 @@ class Batch:
 
 
 def query(slim, hdr: SlimHeader, keys, out=None, stream=None, index_table=None):
-    """Point queries on an exported Slim (device tensors); returns int32 estimates (bit pattern u32)."""
+    """Point queries on an exported Slim; keys and out may be CUDA tensors or pinned CPU tensors.
+    Returns int32 estimates (bit pattern u32); a new out is allocated where the keys live (pinned
+    when the keys are pinned)."""
     torch = _torch()
     kb = hdr.key_bytes
     n = keys.shape[0] if (keys.dim() == 2 and keys.dtype == torch.uint8) else keys.numel() * keys.element_size() // kb
     if out is None:
-        out = torch.empty(n, dtype=torch.int32, device=keys.device)
+        out = torch.empty(n, dtype=torch.int32, device=keys.device, pin_memory=not keys.is_cuda)
     v = SlimView(_dev_ptr(slim, "slim"), hdr, _dev_ptr(index_table, "index_table") if index_table is not None else 0,
                  index_table.shape[0] if index_table is not None else 0)
-    check(load().sf_query_batch(ctypes.byref(v), _dev_ptr(keys, "keys") if n else 0, n,
-                                _dev_ptr(out, "out") if n else 0, _stream_handle(stream)), "sf_query_batch")
+    check(load().sf_query_batch(ctypes.byref(v), _io_ptr(keys, "keys") if n else 0, n,
+                                _io_ptr(out, "out") if n else 0, _stream_handle(stream)), "sf_query_batch")
     return out
 
 
@@ -391,7 +405,7 @@ def update_batch_noalloc(params: Params, fat, slim, keys, ops=None, err=None, st
     n = keys.shape[0] if (keys.dim() == 2 and keys.dtype == torch.uint8) else \
         keys.numel() * keys.element_size() // params.key_bytes
     check(load().sf_update_batch_noalloc(ctypes.byref(params), _dev_ptr(fat, "fat"), _dev_ptr(slim, "slim"),
-                                         _dev_ptr(keys, "keys") if n else 0, _dev_ptr(ops, "ops"), n,
+                                         _io_ptr(keys, "keys") if n else 0, _io_ptr(ops, "ops"), n,
                                          _dev_ptr(err, "err"), _stream_handle(stream)), "sf_update_batch_noalloc")
 
 

@@ -55,10 +55,14 @@ sfk::SketchDesc desc_of(const sf_sketch* s) {
     return d;
 }
 
-sf_status run_update(sf_sketch* s, const void* keys, const int8_t* ops, int op_const, uint64_t n) {
+sf_status run_update(sf_sketch* s, const void* keys_in, const int8_t* ops_in, int op_const, uint64_t n) {
     if (!s) return SF_ERR_INVALID;
     if (n == 0) return SF_OK;
-    if (!keys) return SF_ERR_INVALID;
+    if (!keys_in) return SF_ERR_INVALID;
+    const void *keys = nullptr, *ops_v = nullptr;
+    if (sf_device_access(keys_in, &keys) != SF_OK || sf_device_access(ops_in, &ops_v) != SF_OK)
+        return SF_ERR_INVALID;
+    const int8_t* ops = static_cast<const int8_t*>(ops_v);
     const uint32_t kb = s->p.key_bytes;
     if ((kb == 4 || kb == 8) && ((uintptr_t)keys % kb) != 0) return SF_ERR_INVALID;
     if ((s->p.flags & SF_FLAG_EXPLICIT_INDEX) && !s->idx_table) return SF_ERR_INVALID;
@@ -224,6 +228,11 @@ sf_status sf_query_batch(const sf_slim_view* v, const void* keys_dev, uint64_t n
     if (h.hash_id == SF_HASH_EXPLICIT && (!v->index_table || h.key_bytes != 4)) return SF_ERR_INVALID;
     if (n == 0) return SF_OK;
     if (!v->counters || !keys_dev || !out_dev) return SF_ERR_INVALID;
+    const void *keys_acc = nullptr, *out_acc = nullptr;
+    if (sf_device_access(keys_dev, &keys_acc) != SF_OK || sf_device_access(out_dev, &out_acc) != SF_OK)
+        return SF_ERR_INVALID;
+    keys_dev = keys_acc;
+    out_dev = (uint32_t*)out_acc;
     if ((h.key_bytes == 4 || h.key_bytes == 8) && ((uintptr_t)keys_dev % h.key_bytes) != 0) return SF_ERR_INVALID;
     sfk::QueryArgs q{};
     q.s.A = (uint32_t*)v->counters;

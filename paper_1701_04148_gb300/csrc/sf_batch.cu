@@ -7,6 +7,7 @@
 // sketch's result: it only spreads every stream over the whole GPU.
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "sf_handle.h"
 
@@ -33,6 +34,7 @@ struct sf_batch {
     int exec_grid;
     uint32_t graph_launches, graph_captures;
     uint64_t rounds_last;
+    std::vector<const void*> keys_acc, ops_acc;  // device-usable item pointers of the current call
 };
 
 namespace {
@@ -78,6 +80,13 @@ sf_status sf_batch_create(uint32_t max_sketches, uint64_t max_round_slots, void*
     if (!b) return SF_ERR_OOM;
     b->max_sketches = max_sketches;
     b->max_round_slots = max_round_slots;
+    try {
+        b->keys_acc.assign(max_sketches, nullptr);
+        b->ops_acc.assign(max_sketches, nullptr);
+    } catch (...) {
+        delete b;
+        return SF_ERR_OOM;
+    }
     b->claims_dev = (uint2*)((uint8_t*)scratch_dev + kBatchCtrlBytes + table_bytes_of(max_sketches));
     b->scratch = (uint8_t*)scratch_dev;
     b->ctrl = (uint32_t*)scratch_dev;
@@ -112,8 +121,11 @@ sf_status sf_batch_update(sf_batch* b, uint32_t n_items, const sf_batch_item* it
         if (!s || s->p.d != d || s->p.chunk < 2 || s->device != b->device || (s->p.flags & SF_FLAG_EXPLICIT_INDEX))
             return SF_ERR_INVALID;
         if (items[i].n && !items[i].keys_dev) return SF_ERR_INVALID;
+        if (sf_device_access(items[i].keys_dev, &b->keys_acc[i]) != SF_OK ||
+            sf_device_access(items[i].ops_dev, &b->ops_acc[i]) != SF_OK)
+            return SF_ERR_INVALID;
         const uint32_t kb = s->p.key_bytes;
-        if ((kb == 4 || kb == 8) && ((uintptr_t)items[i].keys_dev % kb) != 0) return SF_ERR_INVALID;
+        if ((kb == 4 || kb == 8) && ((uintptr_t)b->keys_acc[i] % kb) != 0) return SF_ERR_INVALID;
     }
     int cur = -1;
     if (cudaGetDevice(&cur) != cudaSuccess) return SF_ERR_CUDA;
@@ -134,8 +146,8 @@ sf_status sf_batch_update(sf_batch* b, uint32_t n_items, const sf_batch_item* it
         R.s.key_bytes = s->p.key_bytes;
         for (int r = 0; r < SF_MAX_D; ++r) R.s.rs[r] = s->rs[r];
         R.s.sf4_delete = (s->p.flags & SF_FLAG_SF4_DELETE) ? 1u : 0u;
-        R.keys = (const uint8_t*)items[i].keys_dev;
-        R.ops = items[i].ops_dev;
+        R.keys = (const uint8_t*)b->keys_acc[i];
+        R.ops = (const int8_t*)b->ops_acc[i];
         R.op_const = 1;
         R.S = s->p.chunk;
         R.n = items[i].n;

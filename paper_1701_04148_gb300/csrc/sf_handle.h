@@ -7,6 +7,33 @@
 #include "sf.h"
 #include "sf_internal.h"
 
+// Device-usable address of a caller buffer that a kernel reads or writes (keys, operations, query
+// answers): device or managed memory as it is; page-locked host memory (cudaHostAlloc,
+// cudaHostRegister) through its mapping into the device's address space, so the kernel itself
+// moves those bytes over the host link and no staging copy is needed.  Pageable host memory and
+// unknown pointers are refused with SF_ERR_INVALID before anything is launched.  NULL maps to NULL.
+inline sf_status sf_device_access(const void* p, const void** out) {
+    *out = nullptr;
+    if (!p) return SF_OK;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        (void)cudaGetLastError();  // clear the sticky-free error of an unknown pointer
+        return SF_ERR_INVALID;
+    }
+    switch (at.type) {
+        case cudaMemoryTypeDevice:
+        case cudaMemoryTypeManaged:
+            *out = p;
+            return SF_OK;
+        case cudaMemoryTypeHost:
+            if (!at.devicePointer) return SF_ERR_INVALID;
+            *out = at.devicePointer;
+            return SF_OK;
+        default:
+            return SF_ERR_INVALID;
+    }
+}
+
 struct sf_sketch {
     sf_params p;
     uint32_t* A;

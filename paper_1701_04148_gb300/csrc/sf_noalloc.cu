@@ -10,6 +10,7 @@
 #include <mutex>
 
 #include "sf.h"
+#include "sf_handle.h"
 #include "sf_internal.h"
 
 namespace {
@@ -69,6 +70,11 @@ extern "C" sf_status sf_update_batch_noalloc(const sf_params* p, uint32_t* fat_d
     if (((uintptr_t)fat_dev & 15u) || ((uintptr_t)slim_dev & 15u)) return SF_ERR_INVALID;
     if (n == 0) return SF_OK;
     if (!keys_dev) return SF_ERR_INVALID;
+    const void *keys_acc = nullptr, *ops_acc = nullptr;
+    if (sf_device_access(keys_dev, &keys_acc) != SF_OK || sf_device_access(ops_dev, &ops_acc) != SF_OK)
+        return SF_ERR_INVALID;
+    keys_dev = keys_acc;
+    ops_dev = static_cast<const int8_t*>(ops_acc);
     if ((p->key_bytes == 4 || p->key_bytes == 8) && ((uintptr_t)keys_dev % p->key_bytes) != 0) return SF_ERR_INVALID;
 
     int dev = 0, sms = 0;

@@ -1,0 +1,70 @@
+"""Keys, operations and query answers in page-locked host memory: the kernels read and write
+them over the host link themselves.  Results must be bit-identical to device-resident buffers
+on every path (chunked, S = 1, batched, queries), and pageable host memory is refused before
+anything is launched."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def _pinned(t):
+    return t.cpu().pin_memory()
+
+
+@pytest.mark.parametrize("kb,S", [(4, 65536), (13, 4096), (4, 1), (13, 1)])
+def test_pinned_keys_update_like_device_keys(sf, kb, S):
+    import torch
+    st, ids = wl.mixed_stream(60_000, 3_000, 1.1, 0.2, 4, seed=kb * 10 + S % 7)
+    keys = st.keys if kb == 4 else torch.cat([st.keys, st.keys, st.keys, st.keys[:, :1]], 1).contiguous()
+    qk = ids if kb == 4 else torch.cat([ids, ids, ids, ids[:, :1]], 1).contiguous()
+    a = sf.Sketch(4, 1 << 12, 16, kb, 3, S)
+    b = sf.Sketch(4, 1 << 12, 16, kb, 3, S)
+    a.update(keys.cuda(), st.ops.cuda())
+    b.update(_pinned(keys), _pinned(st.ops))
+    a.sync()
+    b.sync()
+    assert torch.equal(a.fat, b.fat) and torch.equal(a.slim, b.slim)
+    slim, hdr = b.export_slim()
+    want = sf.query(slim, hdr, qk.cuda())
+    got = sf.query(slim, hdr, _pinned(qk))          # answers land in pinned host memory
+    torch.cuda.synchronize()
+    assert got.device.type == "cpu" and got.is_pinned()
+    assert torch.equal(want.cpu(), got)
+
+
+def test_pinned_keys_in_a_batch(sf):
+    import torch
+    plan = wl.many_sketch_plan(8, seed=4, w_log2=(7.0, 10.0), n_log10=(3.0, 4.5))
+    streams = [wl.mixed_stream(p["n"], p["distinct"], p["s"], 0.1, 4, seed=p["seed"])[0] for p in plan]
+    chunks = [max(2, -(-p["n"] // 6)) for p in plan]
+    dev_sk = [sf.Sketch(4, p["w"], 16, 4, p["seed"], S) for p, S in zip(plan, chunks)]
+    host_sk = [sf.Sketch(4, p["w"], 16, 4, p["seed"], S) for p, S in zip(plan, chunks)]
+    b1, b2 = sf.Batch(len(plan)), sf.Batch(len(plan))
+    b1.update([(sk, s.keys.cuda(), s.ops.cuda()) for sk, s in zip(dev_sk, streams)])
+    pinned = [(_pinned(s.keys), _pinned(s.ops)) for s in streams]
+    b2.update([(sk, k, o) for sk, (k, o) in zip(host_sk, pinned)])
+    assert b1.sync_status() == sf.SF_OK and b2.sync_status() == sf.SF_OK
+    for x, y in zip(dev_sk, host_sk):
+        assert torch.equal(x.fat, y.fat) and torch.equal(x.slim, y.slim)
+    b1.close()
+    b2.close()
+
+
+def test_pageable_host_memory_is_refused_before_launch(sf):
+    L = sf.load()
+    g = sf.Sketch(2, 64, 4, 4, 1, 1024)
+    keys = np.arange(100, dtype=np.uint32)          # ordinary (pageable) host memory
+    assert L.sf_insert_batch(g.handle, keys.ctypes.data, 100) == sf.SF_ERR_INVALID
+    out = np.zeros(100, dtype=np.uint32)
+    slim, hdr = g.export_slim()
+    v = sf.SlimView(slim.data_ptr(), hdr, 0, 0)
+    assert L.sf_query_batch(ctypes.byref(v), keys.ctypes.data, 100, out.ctypes.data, None) == sf.SF_ERR_INVALID
+    with pytest.raises(ValueError):
+        import torch
+        g.insert(torch.from_numpy(keys))             # the binding refuses it too
+    assert g.sync_status() == sf.SF_OK               # nothing ran, nothing latched
