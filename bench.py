@@ -406,8 +406,12 @@ def run_flows(args, ctx):
     achieved = upd_timed * L2_OPS_PER_UPDATE / (chunk_ms / 1e3) / 1e9
     tr = traffic_record()
     traffic = None
-    if tr is not None:
-        traffic = round(tr["dram_bytes_per_update"] * upd_timed / launches_chunk)
+    if tr is not None and "flows_batched" in tr:
+        # DRAM bytes of this workload's own batched launches (one insert and one delete launch per
+        # step), averaged per launch like `achieved`
+        fb = tr["flows_batched"]
+        per = [fb[k]["dram_bytes_read"] + fb[k]["dram_bytes_write"] for k in ("insert_launch", "delete_launch")]
+        traffic = round(sum(per) / len(per))
     roofline = {"bound": "l2", "kernel": "chunk_update_kernel", "achieved": round(achieved, 2),
                 "peak": round(best["mix"], 2), "unit": "G random L2 ops/s", "frac": round(achieved / best["mix"], 4),
                 "traffic": traffic,
