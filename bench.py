@@ -762,7 +762,7 @@ def run_batch(args, ctx):
     cache = os.path.join(ROOT, "paper_1701_04148_gb300", "_build", "autotune_cache.json")
     key = autotune.shape_key(ws, ns, 4, 16, 4) + "-" + torch.cuda.get_device_name(dev).replace(" ", "_")
     t1 = time.time()
-    tuned = autotune.tune(make, streams, ns, candidates=(64, 256, 1024), cache_path=cache, cache_key=key)
+    tuned = autotune.tune(make, streams, ns, candidates=(32, 64, 256, 1024), cache_path=cache, cache_key=key)
     tune_s = time.time() - t1
     chunks = tuned["chunks"]
     bsk, psk = make(chunks), make(chunks)
@@ -811,6 +811,9 @@ def run_batch(args, ctx):
            "plain_value": round(world * total / (tp / 1e3) / 1e6, 2), "batched_vs_plain_speedup": round(tp / tb, 3),
            "ms_per_step_batched": round(tb, 3), "ms_per_step_plain": round(tp, 3), "rounds": tuned["rounds"],
            "autotune_updates_per_s": tuned["trials"], "graph": info, "status": st_b,
+           "launch_groups": {"groups": info["groups_last"], "group_bytes": info["group_bytes"],
+                             "rule": "sketches whose counters fit the budget packed into L2-sized launch "
+                                     "groups, larger ones share one launch"},
            "batched_equals_plain": bool(exact), "gen_s": round(gen_s, 1), "autotune_s": round(tune_s, 1),
            "n_gpus": world, "scaling": "weak"}
     batch.close()

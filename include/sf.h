@@ -243,6 +243,19 @@ sf_status sf_batch_update(sf_batch *b, uint32_t n_items, const sf_batch_item *it
  * After SF_ERR_TIMEOUT the sketches of the last call must be re-created. */
 sf_status sf_batch_sync(sf_batch *b);
 
+/*
+ * Launch grouping of sf_batch_update (no counterpart in the paper).  Sketches are independent, so a
+ * call may update them in any grouping: sketches whose counters (Fat + Slim + the dictionary entries
+ * one chunk can touch, 32 B per chunk slot) fit `bytes` are packed, in input order, into groups
+ * whose counters fit it together, one cooperative launch per group, so each launch works out of L2;
+ * sketches larger than `bytes` share one launch.  bytes = 0 puts every sketch of a call in one
+ * launch.  The default is 3/4 of the device's L2 (about 95 MiB on a GB300).  Results do not depend
+ * on the grouping (each sketch's updates are the same); only the speed does.
+ */
+sf_status sf_batch_set_group_bytes(sf_batch *b, uint64_t bytes);
+/* The group budget and the number of launches the last sf_batch_update used. */
+sf_status sf_batch_groups(const sf_batch *b, uint32_t *groups_last, uint64_t *group_bytes);
+
 /* Counters: graph launches, graph captures, and the round count of the last call. */
 sf_status sf_batch_info(const sf_batch *b, uint32_t *graph_launches, uint32_t *graph_captures,
                         uint64_t *rounds_last);

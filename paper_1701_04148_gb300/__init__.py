@@ -100,6 +100,9 @@ _SIGS = {
                                          ctypes.c_uint32, ctypes.POINTER(ctypes.c_void_p)]),
     "sf_batch_update": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]),
     "sf_batch_sync": (ctypes.c_int32, [ctypes.c_void_p]),
+    "sf_batch_set_group_bytes": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64]),
+    "sf_batch_groups": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32),
+                                         ctypes.POINTER(ctypes.c_uint64)]),
     "sf_batch_info": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32),
                                        ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint64)]),
     "sf_batch_destroy": (ctypes.c_int32, [ctypes.c_void_p]),
@@ -328,7 +331,9 @@ class Batch:
     """Many sketches updated by one persistent launch (sf_batch_*), CUDA graph replay by default."""
 
     def __init__(self, max_sketches: int, graph: bool = True, stream=None, device=None,
-                 max_round_slots: int = 1 << 22):
+                 max_round_slots: int = 1 << 22, group_bytes: int | None = None):
+        """group_bytes: counter footprint per launch group (None: the library default, 3/4 of L2;
+        0: every sketch of a call in one launch)."""
         torch = _torch()
         L = load()
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
@@ -342,6 +347,8 @@ class Batch:
         self.handle = h
         self.max_sketches = max_sketches
         self._keep = None
+        if group_bytes is not None:
+            check(L.sf_batch_set_group_bytes(self.handle, int(group_bytes)), "sf_batch_set_group_bytes")
 
     def update(self, items):
         """items: list of (Sketch, keys tensor, ops tensor or None)."""
@@ -363,7 +370,10 @@ class Batch:
     def info(self):
         gl, gc, rl = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint64()
         check(load().sf_batch_info(self.handle, ctypes.byref(gl), ctypes.byref(gc), ctypes.byref(rl)), "sf_batch_info")
-        return {"graph_launches": gl.value, "graph_captures": gc.value, "rounds_last": rl.value}
+        ng, gb = ctypes.c_uint32(), ctypes.c_uint64()
+        check(load().sf_batch_groups(self.handle, ctypes.byref(ng), ctypes.byref(gb)), "sf_batch_groups")
+        return {"graph_launches": gl.value, "graph_captures": gc.value, "rounds_last": rl.value,
+                "groups_last": ng.value, "group_bytes": gb.value}
 
     def close(self):
         if getattr(self, "handle", None):

@@ -26,15 +26,19 @@ struct sf_batch {
     uint32_t flags;
     int device;
     int num_sms;
-    // graph of the last shape
+    // graph of the last launch plan
     bool have_exec;
     cudaGraphExec_t exec;
-    sfk::BatchArgs exec_args;
+    std::vector<sfk::BatchArgs> exec_plan;
     uint32_t exec_d;
     int exec_grid;
     uint32_t graph_launches, graph_captures;
     uint64_t rounds_last;
+    uint64_t group_bytes;                        // counter footprint per launch group (0: one launch)
+    uint32_t groups_last;
     std::vector<const void*> keys_acc, ops_acc;  // device-usable item pointers of the current call
+    std::vector<uint32_t> order;                 // item of each table row (group by group)
+    std::vector<sfk::BatchArgs> plan;            // one cooperative launch per group
 };
 
 namespace {
@@ -47,13 +51,28 @@ bool same_shape(const sfk::BatchArgs& x, const sfk::BatchArgs& y) {
            x.claims_global == y.claims_global;
 }
 
-cudaError_t enqueue(sf_batch* b, const sfk::BatchArgs& a, uint32_t d, int grid, size_t table_bytes,
-                    cudaStream_t st) {
+bool same_plan(const std::vector<sfk::BatchArgs>& x, const std::vector<sfk::BatchArgs>& y) {
+    if (x.size() != y.size()) return false;
+    for (size_t g = 0; g < x.size(); ++g)
+        if (!same_shape(x[g], y[g])) return false;
+    return true;
+}
+
+// One table upload, then per launch group: barrier-counter reset and the cooperative launch.
+cudaError_t enqueue(sf_batch* b, const std::vector<sfk::BatchArgs>& plan, uint32_t d, int grid,
+                    size_t table_bytes, cudaStream_t st) {
     cudaError_t e = cudaMemcpyAsync(b->table_dev, b->staging, table_bytes, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(b->ctrl + sfk::kCtrlBarrier64, 0, sizeof(unsigned long long), st);  // barrier counter
-    if (e != cudaSuccess) return e;
-    return sfk::launch_batch_update(a, d, grid, st);
+    for (size_t g = 0; e == cudaSuccess && g < plan.size(); ++g) {
+        e = cudaMemsetAsync(b->ctrl + sfk::kCtrlBarrier64, 0, sizeof(unsigned long long), st);
+        if (e == cudaSuccess) e = sfk::launch_batch_update(plan[g], d, grid, st);
+    }
+    return e;
+}
+
+// Counter footprint of one sketch in a round: Fat + Slim + the dictionary entries a chunk can touch.
+uint64_t item_footprint(const sf_sketch* s) {
+    const uint64_t dw = (uint64_t)s->p.d * s->p.w;
+    return dw * s->p.z * 4ull + dw * 4ull + (uint64_t)s->p.chunk * sizeof(sfk::DictEntry);
 }
 
 }  // namespace
@@ -83,6 +102,7 @@ sf_status sf_batch_create(uint32_t max_sketches, uint64_t max_round_slots, void*
     try {
         b->keys_acc.assign(max_sketches, nullptr);
         b->ops_acc.assign(max_sketches, nullptr);
+        b->order.reserve(max_sketches);
     } catch (...) {
         delete b;
         return SF_ERR_OOM;
@@ -101,6 +121,10 @@ sf_status sf_batch_create(uint32_t max_sketches, uint64_t max_round_slots, void*
         delete b;
         return SF_ERR_CUDA;
     }
+    // default launch groups: counters of up to 3/4 of L2 per group (GB300: 126 MiB -> ~95 MiB)
+    int l2 = 0;
+    if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, b->device) != cudaSuccess) l2 = 0;
+    b->group_bytes = (uint64_t)l2 * 3u / 4u;
     if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming) != cudaSuccess ||
         cudaMemsetAsync(scratch_dev, 0, xb, b->stream) != cudaSuccess) {
@@ -132,61 +156,102 @@ sf_status sf_batch_update(sf_batch* b, uint32_t n_items, const sf_batch_item* it
     if (cur != b->device && cudaSetDevice(b->device) != cudaSuccess) return SF_ERR_CUDA;
     if (b->staging_busy && cudaEventSynchronize(b->staged) != cudaSuccess) return SF_ERR_CUDA;
 
-    uint64_t flat = 0, rounds = 0;
-    bool may_ins = false, may_del = false;
-    for (uint32_t i = 0; i < n_items; ++i) {
-        const sf_sketch* s = items[i].sketch;
-        sfk::SketchRun& R = b->staging[i];
-        std::memset(&R, 0, sizeof(R));
-        R.s.A = s->A;
-        R.s.B = s->B;
-        R.s.d = s->p.d;
-        R.s.w = s->p.w;
-        R.s.z = s->p.z;
-        R.s.key_bytes = s->p.key_bytes;
-        for (int r = 0; r < SF_MAX_D; ++r) R.s.rs[r] = s->rs[r];
-        R.s.sf4_delete = (s->p.flags & SF_FLAG_SF4_DELETE) ? 1u : 0u;
-        R.keys = (const uint8_t*)b->keys_acc[i];
-        R.ops = (const int8_t*)b->ops_acc[i];
-        R.op_const = 1;
-        R.S = s->p.chunk;
-        R.n = items[i].n;
-        R.flat_base = flat;
-        R.dict = s->dict;
-        R.cap_mask = s->cap - 1u;
-        flat += sfk::round_up32(R.S);
-        const uint64_t nr = (R.n + R.S - 1) / R.S;
-        rounds = nr > rounds ? nr : rounds;
-        if (R.n) {
-            may_ins |= R.ops != nullptr;
-            may_del |= R.ops != nullptr;
-            may_ins |= R.ops == nullptr;
+    // Launch groups.  Sketches are independent, so they may run in any grouping.  Sketches whose
+    // counters fit the group budget are packed, in input order, into groups whose counters fit it
+    // together, so each launch works out of L2; sketches larger than the budget share one launch,
+    // where batching them at least fills the GPU.  A zero budget puts every sketch in one launch.
+    b->order.clear();
+    std::vector<std::pair<uint32_t, uint32_t>> groups;  // [first, last) rows of the table
+    {
+        const uint64_t budget = b->group_bytes;
+        uint32_t g0 = 0;
+        uint64_t gb = 0;
+        for (uint32_t i = 0; i < n_items; ++i) {
+            const uint64_t fb = item_footprint(items[i].sketch);
+            if (budget && fb > budget) continue;
+            if (budget && gb > 0 && gb + fb > budget) {
+                groups.emplace_back(g0, (uint32_t)b->order.size());
+                g0 = (uint32_t)b->order.size();
+                gb = 0;
+            }
+            b->order.push_back(i);
+            gb += fb;
         }
+        if ((uint32_t)b->order.size() > g0) groups.emplace_back(g0, (uint32_t)b->order.size());
+        const uint32_t big0 = (uint32_t)b->order.size();
+        for (uint32_t i = 0; i < n_items; ++i)
+            if (budget && item_footprint(items[i].sketch) > budget) b->order.push_back(i);
+        if ((uint32_t)b->order.size() > big0) groups.emplace_back(big0, (uint32_t)b->order.size());
     }
+
     const int bps = sfk::chunk_update_blocks_per_sm(d);
     if (bps <= 0) return SF_ERR_CUDA;
     const int grid = b->num_sms * (bps < 2 ? bps : 2);
-    sfk::BatchArgs a{};
-    a.runs = b->table_dev;
-    a.n_runs = n_items;
-    a.flat_len = flat;
-    a.n_rounds = rounds;
-    a.claims_cap = sfk::chunk_claims_cap(flat, grid);
-    a.ctrl = b->ctrl;
-    a.bar_base = 0;  // the launch zeroes the barrier counter first
-    a.timeout_ns = sfk::kBarrierTimeoutNs;
-    a.may_ins = may_ins;
-    a.may_del = may_del;
-    if (flat > b->max_round_slots) return SF_ERR_INVALID;
-    // claim lists in shared memory when they fit, else in the batch scratch
-    a.claims_global = ((uint64_t)a.claims_cap * sizeof(uint2) > (uint64_t)sfk::kMaxClaimSmem) ? b->claims_dev : nullptr;
+    b->plan.clear();
+    uint64_t rounds_all = 0;
+    for (const auto& gr : groups) {
+        uint64_t flat = 0, rounds = 0;
+        bool may_ins = false, may_del = false;
+        for (uint32_t row = gr.first; row < gr.second; ++row) {
+            const uint32_t i = b->order[row];
+            const sf_sketch* s = items[i].sketch;
+            sfk::SketchRun& R = b->staging[row];
+            std::memset(&R, 0, sizeof(R));
+            R.s.A = s->A;
+            R.s.B = s->B;
+            R.s.d = s->p.d;
+            R.s.w = s->p.w;
+            R.s.z = s->p.z;
+            R.s.key_bytes = s->p.key_bytes;
+            for (int r = 0; r < SF_MAX_D; ++r) R.s.rs[r] = s->rs[r];
+            R.s.sf4_delete = (s->p.flags & SF_FLAG_SF4_DELETE) ? 1u : 0u;
+            R.keys = (const uint8_t*)b->keys_acc[i];
+            R.ops = (const int8_t*)b->ops_acc[i];
+            R.op_const = 1;
+            R.S = s->p.chunk;
+            R.n = items[i].n;
+            R.flat_base = flat;  // slots are numbered per launch group
+            R.dict = s->dict;
+            R.cap_mask = s->cap - 1u;
+            flat += sfk::round_up32(R.S);
+            const uint64_t nr = (R.n + R.S - 1) / R.S;
+            rounds = nr > rounds ? nr : rounds;
+            if (R.n) {
+                may_ins |= R.ops != nullptr;
+                may_del |= R.ops != nullptr;
+                may_ins |= R.ops == nullptr;
+            }
+        }
+        if (flat > b->max_round_slots) {
+            if (cur != b->device) cudaSetDevice(cur);
+            return SF_ERR_INVALID;
+        }
+        if (rounds == 0) continue;  // nothing to update in this group
+        sfk::BatchArgs a{};
+        a.runs = b->table_dev + gr.first;
+        a.n_runs = gr.second - gr.first;
+        a.flat_len = flat;
+        a.n_rounds = rounds;
+        a.claims_cap = sfk::chunk_claims_cap(flat, grid);
+        a.ctrl = b->ctrl;
+        a.bar_base = 0;  // each launch zeroes the barrier counter first
+        a.timeout_ns = sfk::kBarrierTimeoutNs;
+        a.may_ins = may_ins;
+        a.may_del = may_del;
+        // claim lists in shared memory when they fit, else in the batch scratch (launches run in order)
+        a.claims_global =
+            ((uint64_t)a.claims_cap * sizeof(uint2) > (uint64_t)sfk::kMaxClaimSmem) ? b->claims_dev : nullptr;
+        b->plan.push_back(a);
+        rounds_all = rounds > rounds_all ? rounds : rounds_all;
+    }
     const size_t table_bytes = (size_t)n_items * sizeof(sfk::SketchRun);
-    b->rounds_last = rounds;
+    b->rounds_last = rounds_all;
+    b->groups_last = (uint32_t)b->plan.size();
 
     cudaError_t e = cudaSuccess;
     bool launched = false;
     if (b->flags & SF_BATCH_GRAPH) {
-        if (!b->have_exec || !same_shape(b->exec_args, a) || b->exec_d != d || b->exec_grid != grid) {
+        if (!b->have_exec || !same_plan(b->exec_plan, b->plan) || b->exec_d != d || b->exec_grid != grid) {
             if (b->have_exec) {
                 cudaGraphExecDestroy(b->exec);
                 b->have_exec = false;
@@ -194,14 +259,14 @@ sf_status sf_batch_update(sf_batch* b, uint32_t n_items, const sf_batch_item* it
             cudaGraph_t g = nullptr;
             bool ok = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
             if (ok) {
-                const cudaError_t ce = enqueue(b, a, d, grid, table_bytes, b->cap_stream);
+                const cudaError_t ce = enqueue(b, b->plan, d, grid, table_bytes, b->cap_stream);
                 ok = cudaStreamEndCapture(b->cap_stream, &g) == cudaSuccess && ce == cudaSuccess && g;
             }
             if (ok) ok = cudaGraphInstantiate(&b->exec, g, 0) == cudaSuccess;
             if (g) cudaGraphDestroy(g);
             if (ok) {
                 b->have_exec = true;
-                b->exec_args = a;
+                b->exec_plan = b->plan;
                 b->exec_d = d;
                 b->exec_grid = grid;
                 b->graph_captures++;
@@ -216,7 +281,7 @@ sf_status sf_batch_update(sf_batch* b, uint32_t n_items, const sf_batch_item* it
             if (e == cudaSuccess) b->graph_launches++;
         }
     }
-    if (!launched) e = enqueue(b, a, d, grid, table_bytes, b->stream);
+    if (!launched) e = enqueue(b, b->plan, d, grid, table_bytes, b->stream);
     if (e == cudaSuccess) e = cudaEventRecord(b->staged, b->stream);
     b->staging_busy = true;
     if (cur != b->device) cudaSetDevice(cur);
@@ -237,6 +302,19 @@ sf_status sf_batch_sync(sf_batch* b) {
     if (err & (sfk::kErrBadKey | sfk::kErrDictFull)) return SF_ERR_INVALID;
     if (err & sfk::kErrUnderflow) return SF_ERR_UNDERFLOW;
     return SF_ERR_INVALID;
+}
+
+sf_status sf_batch_set_group_bytes(sf_batch* b, uint64_t bytes) {
+    if (!b) return SF_ERR_INVALID;
+    b->group_bytes = bytes;
+    return SF_OK;
+}
+
+sf_status sf_batch_groups(const sf_batch* b, uint32_t* groups_last, uint64_t* group_bytes) {
+    if (!b) return SF_ERR_INVALID;
+    if (groups_last) *groups_last = b->groups_last;
+    if (group_bytes) *group_bytes = b->group_bytes;
+    return SF_OK;
 }
 
 sf_status sf_batch_info(const sf_batch* b, uint32_t* graph_launches, uint32_t* graph_captures, uint64_t* rounds_last) {

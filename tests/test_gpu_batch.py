@@ -139,3 +139,35 @@ def test_batch_mixes_sf4_and_sff_sketches(sf):
         assert np.array_equal(bsk[i].slim.cpu().numpy().view(np.uint32).reshape(o.A.shape), o.A), (i, r)
         ref.close()
     b.close()
+
+
+@pytest.mark.parametrize("group_bytes", [0, 150_000, 1 << 20])
+def test_launch_groups_give_the_same_sketches(sf, group_bytes):
+    """Sketches are independent, so any launch grouping gives the same sketches as one call per
+    sketch.  A 150 KB budget packs the small sketches into several groups and leaves the larger
+    ones (Fat of 2^11-wide sketches: 512 KiB) to share one launch; 0 is a single launch."""
+    import torch
+    plan = _plan(30, seed=11)
+    streams = _streams(plan)
+    chunks = [_chunk_for(p, 6) for p in plan]
+    bsk = [sf.Sketch(4, p["w"], 16, 4, p["seed"], S) for p, S in zip(plan, chunks)]
+    b = sf.Batch(len(plan), group_bytes=group_bytes)
+    for part in (0, 1):                                   # the second call replays the captured plan
+        for sk in bsk:
+            sk.reset()
+        b.update([(sk, st.keys, st.ops) for sk, (st, _) in zip(bsk, streams)])
+    assert b.sync_status() == sf.SF_OK
+    info = b.info()
+    assert info["group_bytes"] == group_bytes
+    if group_bytes == 0:
+        assert info["groups_last"] == 1
+    if group_bytes == 150_000:
+        assert info["groups_last"] >= 3
+    for i, (p, S) in enumerate(zip(plan, chunks)):
+        ref = sf.Sketch(4, p["w"], 16, 4, p["seed"], S)
+        st, _ = streams[i]
+        ref.update(st.keys, st.ops)
+        ref.sync()
+        assert torch.equal(ref.fat, bsk[i].fat) and torch.equal(ref.slim, bsk[i].slim), i
+        ref.close()
+    b.close()
