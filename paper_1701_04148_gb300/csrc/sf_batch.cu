@@ -156,37 +156,52 @@ sf_status sf_batch_update(sf_batch* b, uint32_t n_items, const sf_batch_item* it
     if (cur != b->device && cudaSetDevice(b->device) != cudaSuccess) return SF_ERR_CUDA;
     if (b->staging_busy && cudaEventSynchronize(b->staged) != cudaSuccess) return SF_ERR_CUDA;
 
+    const int bps = sfk::chunk_update_blocks_per_sm(d);
+    if (bps <= 0) return SF_ERR_CUDA;
+    const int grid = b->num_sms * (bps < 2 ? bps : 2);
+
     // Launch groups.  Sketches are independent, so they may run in any grouping.  Sketches whose
     // counters fit the group budget are packed, in input order, into groups whose counters fit it
-    // together, so each launch works out of L2; sketches larger than the budget share one launch,
-    // where batching them at least fills the GPU.  A zero budget puts every sketch in one launch.
+    // together, so each launch works out of L2.  A group whose rounds would not give every thread
+    // of the grid a slot gains nothing from running alone, so it joins the shared launch, as do
+    // the sketches larger than the budget: batching those at least fills the GPU.  A zero budget
+    // puts every sketch in one launch.
     b->order.clear();
     std::vector<std::pair<uint32_t, uint32_t>> groups;  // [first, last) rows of the table
     {
         const uint64_t budget = b->group_bytes;
-        uint32_t g0 = 0;
-        uint64_t gb = 0;
+        const uint64_t min_slots = (uint64_t)grid * sfk::kChunkBlock;
+        std::vector<uint32_t> shared, cur_g;
+        uint64_t gb = 0, gs = 0;
+        auto close = [&]() {
+            if (cur_g.empty()) return;
+            if (gs >= min_slots) {
+                groups.emplace_back((uint32_t)b->order.size(), (uint32_t)(b->order.size() + cur_g.size()));
+                b->order.insert(b->order.end(), cur_g.begin(), cur_g.end());
+            } else {
+                shared.insert(shared.end(), cur_g.begin(), cur_g.end());
+            }
+            cur_g.clear();
+            gb = gs = 0;
+        };
         for (uint32_t i = 0; i < n_items; ++i) {
             const uint64_t fb = item_footprint(items[i].sketch);
-            if (budget && fb > budget) continue;
-            if (budget && gb > 0 && gb + fb > budget) {
-                groups.emplace_back(g0, (uint32_t)b->order.size());
-                g0 = (uint32_t)b->order.size();
-                gb = 0;
+            if (budget == 0 || fb > budget) {
+                shared.push_back(i);
+                continue;
             }
-            b->order.push_back(i);
+            if (gb > 0 && gb + fb > budget) close();
+            cur_g.push_back(i);
             gb += fb;
+            gs += sfk::round_up32(items[i].sketch->p.chunk);
         }
-        if ((uint32_t)b->order.size() > g0) groups.emplace_back(g0, (uint32_t)b->order.size());
-        const uint32_t big0 = (uint32_t)b->order.size();
-        for (uint32_t i = 0; i < n_items; ++i)
-            if (budget && item_footprint(items[i].sketch) > budget) b->order.push_back(i);
-        if ((uint32_t)b->order.size() > big0) groups.emplace_back(big0, (uint32_t)b->order.size());
+        close();
+        if (!shared.empty()) {
+            groups.emplace_back((uint32_t)b->order.size(), (uint32_t)(b->order.size() + shared.size()));
+            b->order.insert(b->order.end(), shared.begin(), shared.end());
+        }
     }
 
-    const int bps = sfk::chunk_update_blocks_per_sm(d);
-    if (bps <= 0) return SF_ERR_CUDA;
-    const int grid = b->num_sms * (bps < 2 ? bps : 2);
     b->plan.clear();
     uint64_t rounds_all = 0;
     for (const auto& gr : groups) {

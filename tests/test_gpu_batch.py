@@ -141,33 +141,47 @@ def test_batch_mixes_sf4_and_sff_sketches(sf):
     b.close()
 
 
-@pytest.mark.parametrize("group_bytes", [0, 150_000, 1 << 20])
-def test_launch_groups_give_the_same_sketches(sf, group_bytes):
-    """Sketches are independent, so any launch grouping gives the same sketches as one call per
-    sketch.  A 150 KB budget packs the small sketches into several groups and leaves the larger
-    ones (Fat of 2^11-wide sketches: 512 KiB) to share one launch; 0 is a single launch."""
+def _same_as_per_sketch_calls(sf, shapes, streams, bsk):
     import torch
-    plan = _plan(30, seed=11)
-    streams = _streams(plan)
-    chunks = [_chunk_for(p, 6) for p in plan]
-    bsk = [sf.Sketch(4, p["w"], 16, 4, p["seed"], S) for p, S in zip(plan, chunks)]
-    b = sf.Batch(len(plan), group_bytes=group_bytes)
-    for part in (0, 1):                                   # the second call replays the captured plan
+    for (w, seed, S), (st, _), sk in zip(shapes, streams, bsk):
+        ref = sf.Sketch(4, w, 16, 4, seed, S)
+        ref.update(st.keys, st.ops)
+        ref.sync()
+        assert torch.equal(ref.fat, sk.fat) and torch.equal(ref.slim, sk.slim), (w, seed, S)
+        ref.close()
+
+
+@pytest.mark.parametrize("group_bytes,want_groups", [(0, 1), (8 << 20, 6), (2 << 20, 1)])
+def test_launch_groups_give_the_same_sketches(sf, group_bytes, want_groups):
+    """Sketches are independent, so any launch grouping gives the same sketches as one call per
+    sketch.  Twelve sketches with 100,000-slot chunks (each fills the grid alone; counters
+    ~3.3 MB): an 8 MiB budget packs them two per launch; a 2 MiB budget is below every sketch, so
+    they share one launch; 0 is one launch."""
+    shapes = [(256, 40 + i, 100_000) for i in range(12)]
+    streams = [wl.mixed_stream(400_000, 3_000, 1.0, 0.1, 4, seed=seed, device="cuda") for _, seed, _ in shapes]
+    bsk = [sf.Sketch(4, w, 16, 4, seed, S) for w, seed, S in shapes]
+    b = sf.Batch(len(bsk), group_bytes=group_bytes, max_round_slots=12 * 100_000)
+    for _ in range(2):                                    # the second call replays the captured plan
         for sk in bsk:
             sk.reset()
         b.update([(sk, st.keys, st.ops) for sk, (st, _) in zip(bsk, streams)])
     assert b.sync_status() == sf.SF_OK
     info = b.info()
-    assert info["group_bytes"] == group_bytes
-    if group_bytes == 0:
-        assert info["groups_last"] == 1
-    if group_bytes == 150_000:
-        assert info["groups_last"] >= 3
-    for i, (p, S) in enumerate(zip(plan, chunks)):
-        ref = sf.Sketch(4, p["w"], 16, 4, p["seed"], S)
-        st, _ = streams[i]
-        ref.update(st.keys, st.ops)
-        ref.sync()
-        assert torch.equal(ref.fat, bsk[i].fat) and torch.equal(ref.slim, bsk[i].slim), i
-        ref.close()
+    assert info["group_bytes"] == group_bytes and info["groups_last"] == want_groups
+    _same_as_per_sketch_calls(sf, shapes, streams, bsk)
+    b.close()
+
+
+def test_underfilled_groups_join_the_shared_launch(sf):
+    """Small sketches whose groups would leave most of the grid idle all run in one launch, with
+    the same results."""
+    plan = _plan(30, seed=11)
+    streams = _streams(plan)
+    shapes = [(p["w"], p["seed"], _chunk_for(p, 6)) for p in plan]
+    bsk = [sf.Sketch(4, w, 16, 4, seed, S) for w, seed, S in shapes]
+    b = sf.Batch(len(bsk), group_bytes=150_000)
+    b.update([(sk, st.keys, st.ops) for sk, (st, _) in zip(bsk, streams)])
+    assert b.sync_status() == sf.SF_OK
+    assert b.info()["groups_last"] == 1
+    _same_as_per_sketch_calls(sf, shapes, streams, bsk)
     b.close()
