@@ -279,7 +279,9 @@ typedef struct sfc sfc;
 typedef struct sfc_config {
     void *arena_dev;          /* device memory holding resident Slims: the admission budget      */
     uint64_t arena_bytes;
-    void *staging_dev;        /* device memory for in-flight batches (sfc_required_staging_bytes) */
+    void *staging_dev;        /* device memory for the request tables of in-flight batches
+                                 (sfc_required_staging_bytes); their keys and answers live in
+                                 mapped pinned host memory that the query kernel reads and writes */
     uint64_t staging_bytes;
     uint32_t max_sketches;    /* sketch ids are 0 .. max_sketches-1                              */
     uint32_t n_streams;       /* batches in flight at once, 1..16                                */
@@ -295,7 +297,7 @@ typedef struct sfc_stats {
     uint64_t arena_used_bytes;
 } sfc_stats;
 
-/* Device staging bytes for a configuration (keys, answers and request tables of n_streams batches). */
+/* Device staging bytes for a configuration (the request tables of n_streams batches). */
 sf_status sfc_required_staging_bytes(const sfc_config *c, uint64_t *bytes);
 
 /* Starts a collector (and its worker thread) on the current device.  Host staging is pinned

@@ -99,12 +99,12 @@ struct Slot {  // one in-flight batch
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;
     bool busy = false;
-    uint8_t* keys_dev = nullptr;
-    uint32_t* out_dev = nullptr;
     sfk::QueryReq* reqs_dev = nullptr;
-    uint8_t* keys_host = nullptr;  // pinned
-    uint32_t* out_host = nullptr;  // pinned
+    uint8_t* keys_host = nullptr;  // pinned, mapped: the query kernel reads the keys from here
+    uint32_t* out_host = nullptr;  // pinned, mapped: the query kernel writes the answers here
     sfk::QueryReq* reqs_host = nullptr;  // pinned
+    const uint8_t* keys_map = nullptr;   // device addresses of keys_host / out_host
+    uint32_t* out_map = nullptr;
     std::vector<std::shared_ptr<Request>> members;
 };
 
@@ -124,7 +124,8 @@ Layout layout_of(const sfc_config* c) {
     L.keys_bytes = align_up((uint64_t)c->max_batch_keys * SF_MAX_KEY_BYTES + (uint64_t)c->max_batch_reqs * 16, kAlign);
     L.out_bytes = align_up((uint64_t)c->max_batch_keys * 4, kAlign);
     L.reqs_bytes = align_up((uint64_t)c->max_batch_reqs * sizeof(sfk::QueryReq), kAlign);
-    L.slot_bytes = L.keys_bytes + L.out_bytes + L.reqs_bytes;
+    L.slot_bytes = L.reqs_bytes;  // device staging holds only the request tables: keys and answers
+                                  // stay in mapped pinned host memory
     return L;
 }
 
@@ -225,7 +226,9 @@ struct sfc {
         }
     }
 
-    // Packs pending requests into slot s and enqueues copy-in, kernel and copy-out (holds mu).
+    // Packs pending requests into slot s and enqueues the request-table copy and the kernel, which
+    // reads the keys from the slot's pinned host buffer and writes the answers to another one over
+    // the host link (no key or answer copies on the batch's critical path) (holds mu).
     void launch(Slot& s) {
         uint64_t nkeys = 0, koff = 0;
         uint32_t nreq = 0;
@@ -256,15 +259,11 @@ struct sfc {
         a.reqs = s.reqs_dev;
         a.n_reqs = nreq;
         a.total = nkeys;
-        a.keys = s.keys_dev;
-        a.out = s.out_dev;
-        cudaError_t e = cudaSuccess;
-        if (koff) e = cudaMemcpyAsync(s.keys_dev, s.keys_host, koff, cudaMemcpyHostToDevice, s.stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(s.reqs_dev, s.reqs_host, nreq * sizeof(sfk::QueryReq), cudaMemcpyHostToDevice, s.stream);
+        a.keys = s.keys_map;
+        a.out = s.out_map;
+        cudaError_t e =
+            cudaMemcpyAsync(s.reqs_dev, s.reqs_host, nreq * sizeof(sfk::QueryReq), cudaMemcpyHostToDevice, s.stream);
         if (e == cudaSuccess) e = sfk::launch_multi_query(a, num_sms, s.stream);
-        if (e == cudaSuccess && nkeys)
-            e = cudaMemcpyAsync(s.out_host, s.out_dev, nkeys * sizeof(uint32_t), cudaMemcpyDeviceToHost, s.stream);
         if (e == cudaSuccess) e = cudaEventRecord(s.ev, s.stream);
         if (e != cudaSuccess) {
             for (auto& r : s.members) r->status = SF_ERR_CUDA;
@@ -306,14 +305,14 @@ sf_status sfc_create(const sfc_config* c, sfc** out) {
     for (uint32_t i = 0; i < c->n_streams; ++i) {
         Slot& s = x->slots[i];
         uint8_t* base = (uint8_t*)c->staging_dev + i * L.slot_bytes;
-        s.keys_dev = base;
-        s.out_dev = (uint32_t*)(base + L.keys_bytes);
-        s.reqs_dev = (sfk::QueryReq*)(base + L.keys_bytes + L.out_bytes);
+        s.reqs_dev = (sfk::QueryReq*)base;
         if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming) != cudaSuccess ||
-            cudaHostAlloc((void**)&s.keys_host, L.keys_bytes, cudaHostAllocDefault) != cudaSuccess ||
-            cudaHostAlloc((void**)&s.out_host, L.out_bytes, cudaHostAllocDefault) != cudaSuccess ||
-            cudaHostAlloc((void**)&s.reqs_host, L.reqs_bytes, cudaHostAllocDefault) != cudaSuccess) {
+            cudaHostAlloc((void**)&s.keys_host, L.keys_bytes, cudaHostAllocMapped) != cudaSuccess ||
+            cudaHostAlloc((void**)&s.out_host, L.out_bytes, cudaHostAllocMapped) != cudaSuccess ||
+            cudaHostAlloc((void**)&s.reqs_host, L.reqs_bytes, cudaHostAllocDefault) != cudaSuccess ||
+            cudaHostGetDevicePointer((void**)&s.keys_map, s.keys_host, 0) != cudaSuccess ||
+            cudaHostGetDevicePointer((void**)&s.out_map, s.out_host, 0) != cudaSuccess) {
             sfc_destroy(x);
             return SF_ERR_CUDA;
         }
