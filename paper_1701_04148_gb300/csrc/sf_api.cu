@@ -66,9 +66,8 @@ sf_status run_update(sf_sketch* s, const void* keys_in, const int8_t* ops_in, in
     const uint32_t kb = s->p.key_bytes;
     if ((kb == 4 || kb == 8) && ((uintptr_t)keys % kb) != 0) return SF_ERR_INVALID;
     if ((s->p.flags & SF_FLAG_EXPLICIT_INDEX) && !s->idx_table) return SF_ERR_INVALID;
-    int cur = -1;
-    if (cudaGetDevice(&cur) != cudaSuccess) return SF_ERR_CUDA;
-    if (cur != s->device && cudaSetDevice(s->device) != cudaSuccess) return SF_ERR_CUDA;
+    DeviceGuard guard(s->device);
+    if (!guard.ok) return SF_ERR_CUDA;
     cudaError_t e;
     if (s->p.chunk == 1) {
         sfk::SeqArgs a{};
@@ -93,7 +92,6 @@ sf_status run_update(sf_sketch* s, const void* keys_in, const int8_t* ops_in, in
         e = sfk::launch_chunk_update(one, s->ctrl, s->bar_epoch, s->claims_cap, s->chunk_grid, s->stream);
         if (e == cudaSuccess) s->bar_epoch += 2ull * ((n + s->p.chunk - 1) / s->p.chunk);
     }
-    if (cur != s->device) cudaSetDevice(cur);
     return e == cudaSuccess ? SF_OK : SF_ERR_CUDA;
 }
 

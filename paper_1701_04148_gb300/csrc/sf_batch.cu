@@ -151,9 +151,8 @@ sf_status sf_batch_update(sf_batch* b, uint32_t n_items, const sf_batch_item* it
         const uint32_t kb = s->p.key_bytes;
         if ((kb == 4 || kb == 8) && ((uintptr_t)b->keys_acc[i] % kb) != 0) return SF_ERR_INVALID;
     }
-    int cur = -1;
-    if (cudaGetDevice(&cur) != cudaSuccess) return SF_ERR_CUDA;
-    if (cur != b->device && cudaSetDevice(b->device) != cudaSuccess) return SF_ERR_CUDA;
+    DeviceGuard guard(b->device);
+    if (!guard.ok) return SF_ERR_CUDA;
     if (b->staging_busy && cudaEventSynchronize(b->staged) != cudaSuccess) return SF_ERR_CUDA;
 
     const int bps = sfk::chunk_update_blocks_per_sm(d);
@@ -237,10 +236,7 @@ sf_status sf_batch_update(sf_batch* b, uint32_t n_items, const sf_batch_item* it
                 may_ins |= R.ops == nullptr;
             }
         }
-        if (flat > b->max_round_slots) {
-            if (cur != b->device) cudaSetDevice(cur);
-            return SF_ERR_INVALID;
-        }
+        if (flat > b->max_round_slots) return SF_ERR_INVALID;
         if (rounds == 0) continue;  // nothing to update in this group
         sfk::BatchArgs a{};
         a.runs = b->table_dev + gr.first;
@@ -299,7 +295,6 @@ sf_status sf_batch_update(sf_batch* b, uint32_t n_items, const sf_batch_item* it
     if (!launched) e = enqueue(b, b->plan, d, grid, table_bytes, b->stream);
     if (e == cudaSuccess) e = cudaEventRecord(b->staged, b->stream);
     b->staging_busy = true;
-    if (cur != b->device) cudaSetDevice(cur);
     return e == cudaSuccess ? SF_OK : SF_ERR_CUDA;
 }
 

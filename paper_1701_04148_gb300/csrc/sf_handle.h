@@ -34,6 +34,26 @@ inline sf_status sf_device_access(const void* p, const void** out) {
     }
 }
 
+// Makes `dev` the current device for the scope of a call and restores the caller's device on
+// every return path.
+struct DeviceGuard {
+    int prev = -1;
+    bool switched = false, ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) return;
+        if (prev != dev) {
+            if (cudaSetDevice(dev) != cudaSuccess) return;
+            switched = true;
+        }
+        ok = true;
+    }
+    ~DeviceGuard() {
+        if (switched) cudaSetDevice(prev);
+    }
+    DeviceGuard(const DeviceGuard&) = delete;
+    DeviceGuard& operator=(const DeviceGuard&) = delete;
+};
+
 struct sf_sketch {
     sf_params p;
     uint32_t* A;
