@@ -223,7 +223,8 @@ def main():
     ap.add_argument("--ref-queries", type=int, default=20_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["all", "flows", "batch", "serve", "accuracy", "pipeline", "profile"],
+    ap.add_argument("--workload", choices=["all", "flows", "batch", "serve", "accuracy", "pipeline", "profile",
+                                           "l2curve"],
                     default="all",
                     help="all: the flows line with the batched and serving results embedded; profile: the small "
                          "fixed case the committed ncu summaries capture (two insert launches, the second profiled)")
@@ -281,6 +282,8 @@ def main():
         line = run_pipeline(args, ctx)
     if args.workload == "profile":
         line = run_profile(args, ctx)
+    if args.workload == "l2curve":
+        line = run_l2curve(args, ctx)
     if args.workload in ("all", "serve"):
         v = run_serve(args, ctx)
         if line is None:
@@ -621,6 +624,48 @@ def run_profile(args, ctx):
     return {"workload": "profile", "inserts": int(ins.shape[0]), "zipf": args.profile_zipf,
             "insert_ms": round(ms, 4), "M_inserts_per_s": round(ins.shape[0] / ms / 1e3, 1),
             "query_mean": float(q.to(torch.float64).mean())}
+
+
+def run_l2curve(args, ctx):
+    """Random 32-bit loads, reductions and the 1:1 mix (sf_bench_random_access kinds 2, 0, 5;
+    2^28 operations, best of three) over buffers of 32-160 MiB: where the L2 stops holding a
+    random working set."""
+    import torch
+    L, dev, stream = ctx["L"], ctx["dev"], ctx["stream"]
+    mib = 1 << 20
+    buf = torch.zeros((160 * mib) // 4, dtype=torch.int32, device=dev)
+    h_st = int(stream.cuda_stream)
+    rows = []
+    for size in (32, 48, 56, 60, 64, 68, 72, 76, 80, 88, 96, 112, 128, 160):
+        n = size * mib // 4
+        row = {"mib": size}
+        for name, kind in (("ld", 2), ("red", 0), ("mix", 5)):
+            L.sf_bench_random_access(buf.data_ptr(), n, 1 << 26, kind, 0, h_st)
+            best = 0.0
+            for _ in range(3):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                rc = L.sf_bench_random_access(buf.data_ptr(), n, 1 << 28, kind, 0, h_st)
+                b.record(stream)
+                torch.cuda.synchronize()
+                if rc != 0:
+                    raise SystemExit(f"sf_bench_random_access failed: {rc}")
+                best = max(best, (1 << 28) / a.elapsed_time(b) / 1e6)
+            row[name] = round(best, 1)
+        rows.append(row)
+    del buf
+    # one grid barrier of the persistent update kernel's kind (cooperative, one block per SM)
+    scr = torch.zeros(64, dtype=torch.int32, device=dev)
+    L.sf_bench_grid_barrier(scr.data_ptr(), 100, h_st)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    rc = L.sf_bench_grid_barrier(scr.data_ptr(), 2000, h_st)
+    b.record(stream)
+    torch.cuda.synchronize()
+    if rc != 0:
+        raise SystemExit(f"sf_bench_grid_barrier failed: {rc}")
+    return {"workload": "l2curve", "unit": "G random 32-bit ops/s", "rows": rows,
+            "grid_barrier_us": round(a.elapsed_time(b) * 1e3 / 2000, 3)}
 
 
 def run_accuracy(args, ctx):
