@@ -69,7 +69,10 @@ sf_status run_update(sf_sketch* s, const void* keys_in, const int8_t* ops_in, in
     DeviceGuard guard(s->device);
     if (!guard.ok) return SF_ERR_CUDA;
     cudaError_t e;
-    if (s->p.chunk == 1) {
+    if (s->p.chunk == 1 && s->dag_ws && !ops && op_const > 0) {
+        // insertions only: the dependency-graph path (sf_seqdag.cu)
+        e = sfk::launch_seq_dag(desc_of(s), (const uint8_t*)keys, n, s->dag_ws, s->ctrl, s->smem_optin, s->stream);
+    } else if (s->p.chunk == 1) {
         sfk::SeqArgs a{};
         a.s = desc_of(s);
         a.keys = (const uint8_t*)keys;
@@ -121,7 +124,9 @@ sf_status sf_required_bytes(const sf_params* p, uint64_t* fat_bytes, uint64_t* s
     if (slim_bytes) *slim_bytes = (uint64_t)p->d * p->w * 4ull;
     if (scratch_bytes) {
         const uint64_t cap = p->chunk > 1 ? sfk::dict_capacity(p->chunk) : 0;
-        *scratch_bytes = kCtrlBytes + cap * sizeof(sfk::DictEntry);
+        // S = 1 sketches wide enough for the dependency-graph path also hold its workspace
+        const uint64_t dag = (p->chunk == 1 && p->w >= sfk::kDagMinW) ? sfk::dag_workspace_bytes(p->d) : 0;
+        *scratch_bytes = kCtrlBytes + cap * sizeof(sfk::DictEntry) + dag;
     }
     return SF_OK;
 }
@@ -143,6 +148,7 @@ sf_status sf_create(const sf_params* p, void* fat_dev, void* slim_dev, void* scr
     s->ctrl = (uint32_t*)scratch_dev;
     s->dict = (sfk::DictEntry*)((uint8_t*)scratch_dev + kCtrlBytes);
     s->cap = p->chunk > 1 ? sfk::dict_capacity(p->chunk) : 0;
+    s->dag_ws = (p->chunk == 1 && p->w >= sfk::kDagMinW) ? (uint8_t*)scratch_dev + kCtrlBytes : nullptr;
     uint64_t st = p->seed;
     for (uint32_t i = 0; i < SF_MAX_D; ++i) s->rs[i] = i < p->d ? splitmix64_next(&st) : 0;
     if (cudaGetDevice(&s->device) != cudaSuccess ||

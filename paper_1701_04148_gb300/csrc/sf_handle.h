@@ -72,5 +72,6 @@ struct sf_sketch {
     uint32_t n_ids;
     uint64_t bar_epoch;     // grid barriers passed on this scratch buffer (monotonic counter)
     uint32_t claims_cap;    // per-block claim list length of the chunk kernel
+    void* dag_ws;           // S = 1 sketches of width >= kDagMinW: workspace of the graph path, else nullptr
 };
 

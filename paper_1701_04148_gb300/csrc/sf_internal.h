@@ -95,6 +95,14 @@ cudaError_t launch_chunk_update(const SketchRun& one, uint32_t* ctrl, uint64_t b
                                 int grid, cudaStream_t st);
 // One-at-a-time update (S = 1).
 cudaError_t launch_seq_update(const SeqArgs& a, cudaStream_t st, int smem_limit);
+// One-at-a-time insertions as a dependency graph over pieces of up to kDagN updates (sf_seqdag.cu):
+// for insertion-only calls on sketches of width >= kDagMinW, with a workspace of
+// dag_workspace_bytes(d) bytes (4-byte aligned) owned by the sketch.
+constexpr uint32_t kDagN = 131072;
+constexpr uint32_t kDagMinW = 1024;
+uint64_t dag_workspace_bytes(uint32_t d);
+cudaError_t launch_seq_dag(const SketchDesc& s, const uint8_t* keys, uint64_t n, void* ws_base, uint32_t* ctrl,
+                           int smem_limit, cudaStream_t st);
 // Point queries.
 cudaError_t launch_query(const QueryArgs& a, int num_sms, cudaStream_t st);
 cudaError_t launch_multi_query(const MultiQueryArgs& a, int num_sms, cudaStream_t st);

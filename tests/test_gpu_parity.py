@@ -98,6 +98,49 @@ def test_one_at_a_time_windows(sf, del_frac, d, w, z):
     _queries_match(sf, g, o, ids)
 
 
+@pytest.mark.parametrize("d,w,z,kb,s_,n", [
+    (4, 4096, 16, 4, 1.0, 100_000),      # the C1 shape
+    (1, 1024, 16, 4, 1.5, 50_000),       # one row, hot keys: long runs
+    (8, 2048, 7, 13, 1.1, 60_000),       # eight rows, 13-byte keys, odd bucket size
+    (3, 1 << 14, 16, 8, 0.8, 300_001),   # several pieces of the graph path, a ragged last one
+])
+def test_one_at_a_time_insertions_graph_path(sf, d, w, z, kb, s_, n):
+    """S = 1 insertion-only calls on sketches of width >= 1024 take the dependency-graph path:
+    every counter and query equals the oracle's literal one-at-a-time rule, over two calls."""
+    import torch
+    st, ids = wl.mixed_stream(n, 5_000, s_, 0.0, 4, seed=d * 1000 + w % 997 + n % 13)
+    keys = st.keys if kb == 4 else torch.cat([st.keys] * 4, 1)[:, :kb].contiguous()
+    qk = ids if kb == 4 else torch.cat([ids] * 4, 1)[:, :kb].contiguous()
+    h = n // 3
+    g, o = _run_both(sf, d, w, z, kb, 21, 1, [(keys[:h], None), (keys[h:], None)])
+    _assert_same(g, o)
+    _queries_match(sf, g, o, qk)
+
+
+def test_one_at_a_time_graph_path_pinned_keys_and_explicit_ids(sf):
+    import torch
+    st, ids = wl.mixed_stream(40_000, 2_000, 1.2, 0.0, 4, seed=77)
+    a = sf.Sketch(4, 2048, 16, 4, 5, 1)
+    b = sf.Sketch(4, 2048, 16, 4, 5, 1)
+    a.insert(st.keys.cuda())
+    b.insert(st.keys.cpu().pin_memory())
+    a.sync()
+    b.sync()
+    assert torch.equal(a.fat, b.fat) and torch.equal(a.slim, b.slim)
+    # explicit-index mode: key ids into a table of (h_i, f_i)
+    gen = np.random.default_rng(3)
+    table = np.stack([gen.integers(0, 2048, (500, 4)), gen.integers(0, 16, (500, 4))], axis=2).astype(np.uint32)
+    idx = gen.integers(0, 500, 30_000).astype(np.uint32)
+    g = sf.Sketch(4, 2048, 16, 4, 0, 1, explicit_index=True)
+    g.set_index_table(torch.from_numpy(table.view(np.int32)).cuda())
+    g.insert(torch.from_numpy(idx.view(np.int32)).cuda())
+    g.sync()
+    o = oracle.Sketch(4, 2048, 16, 4, 0)
+    hh, ff, ident = oracle.explicit_indices(table, idx)
+    o.seq_apply(hh, ff, np.ones(len(idx), np.int8))
+    _assert_same(g, o)
+
+
 @pytest.mark.parametrize("n", [1, 31, 32, 33, 64, 65, 97])
 def test_one_at_a_time_short_streams(sf, n):
     """S = 1 on lengths around the 32-update window and the two-window key prefetch."""
