@@ -224,7 +224,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", choices=["all", "flows", "batch", "serve", "accuracy", "pipeline", "profile",
-                                           "l2curve"],
+                                           "l2curve", "seq"],
                     default="all",
                     help="all: the flows line with the batched and serving results embedded; profile: the small "
                          "fixed case the committed ncu summaries capture (two insert launches, the second profiled)")
@@ -284,6 +284,8 @@ def main():
         line = run_profile(args, ctx)
     if args.workload == "l2curve":
         line = run_l2curve(args, ctx)
+    if args.workload == "seq":
+        line = run_seq(args, ctx)
     if args.workload in ("all", "serve"):
         v = run_serve(args, ctx)
         if line is None:
@@ -624,6 +626,50 @@ def run_profile(args, ctx):
     return {"workload": "profile", "inserts": int(ins.shape[0]), "zipf": args.profile_zipf,
             "insert_ms": round(ms, 4), "M_inserts_per_s": round(ins.shape[0] / ms / 1e3, 1),
             "query_mean": float(q.to(torch.float64).mean())}
+
+
+def run_seq(args, ctx):
+    """The paper's one-at-a-time rule (chunk 1) on the insertion-only u32 workload: 100,000 keys
+    Zipf(1.0) over 10,000 ids, d=4, w=4096, z=16; then all 10,000 ids queried.  GPU time of the
+    insert call (best of --steps after --warmup), the CPU oracle's time for the same stream on one
+    core, and a counter-by-counter check."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_1701_04148_gb300 as sf
+    import workloads as wl
+    dev, stream = ctx["dev"], ctx["stream"]
+    keys, ids = wl.insert_only_u32(100_000, 10_000, 1.0, seed=1)
+    kd, qd = keys.to(dev), ids.to(dev)
+    g = sf.Sketch(4, 4096, 16, 4, 1, 1, stream=stream)
+    for _ in range(args.warmup):
+        g.reset()
+        g.insert(kd)
+    best = float("inf")
+    for _ in range(args.steps):
+        g.reset()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        g.insert(kd)
+        b.record(stream)
+        torch.cuda.synchronize()
+        best = min(best, a.elapsed_time(b))
+    slim, hdr = g.export_slim()
+    est = sf.query(slim, hdr, qd, stream=stream)
+    st = g.sync_status()
+    o = oracle.Sketch(4, 4096, 16, 4, 1)
+    t0 = time.perf_counter()
+    o.update(keys.numpy(), np.ones(len(keys), np.int8), S=None)
+    t_cpu = time.perf_counter() - t0
+    exact = (st == sf.SF_OK
+             and np.array_equal(g.fat.cpu().numpy().view(np.uint32).reshape(o.B.shape), o.B)
+             and np.array_equal(slim.cpu().numpy().view(np.uint32).reshape(o.A.shape), o.A)
+             and np.array_equal(est.cpu().numpy().view(np.uint32), o.query(ids.numpy())))
+    return {"workload": "one-at-a-time-insert-u32", "updates": len(keys), "gpu_ms": round(best, 3),
+            "gpu_M_updates_per_s": round(len(keys) / best / 1e3, 1), "oracle_ms_one_core": round(t_cpu * 1e3, 3),
+            "speedup_vs_oracle": round(t_cpu * 1e3 / best, 2), "bit_exact": bool(exact)}
 
 
 def run_l2curve(args, ctx):

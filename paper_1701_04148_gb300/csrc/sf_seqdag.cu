@@ -239,32 +239,44 @@ __global__ void __launch_bounds__(256) dag_count_kernel(DagWs w, const uint32_t*
     atomicMax(&w.lastm[hd], j);
 }
 
-// 3d. pending predecessors of every head (one per row that has one); heads without any start
-__global__ void __launch_bounds__(256) dag_npred_kernel(DagWs w, const uint32_t* __restrict__ head, uint32_t n,
-                                                        uint32_t d) {
+// 3d. pending predecessors of every head (one per row that has one), and its successors: the
+//     next update, in each row's bucket, after the run's last member -- always another run's
+//     head, since a run member's predecessors are all inside its run.  Heads without any
+//     predecessor start the walk.
+__global__ void __launch_bounds__(256) dag_npred_kernel(DagWs w, const uint32_t* __restrict__ head,
+                                                        uint32_t* __restrict__ succ_head, uint32_t n, uint32_t d) {
     const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n || head[j] != j) return;
+    const uint32_t l = w.lastm[j];
     uint32_t c = 0;
-    for (uint32_t i = 0; i < d; ++i) c += w.pred[i * kDagN + j] != kDagNone ? 1u : 0u;
+    for (uint32_t i = 0; i < d; ++i) {
+        c += w.pred[i * kDagN + j] != kDagNone ? 1u : 0u;
+        succ_head[i * kDagN + j] = w.succ[i * kDagN + l];
+    }
     w.npred[j] = c;
     if (c == 0) w.q0[atomicAdd(&w.qcount[0], 1u)] = j;
 }
 
-// 4. the graph walk, one block; the Slim in shared memory when slim_in_smem, else in place
+// 4. the graph walk, one block; the Slim in shared memory when slim_in_smem, else in place.  The
+//    frontier queues live in shared memory up to kDagQCap entries, the rest in the global queues.
+constexpr uint32_t kDagQCap = 4096;
+
 __global__ void __launch_bounds__(kDagExecThreads, 1) dag_exec_kernel(SketchDesc s, DagWs w,
-                                                                      const uint32_t* __restrict__ head, uint32_t n,
+                                                                      const uint32_t* __restrict__ succ_head, uint32_t n,
                                                                       int slim_in_smem, uint32_t* ctrl) {
     extern __shared__ uint32_t sA[];
+    __shared__ uint32_t s_q[2][kDagQCap];
+    __shared__ uint32_t s_next;
     const uint64_t slim_n = (uint64_t)s.d * s.w;
     if (slim_in_smem) {
         for (uint64_t i = threadIdx.x; i < slim_n; i += blockDim.x) sA[i] = __ldcg(s.A + i);
     }
     uint32_t* A = slim_in_smem ? sA : s.A;
-    __shared__ uint32_t s_next;
-    uint32_t* cur = w.q0;
-    uint32_t* nxt = w.q1;
-    __syncthreads();
     uint32_t ncur = __ldcg(&w.qcount[0]);
+    for (uint32_t q = threadIdx.x; q < ncur && q < kDagQCap; q += blockDim.x) s_q[0][q] = __ldcg(w.q0 + q);
+    uint32_t* gq[2] = {w.q0, w.q1};
+    uint32_t cb = 0;  // which queue holds the current frontier
+    __syncthreads();
     for (uint32_t step = 0; ncur > 0; ++step) {
         if (step > n) {  // a graph of n updates has at most n levels
             if (threadIdx.x == 0) atomicOr(ctrl + kCtrlErr, kErrTimeout);
@@ -272,19 +284,37 @@ __global__ void __launch_bounds__(kDagExecThreads, 1) dag_exec_kernel(SketchDesc
         }
         if (threadIdx.x == 0) s_next = 0u;
         __syncthreads();
+        const uint32_t nb = cb ^ 1u;
         for (uint32_t q = threadIdx.x; q < ncur; q += blockDim.x) {
-            const uint32_t j = __ldcg(cur + q);
-            if (!w.bad[j]) {
-                const uint32_t r = w.rlen[j];
-                uint32_t hb[kMaxD], F = 0xFFFFFFFFu, m = 0xFFFFFFFFu;
+            const uint32_t j = q < kDagQCap ? s_q[cb][q] : __ldcg(gq[cb] + q);
+            const bool live = !w.bad[j];
+            const uint32_t r = w.rlen[j];
+            uint32_t hb[kMaxD], sx[kMaxD], F = 0xFFFFFFFFu, m = 0xFFFFFFFFu;
 #pragma unroll
-                for (int i = 0; i < kMaxD; ++i) {
-                    if (i < (int)s.d) {
-                        hb[i] = w.hb[i * kDagN + j];
-                        uint32_t* c = s.B + ((uint64_t)i * s.w + hb[i]) * s.z + w.fb[i * kDagN + j];
-                        F = min(F, atomicAdd(c, r) + r);
-                    }
+            for (int i = 0; i < kMaxD; ++i) {
+                hb[i] = 0u;
+                sx[i] = kDagNone;
+                if (i < (int)s.d) {
+                    hb[i] = w.hb[i * kDagN + j];
+                    sx[i] = succ_head[i * kDagN + j];
                 }
+            }
+            // the run's Fat increments and its successors' pending counts, all in flight together
+            // (every return value is collected before any is used)
+            uint32_t old_v[kMaxD], left[kMaxD];
+#pragma unroll
+            for (int i = 0; i < kMaxD; ++i) {
+                old_v[i] = 0u;
+                left[i] = 0xFFFFFFFFu;
+                if (i < (int)s.d) {
+                    if (live) old_v[i] = atomicAdd(s.B + ((uint64_t)i * s.w + hb[i]) * s.z + w.fb[i * kDagN + j], r);
+                    if (sx[i] != kDagNone) left[i] = atomicSub(&w.npred[sx[i]], 1u);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < kMaxD; ++i)
+                if (i < (int)s.d) F = min(F, old_v[i] + r);
+            if (live) {
 #pragma unroll
                 for (int i = 0; i < kMaxD; ++i)
                     if (i < (int)s.d) m = min(m, A[(uint64_t)i * s.w + hb[i]]);
@@ -294,20 +324,18 @@ __global__ void __launch_bounds__(kDagExecThreads, 1) dag_exec_kernel(SketchDesc
                 for (int i = 0; i < kMaxD; ++i)
                     if (i < (int)s.d && A[(uint64_t)i * s.w + hb[i]] < T) A[(uint64_t)i * s.w + hb[i]] = T;
             }
-            const uint32_t l = w.lastm[j];
-            for (uint32_t i = 0; i < s.d; ++i) {
-                const uint32_t sx = w.succ[i * kDagN + l];
-                if (sx != kDagNone) {
-                    const uint32_t k = head[sx];
-                    if (atomicSub(&w.npred[k], 1u) == 1u) nxt[atomicAdd(&s_next, 1u)] = k;
+#pragma unroll
+            for (int i = 0; i < kMaxD; ++i) {
+                if (i < (int)s.d && left[i] == 1u) {  // the last pending predecessor of that head
+                    const uint32_t idx = atomicAdd(&s_next, 1u);
+                    if (idx < kDagQCap) s_q[nb][idx] = sx[i];
+                    else gq[nb][idx] = sx[i];
                 }
             }
         }
         __syncthreads();
         ncur = s_next;
-        uint32_t* t = cur;
-        cur = nxt;
-        nxt = t;
+        cb = nb;
         __syncthreads();
     }
     if (slim_in_smem) {
@@ -324,7 +352,7 @@ cudaError_t launch_seq_dag(const SketchDesc& s, const uint8_t* keys, uint64_t n,
                            int smem_limit, cudaStream_t st) {
     const DagWs w = dag_carve(ws_base, s.d);
     const uint64_t slim_bytes = (uint64_t)s.d * s.w * 4ull;
-    const int slim_in_smem = slim_bytes + 1024 <= (uint64_t)smem_limit ? 1 : 0;
+    const int slim_in_smem = slim_bytes + 2 * kDagQCap * 4 + 1024 <= (uint64_t)smem_limit ? 1 : 0;
     if (slim_in_smem) {
         cudaError_t e = cudaFuncSetAttribute(dag_exec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)slim_bytes);
@@ -365,8 +393,10 @@ cudaError_t launch_seq_dag(const SketchDesc& s, const uint8_t* keys, uint64_t n,
         dag_count_kernel<<<blocks, 256, 0, st>>>(ws, pa, nc);
         cudaError_t e = cudaMemsetAsync(w.qcount, 0, 16, st);
         if (e != cudaSuccess) return e;
-        dag_npred_kernel<<<blocks, 256, 0, st>>>(ws, pa, nc, s.d);
-        dag_exec_kernel<<<1, kDagExecThreads, slim_in_smem ? (size_t)slim_bytes : 0, st>>>(s, ws, pa, nc,
+        // successors of each run go to the first sort buffer that does not hold the sorted rows
+        uint32_t* succ_head = (ki == w.sk0) ? w.sk1 : w.sk0;
+        dag_npred_kernel<<<blocks, 256, 0, st>>>(ws, pa, succ_head, nc, s.d);
+        dag_exec_kernel<<<1, kDagExecThreads, slim_in_smem ? (size_t)slim_bytes : 0, st>>>(s, ws, succ_head, nc,
                                                                                         slim_in_smem, ctrl);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
