@@ -121,7 +121,9 @@ const char *sf_status_str(sf_status s);
  *   fat_bytes     = d*w*z*4, layout B[((i*w + j)*z + k]  (bucket-contiguous, Sec. 3.4: all z
  *                   counters of a bucket sit together so one access reads them)
  *   slim_bytes    = d*w*4,   layout A[i*w + j]
- *   scratch_bytes = control words + the per-chunk key dictionary (grows with params.chunk)
+ *   scratch_bytes = control words + the per-chunk key dictionary (grows with params.chunk);
+ *                   sketches with chunk == 1 and w >= 1024 also hold the one-at-a-time
+ *                   dependency-graph workspace (about (16 + 8d) * 512 KiB)
  * Any output pointer may be NULL.  Returns SF_ERR_INVALID for parameters out of range.
  */
 sf_status sf_required_bytes(const sf_params *p, uint64_t *fat_bytes, uint64_t *slim_bytes,

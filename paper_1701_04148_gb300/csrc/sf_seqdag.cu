@@ -34,6 +34,7 @@ constexpr int kDagExecThreads = 1024;
 
 // Workspace arrays of one piece (kDagN updates, d rows), carved out of the sketch scratch.
 struct DagWs {
+    uint4* rec;                   // [N][4G] walk record of every run head (dag_npred_kernel)
     uint32_t *hb, *fb;            // [d][N] bucket and slot of every update
     uint32_t *sk0, *sv0, *sk1, *sv1;  // [d][N] radix sort keys (buckets) and values (positions)
     uint32_t *pred, *succ;        // [d][N] previous / next update in the same bucket
@@ -46,15 +47,21 @@ struct DagWs {
     uint32_t *hist;               // [d][bins][tiles] digit counts, then offsets
 };
 
+// A walk record holds G = ceil(d / 4) uint4 groups each of buckets, Fat slots and successor
+// heads, then the run length: 4G uint4 (64 bytes for d <= 4, 128 for d <= 8).
+__host__ __device__ inline uint32_t dag_groups(uint32_t d) { return d <= 4 ? 1u : 2u; }
+
 __host__ __device__ inline uint64_t dag_bytes_for(uint32_t d) {
     const uint64_t N = kDagN;
-    return (8ull * d * N + 8ull * N + 64ull + (uint64_t)d * kDagBins * kDagTiles) * 4ull;
+    return (16ull * dag_groups(d) * N + 8ull * d * N + 8ull * N + 64ull + (uint64_t)d * kDagBins * kDagTiles) * 4ull;
 }
 
 DagWs dag_carve(void* base, uint32_t d) {
     uint32_t* p = static_cast<uint32_t*>(base);
     const uint64_t N = kDagN;
     DagWs w;
+    w.rec = reinterpret_cast<uint4*>(p);
+    p += 16 * dag_groups(d) * N;
     w.hb = p;
     p += d * N;
     w.fb = p;
@@ -241,40 +248,66 @@ __global__ void __launch_bounds__(256) dag_count_kernel(DagWs w, const uint32_t*
 
 // 3d. pending predecessors of every head (one per row that has one), and its successors: the
 //     next update, in each row's bucket, after the run's last member -- always another run's
-//     head, since a run member's predecessors are all inside its run.  Heads without any
-//     predecessor start the walk.
-__global__ void __launch_bounds__(256) dag_npred_kernel(DagWs w, const uint32_t* __restrict__ head,
-                                                        uint32_t* __restrict__ succ_head, uint32_t n, uint32_t d) {
+//     head, since a run member's predecessors are all inside its run.  Everything the walk needs
+//     of a head goes into its 64-byte record: buckets, Fat slots, successor heads, and the run
+//     length (0 for an update that does nothing).  Heads without any predecessor start the walk.
+__global__ void __launch_bounds__(256) dag_npred_kernel(DagWs w, const uint32_t* __restrict__ head, uint32_t n,
+                                                        uint32_t d) {
     const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n || head[j] != j) return;
     const uint32_t l = w.lastm[j];
-    uint32_t c = 0;
-    for (uint32_t i = 0; i < d; ++i) {
-        c += w.pred[i * kDagN + j] != kDagNone ? 1u : 0u;
-        succ_head[i * kDagN + j] = w.succ[i * kDagN + l];
+    uint32_t c = 0, hb[kMaxD], fb[kMaxD], sx[kMaxD];
+#pragma unroll
+    for (int i = 0; i < kMaxD; ++i) {
+        hb[i] = fb[i] = 0u;
+        sx[i] = kDagNone;
+        if (i < (int)d) {
+            c += w.pred[i * kDagN + j] != kDagNone ? 1u : 0u;
+            hb[i] = w.hb[i * kDagN + j];
+            fb[i] = w.fb[i * kDagN + j];
+            sx[i] = w.succ[i * kDagN + l];
+        }
     }
+    const uint32_t G = dag_groups(d);
+    uint4* r = w.rec + 4ull * G * j;
+#pragma unroll
+    for (uint32_t g = 0; g < 2; ++g) {
+        if (g < G) {
+            r[g] = make_uint4(hb[4 * g], hb[4 * g + 1], hb[4 * g + 2], hb[4 * g + 3]);
+            r[G + g] = make_uint4(fb[4 * g], fb[4 * g + 1], fb[4 * g + 2], fb[4 * g + 3]);
+            r[2 * G + g] = make_uint4(sx[4 * g], sx[4 * g + 1], sx[4 * g + 2], sx[4 * g + 3]);
+        }
+    }
+    r[3 * G] = make_uint4(w.bad[j] ? 0u : w.rlen[j], 0u, 0u, 0u);
     w.npred[j] = c;
     if (c == 0) w.q0[atomicAdd(&w.qcount[0], 1u)] = j;
 }
 
-// 4. the graph walk, one block; the Slim in shared memory when slim_in_smem, else in place.  The
-//    frontier queues live in shared memory up to kDagQCap entries, the rest in the global queues.
+// 4. the graph walk, one block; the Slim in shared memory (kSmemSlim) or in place.  The frontier
+//    queues live in shared memory up to kDagQCap entries, the rest in the global queues.  A
+//    level's cost is its longest chain of dependent memory round trips, so each head's record
+//    comes in four vector loads, and while a head's atomics are in flight the records of its
+//    successors are prefetched into L1 for the next level.
 constexpr uint32_t kDagQCap = 4096;
 
-__global__ void __launch_bounds__(kDagExecThreads, 1) dag_exec_kernel(SketchDesc s, DagWs w,
-                                                                      const uint32_t* __restrict__ succ_head, uint32_t n,
-                                                                      int slim_in_smem, uint32_t* ctrl) {
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
+template <bool kSmemSlim>
+__global__ void __launch_bounds__(kDagExecThreads, 1) dag_exec_kernel(SketchDesc s, DagWs w, uint32_t n,
+                                                                      uint32_t* ctrl) {
     extern __shared__ uint32_t sA[];
     __shared__ uint32_t s_q[2][kDagQCap];
     __shared__ uint32_t s_next;
     const uint64_t slim_n = (uint64_t)s.d * s.w;
-    if (slim_in_smem) {
+    if (kSmemSlim) {
         for (uint64_t i = threadIdx.x; i < slim_n; i += blockDim.x) sA[i] = __ldcg(s.A + i);
     }
-    uint32_t* A = slim_in_smem ? sA : s.A;
+    uint32_t* A = kSmemSlim ? sA : s.A;
+    const uint32_t G = dag_groups(s.d);
     uint32_t ncur = __ldcg(&w.qcount[0]);
     for (uint32_t q = threadIdx.x; q < ncur && q < kDagQCap; q += blockDim.x) s_q[0][q] = __ldcg(w.q0 + q);
-    uint32_t* gq[2] = {w.q0, w.q1};
     uint32_t cb = 0;  // which queue holds the current frontier
     __syncthreads();
     for (uint32_t step = 0; ncur > 0; ++step) {
@@ -285,20 +318,25 @@ __global__ void __launch_bounds__(kDagExecThreads, 1) dag_exec_kernel(SketchDesc
         if (threadIdx.x == 0) s_next = 0u;
         __syncthreads();
         const uint32_t nb = cb ^ 1u;
+        uint32_t* gcur = cb ? w.q1 : w.q0;
+        uint32_t* gnext = cb ? w.q0 : w.q1;
         for (uint32_t q = threadIdx.x; q < ncur; q += blockDim.x) {
-            const uint32_t j = q < kDagQCap ? s_q[cb][q] : __ldcg(gq[cb] + q);
-            const bool live = !w.bad[j];
-            const uint32_t r = w.rlen[j];
-            uint32_t hb[kMaxD], sx[kMaxD], F = 0xFFFFFFFFu, m = 0xFFFFFFFFu;
+            const uint32_t j = q < kDagQCap ? s_q[cb][q] : __ldcg(gcur + q);
+            const uint4* rj = w.rec + 4ull * G * j;
+            uint32_t hb[kMaxD], fb[kMaxD], sx[kMaxD];
 #pragma unroll
-            for (int i = 0; i < kMaxD; ++i) {
-                hb[i] = 0u;
-                sx[i] = kDagNone;
-                if (i < (int)s.d) {
-                    hb[i] = w.hb[i * kDagN + j];
-                    sx[i] = succ_head[i * kDagN + j];
+            for (uint32_t g = 0; g < 2; ++g) {
+                uint4 h4 = make_uint4(0u, 0u, 0u, 0u), f4 = h4, x4 = make_uint4(kDagNone, kDagNone, kDagNone, kDagNone);
+                if (g < G) {
+                    h4 = __ldg(rj + g);
+                    f4 = __ldg(rj + G + g);
+                    x4 = __ldg(rj + 2 * G + g);
                 }
+                hb[4 * g] = h4.x, hb[4 * g + 1] = h4.y, hb[4 * g + 2] = h4.z, hb[4 * g + 3] = h4.w;
+                fb[4 * g] = f4.x, fb[4 * g + 1] = f4.y, fb[4 * g + 2] = f4.z, fb[4 * g + 3] = f4.w;
+                sx[4 * g] = x4.x, sx[4 * g + 1] = x4.y, sx[4 * g + 2] = x4.z, sx[4 * g + 3] = x4.w;
             }
+            const uint32_t r = __ldg(&rj[3 * G].x);
             // the run's Fat increments and its successors' pending counts, all in flight together
             // (every return value is collected before any is used)
             uint32_t old_v[kMaxD], left[kMaxD];
@@ -307,29 +345,38 @@ __global__ void __launch_bounds__(kDagExecThreads, 1) dag_exec_kernel(SketchDesc
                 old_v[i] = 0u;
                 left[i] = 0xFFFFFFFFu;
                 if (i < (int)s.d) {
-                    if (live) old_v[i] = atomicAdd(s.B + ((uint64_t)i * s.w + hb[i]) * s.z + w.fb[i * kDagN + j], r);
+                    if (r != 0u) old_v[i] = atomicAdd(s.B + ((uint64_t)i * s.w + hb[i]) * s.z + fb[i], r);
                     if (sx[i] != kDagNone) left[i] = atomicSub(&w.npred[sx[i]], 1u);
                 }
             }
 #pragma unroll
             for (int i = 0; i < kMaxD; ++i)
-                if (i < (int)s.d) F = min(F, old_v[i] + r);
-            if (live) {
+                if (i < (int)s.d && sx[i] != kDagNone) prefetch_l1(w.rec + 4ull * G * sx[i]);
+            if (r != 0u) {
+                uint32_t F = 0xFFFFFFFFu, m = 0xFFFFFFFFu, a[kMaxD];
+#pragma unroll
+                for (int i = 0; i < kMaxD; ++i) {
+                    a[i] = 0u;
+                    if (i < (int)s.d) {
+                        a[i] = A[(uint64_t)i * s.w + hb[i]];
+                        m = min(m, a[i]);
+                    }
+                }
 #pragma unroll
                 for (int i = 0; i < kMaxD; ++i)
-                    if (i < (int)s.d) m = min(m, A[(uint64_t)i * s.w + hb[i]]);
+                    if (i < (int)s.d) F = min(F, old_v[i] + r);
                 const uint64_t mr = (uint64_t)m + r;
                 const uint32_t T = mr < (uint64_t)F ? (uint32_t)mr : F;
 #pragma unroll
                 for (int i = 0; i < kMaxD; ++i)
-                    if (i < (int)s.d && A[(uint64_t)i * s.w + hb[i]] < T) A[(uint64_t)i * s.w + hb[i]] = T;
+                    if (i < (int)s.d && a[i] < T) A[(uint64_t)i * s.w + hb[i]] = T;
             }
 #pragma unroll
             for (int i = 0; i < kMaxD; ++i) {
                 if (i < (int)s.d && left[i] == 1u) {  // the last pending predecessor of that head
                     const uint32_t idx = atomicAdd(&s_next, 1u);
                     if (idx < kDagQCap) s_q[nb][idx] = sx[i];
-                    else gq[nb][idx] = sx[i];
+                    else gnext[idx] = sx[i];
                 }
             }
         }
@@ -338,7 +385,7 @@ __global__ void __launch_bounds__(kDagExecThreads, 1) dag_exec_kernel(SketchDesc
         cb = nb;
         __syncthreads();
     }
-    if (slim_in_smem) {
+    if (kSmemSlim) {
         __syncthreads();
         for (uint64_t i = threadIdx.x; i < slim_n; i += blockDim.x) s.A[i] = sA[i];
     }
@@ -352,9 +399,9 @@ cudaError_t launch_seq_dag(const SketchDesc& s, const uint8_t* keys, uint64_t n,
                            int smem_limit, cudaStream_t st) {
     const DagWs w = dag_carve(ws_base, s.d);
     const uint64_t slim_bytes = (uint64_t)s.d * s.w * 4ull;
-    const int slim_in_smem = slim_bytes + 2 * kDagQCap * 4 + 1024 <= (uint64_t)smem_limit ? 1 : 0;
+    const bool slim_in_smem = slim_bytes + 2 * kDagQCap * 4 + 1024 <= (uint64_t)smem_limit;
     if (slim_in_smem) {
-        cudaError_t e = cudaFuncSetAttribute(dag_exec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(dag_exec_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)slim_bytes);
         if (e != cudaSuccess) return e;
     }
@@ -393,11 +440,11 @@ cudaError_t launch_seq_dag(const SketchDesc& s, const uint8_t* keys, uint64_t n,
         dag_count_kernel<<<blocks, 256, 0, st>>>(ws, pa, nc);
         cudaError_t e = cudaMemsetAsync(w.qcount, 0, 16, st);
         if (e != cudaSuccess) return e;
-        // successors of each run go to the first sort buffer that does not hold the sorted rows
-        uint32_t* succ_head = (ki == w.sk0) ? w.sk1 : w.sk0;
-        dag_npred_kernel<<<blocks, 256, 0, st>>>(ws, pa, succ_head, nc, s.d);
-        dag_exec_kernel<<<1, kDagExecThreads, slim_in_smem ? (size_t)slim_bytes : 0, st>>>(s, ws, succ_head, nc,
-                                                                                        slim_in_smem, ctrl);
+        dag_npred_kernel<<<blocks, 256, 0, st>>>(ws, pa, nc, s.d);
+        if (slim_in_smem)
+            dag_exec_kernel<true><<<1, kDagExecThreads, (size_t)slim_bytes, st>>>(s, ws, nc, ctrl);
+        else
+            dag_exec_kernel<false><<<1, kDagExecThreads, 0, st>>>(s, ws, nc, ctrl);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
