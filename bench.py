@@ -7,6 +7,11 @@ keys, chunk 65,536) takes 32,000,000 inserts drawn Zipf(s) over 1,000,000 distin
 deletes of a random 10 % of the inserted occurrences; its Slim-subsketch is exported and all
 1,000,000 flows are queried.  value = (inserts + deletes + queries) of all ranks / step time.
 
+The default run (--workload all) embeds the other measured configurations in the same line:
+"batched" (1,024 uneven sketches in one graph launch vs one call per sketch), "out_of_l2"
+(10^9 u64 keys on a 1 GiB Fat), "one_at_a_time" (the paper's rule, chunk 1) and "serving" (the
+collector loop, p50/p99).  Each can also be run alone with --workload.
+
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 --impl reference times the CPU oracle (plain sequential C, one core) on a bounded sample of the
@@ -224,7 +229,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", choices=["all", "flows", "batch", "serve", "accuracy", "pipeline", "profile",
-                                           "l2curve", "seq"],
+                                           "l2curve", "seq", "outofl2"],
                     default="all",
                     help="all: the flows line with the batched and serving results embedded; profile: the small "
                          "fixed case the committed ncu summaries capture (two insert launches, the second profiled)")
@@ -234,6 +239,8 @@ def main():
     ap.add_argument("--profile-inserts", type=int, default=2_000_000)
     ap.add_argument("--batch-sketches", type=int, default=1024)
     ap.add_argument("--serve-seconds", type=float, default=8.0)
+    ap.add_argument("--ool2-updates", type=int, default=1_000_000_000,
+                    help="outofl2: stream length (10^9 in the measured configuration)")
     args = ap.parse_args()
     if args.print_kernel_sha:
         print(chunk_kernel_source_sha256())
@@ -284,8 +291,18 @@ def main():
         line = run_profile(args, ctx)
     if args.workload == "l2curve":
         line = run_l2curve(args, ctx)
-    if args.workload == "seq":
-        line = run_seq(args, ctx)
+    if args.workload in ("all", "outofl2"):
+        v = run_outofl2(args, ctx)
+        if line is None:
+            line = v
+        elif rank == 0:
+            line["out_of_l2"] = v
+    if args.workload in ("all", "seq"):
+        v = run_seq(args, ctx)
+        if line is None:
+            line = v
+        elif rank == 0:
+            line["one_at_a_time"] = v
     if args.workload in ("all", "serve"):
         v = run_serve(args, ctx)
         if line is None:
@@ -670,6 +687,208 @@ def run_seq(args, ctx):
     return {"workload": "one-at-a-time-insert-u32", "updates": len(keys), "gpu_ms": round(best, 3),
             "gpu_M_updates_per_s": round(len(keys) / best / 1e3, 1), "oracle_ms_one_core": round(t_cpu * 1e3, 3),
             "speedup_vs_oracle": round(t_cpu * 1e3 / best, 2), "bit_exact": bool(exact)}
+
+
+OOL2_D, OOL2_W, OOL2_Z, OOL2_KB, OOL2_S = 4, 1 << 22, 16, 8, 1 << 20
+OOL2_DISTINCT, OOL2_ZIPF, OOL2_DEL, OOL2_SEED, OOL2_QUERIES = 1 << 26, 1.2, 0.2, 5, 1 << 24
+OOL2_SECTOR = 32   # bytes one random counter access moves between L2 and HBM
+
+
+def hbm_random_peaks(L, dev, stream, words=1 << 28):
+    """Best of three rates (G ops/s) of sf_bench_random_access on a 1 GiB buffer (far beyond L2):
+    32-bit loads (kind 2), reductions (kind 0) and the 1:1 reduce/load mix (kind 5)."""
+    import torch
+    buf = torch.zeros(words, dtype=torch.int32, device=dev)
+    h_st = int(stream.cuda_stream)
+    out = {}
+    for name, kind in (("ld", 2), ("red", 0), ("mix", 5)):
+        L.sf_bench_random_access(buf.data_ptr(), buf.numel(), 1 << 26, kind, 0, h_st)
+        best = 0.0
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            rc = L.sf_bench_random_access(buf.data_ptr(), buf.numel(), 1 << 28, kind, 0, h_st)
+            b.record(stream)
+            torch.cuda.synchronize()
+            if rc != 0:
+                raise SystemExit(f"sf_bench_random_access failed: {rc}")
+            best = max(best, (1 << 28) / a.elapsed_time(b) / 1e6)
+        out[name] = best
+    del buf
+    return out
+
+
+def run_outofl2(args, ctx):
+    """The out-of-L2 stress configuration: 10^9 u64 keys drawn Zipf(1.2) over 2^26 distinct ids,
+    an 80/20 strict-turnstile insert/delete mix (each delete removes an earlier inserted
+    occurrence), d=4, Fat 4 x 2^26 u32 counters (1 GiB, beyond L2), Slim 4 x 2^22, chunk 2^20,
+    the whole stream in one update call per step; then the Slim is exported and 2^24 keys are
+    queried (half drawn from the stream, half random 64-bit ids).  `--ool2-updates` shrinks the
+    stream for the small case an ncu capture takes (same shapes otherwise).
+
+    value = (updates + queries) / step time.  Roofline: the Fat and the chunk dictionary live in
+    HBM, so every counter access is a random 32-byte sector; the ceiling is the random-access
+    rate of a 1 GiB buffer with the update's 1:1 read-modify-write / load mix, measured in the
+    same run."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_1701_04148_gb300 as sf
+    import workloads as wl
+    world, rank, local, dist = ctx["world"], ctx["rank"], ctx["local"], ctx["dist"]
+    dev, L, stream = ctx["dev"], ctx["L"], ctx["stream"]
+    n = args.ool2_updates
+    st, _ = wl.mixed_stream(n, OOL2_DISTINCT, OOL2_ZIPF, OOL2_DEL, OOL2_KB, seed=OOL2_SEED + 1000 * rank,
+                            device=dev)
+    keys, ops = st.keys, st.ops
+    n_del = int((ops < 0).sum())
+    gq = wl._gen(77 + rank, dev)
+    nq = OOL2_QUERIES
+    pos = torch.randint(0, n, (nq // 2,), generator=gq, device=dev)
+    absent = wl.ids_to_bytes(wl.distinct_ids(nq - nq // 2, 64, gq, dev), OOL2_KB)
+    q = torch.cat([keys.index_select(0, pos), absent])
+    q = q[torch.randperm(nq, generator=gq, device=dev)].contiguous()
+    del pos, absent
+    torch.cuda.synchronize()
+    g = sf.Sketch(OOL2_D, OOL2_W, OOL2_Z, OOL2_KB, OOL2_SEED, OOL2_S, stream=stream)
+    slim_buf = torch.empty(OOL2_D * OOL2_W, dtype=torch.int32, device=dev)
+    ans = torch.empty(nq, dtype=torch.int32, device=dev)
+
+    def step(evs=None, src=None):
+        k, o, qq, out = src if src is not None else (keys, ops, q, ans)
+        g.reset()
+        if evs is not None:
+            evs[0].record(stream)
+        g.update(k, o)
+        if evs is not None:
+            evs[1].record(stream)
+        slim, hdr = g.export_slim(slim_buf)
+        sf.query(slim, hdr, qq, out=out, stream=stream)
+        if evs is not None:
+            evs[2].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    g.sync()
+    evs_all = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(gpu_index_for(local))
+    clocks.start()
+    time.sleep(0.3)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for k in range(args.steps):
+        step(evs_all[k])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+    g.sync()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    t_upd = sum(e[0].elapsed_time(e[1]) for e in evs_all) / args.steps
+    t_qry = sum(e[1].elapsed_time(e[2]) for e in evs_all) / args.steps
+    value = world * (n + nq) / (ms_max / 1e3) / 1e6
+
+    # Roofline.  Algorithmic bytes per update, every Fat access a random 32-byte sector of HBM
+    # (the Slim, 64 MiB, counted as L2-resident): the key and op byte, d Fat increments (sector
+    # read and write back) and the read-back: d sectors for an insertion's estimate, d 64-byte
+    # buckets for a deletion's maximum.  Peak: the measured streaming copy rate.  The DRAM bytes
+    # the kernel really moves come from an ncu capture of a 16-chunk prefix of the same stream,
+    # scaled to this launch; as 32-byte sectors per second they are set against the random-access
+    # rate of a 1 GiB buffer (the 1:1 reduce / load mix), measured in this run.
+    n_ins = n - n_del
+    alg_bytes = n_ins * (OOL2_KB + 1 + OOL2_D * 3 * OOL2_SECTOR) + n_del * (OOL2_KB + 1 + OOL2_D * 4 * OOL2_SECTOR)
+    peaks, psrc = measured_peaks()
+    achieved = alg_bytes / (t_upd / 1e3) / 1e9
+    peaks_r = hbm_random_peaks(L, dev, stream)
+    tr = traffic_record()
+    traffic = None
+    if tr is not None and "outofl2" in tr:
+        rec = tr["outofl2"]
+        traffic = round((rec["dram_bytes_read"] + rec["dram_bytes_write"]) / rec["updates"] * n)
+    roofline = {"bound": "hbm", "kernel": "chunk_update_kernel", "achieved": round(achieved, 1),
+                "peak": peaks.get("hbm_gbs"), "unit": "GB/s", "frac": round(achieved / peaks.get("hbm_gbs", 1.0), 4),
+                "traffic": traffic,
+                "counting": f"algorithmic bytes per update: key + op byte + d Fat read-modify-writes "
+                            f"(2 x {OOL2_SECTOR} B) + d Fat read-backs ({OOL2_SECTOR} B per insertion, "
+                            f"{2 * OOL2_SECTOR} B bucket per deletion); {alg_bytes / n:.1f} B per update here",
+                "peak_source": f"{psrc} streaming copy rate (MEASURED_PEAKS hbm_gbs)" if psrc == "measured"
+                               else "fallback streaming copy rate",
+                "avg_launch_ms": round(t_upd, 3)}
+    if traffic is not None:
+        sect = traffic / OOL2_SECTOR / (t_upd / 1e3) / 1e9
+        roofline["dram_sectors"] = {
+            "achieved_g_per_s": round(sect, 2), "peak_g_per_s": round(peaks_r["mix"], 2),
+            "frac": round(sect / peaks_r["mix"], 4),
+            "note": "DRAM bytes the kernel moves (ncu, scaled) as 32-byte sectors per second, against random "
+                    "32-bit ops on a 1 GiB buffer (sf_bench_random_access kind 5, 1:1 reduce / load) in this run"}
+    roofline["random_hbm_rates_g_ops"] = {k: round(v, 2) for k, v in peaks_r.items()}
+
+    # ---- e2e: keys, ops and queries in pinned host memory, answers written back to it --------
+    e2e = None
+    if not args.no_e2e:
+        host = (keys.cpu().pin_memory(), ops.cpu().pin_memory(), q.cpu().pin_memory(),
+                torch.empty(nq, dtype=torch.int32).pin_memory())
+        step(src=host)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            step(src=host)
+        b.record(stream)
+        torch.cuda.synchronize()
+        g.sync()
+        ems = a.elapsed_time(b) / args.steps
+        e2e = {"value": round(world * (n + nq) / (ems / 1e3) / 1e6, 2), "unit": "M ops/s",
+               "h2d_bytes_per_step": int(host[0].numel() + host[1].numel() + host[2].numel()),
+               "d2h_bytes_per_step": int(host[3].numel() * 4), "ms_per_step": round(ems, 3),
+               "transfer": "pinned host buffers passed to the same calls (kernels read keys and ops and write "
+                           "the answers over the host link)",
+               "answers_equal_device_resident": bool(torch.equal(host[3], ans.cpu()))}
+        del host
+
+    # ---- CPU baseline and bit-exact check on the first two chunks ----------------------------
+    cpu = exact = None
+    if rank == 0 and not args.no_cpu_baseline:
+        pre = min(n, 2 * OOL2_S)
+        kh, oh = keys[:pre].cpu().numpy(), ops[:pre].cpu().numpy()
+        o = oracle.Sketch(OOL2_D, OOL2_W, OOL2_Z, OOL2_KB, OOL2_SEED)
+        t0 = time.perf_counter()
+        o.update(kh, oh, S=OOL2_S)
+        dt = time.perf_counter() - t0
+        cpu = {"value": round(pre / dt / 1e6, 4), "unit": "M updates/s", "cores": 1, "kind": "oracle",
+               "sample": f"the first {pre} updates of the stream (two chunks, {dt:.1f} s)"}
+        g2 = sf.Sketch(OOL2_D, OOL2_W, OOL2_Z, OOL2_KB, OOL2_SEED, OOL2_S, stream=stream)
+        g2.update(keys[:pre], ops[:pre])
+        g2.sync()
+        exact = bool(np.array_equal(g2.fat.cpu().numpy().view(np.uint32).reshape(o.B.shape), o.B)
+                     and np.array_equal(g2.slim.cpu().numpy().view(np.uint32).reshape(o.A.shape), o.A))
+        g2.close()
+        del o
+    if rank != 0:
+        return None
+    return {"metric": METRIC, "value": round(value, 2), "unit": "M ops/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_max, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "out-of-l2-stress", "d": OOL2_D, "w": OOL2_W, "z": OOL2_Z, "key_bytes": OOL2_KB,
+                       "chunk": OOL2_S, "updates": n, "deletes": n_del, "distinct": OOL2_DISTINCT,
+                       "zipf_s": OOL2_ZIPF, "queries": nq, "fat_bytes": OOL2_D * OOL2_W * OOL2_Z * 4,
+                       "l2": f"inputs larger than L2 ({n * (OOL2_KB + 1) / 1e9:.1f} GB of keys and ops per step)",
+                       "parallelism": f"replicas x{world}"},
+            "breakdown": {"update_ms": round(t_upd, 3), "M_updates_per_s": round(n / t_upd / 1e3, 1),
+                          "export_query_ms": round(t_qry, 3), "M_queries_per_s": round(nq / t_qry / 1e3, 1)},
+            "roofline": roofline, "cpu_baseline": cpu,
+            "bit_exact_first_two_chunks": exact, "e2e": e2e, "gpu_launches": args.steps * 2, "clocks": clk}
 
 
 def run_l2curve(args, ctx):
