@@ -370,11 +370,13 @@ def run_flows(args, ctx):
         b_del.update([(sk, inp[1], o) for sk, inp, o in zip(sketches, src, del_ops)])
         if evs is not None:
             evs[2].record(stream)
-        for idx in range(len(SWEEP)):
-            slim, hdr = sketches[idx].export_slim(slims[idx])
-            sf.query(slim, hdr, src[idx][2], out=out[idx], stream=stream)
+        hdrs = [sketches[idx].export_slim(slims[idx])[1] for idx in range(len(SWEEP))]
         if evs is not None:
             evs[3].record(stream)
+        for idx in range(len(SWEEP)):
+            sf.query(slims[idx], hdrs[idx], src[idx][2], out=out[idx], stream=stream)
+        if evs is not None:
+            evs[4].record(stream)
         if host is not None and not direct:
             for idx in range(len(SWEEP)):
                 host[idx][3].copy_(answers[idx], non_blocking=True)
@@ -387,7 +389,7 @@ def run_flows(args, ctx):
     assert b_ins.sync_status() == sf.SF_OK and b_del.sync_status() == sf.SF_OK
 
     # ---- timed region (device-resident inputs) --------------------------------------------
-    evs_all = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    evs_all = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(gpu_index_for(local))
     clocks.start()
@@ -408,7 +410,8 @@ def run_flows(args, ctx):
         sk.sync()
     t_ins = sum(evs_all[k][0].elapsed_time(evs_all[k][1]) for k in range(args.steps))
     t_del = sum(evs_all[k][1].elapsed_time(evs_all[k][2]) for k in range(args.steps))
-    t_qry = sum(evs_all[k][2].elapsed_time(evs_all[k][3]) for k in range(args.steps))
+    t_qry = sum(evs_all[k][2].elapsed_time(evs_all[k][4]) for k in range(args.steps))
+    t_q_only = sum(evs_all[k][3].elapsed_time(evs_all[k][4]) for k in range(args.steps))
     ms_max = ms
     if dist is not None:
         t = torch.tensor([ms], dtype=torch.float64, device=dev)
@@ -442,6 +445,16 @@ def run_flows(args, ctx):
                 "peak_load_only": round(best["ld"], 2), "frac_of_load_only": round(achieved / best["ld"], 4),
                 "ops_per_update": L2_OPS_PER_UPDATE,
                 "avg_launch_ms": round(chunk_ms / launches_chunk, 4)}
+    # queries: d random gathers from an L2-resident Slim (4 MiB) per key, against the measured
+    # random-load rate; the six query launches of a step are timed together (1 M keys each)
+    gathers = args.steps * len(SWEEP) * N_FLOWS * L2_OPS_PER_QUERY
+    roofline_query = {"bound": "l2", "kernel": "query_kernel",
+                      "achieved": round(gathers / (t_q_only / 1e3) / 1e9, 2), "peak": round(best["ld"], 2),
+                      "unit": "G random L2 ops/s", "frac": round(gathers / (t_q_only / 1e3) / 1e9 / best["ld"], 4),
+                      "M_queries_per_s": round(args.steps * len(SWEEP) * N_FLOWS / t_q_only / 1e3, 1),
+                      "avg_launch_us": round(t_q_only * 1e3 / (args.steps * len(SWEEP)), 2),
+                      "note": f"{L2_OPS_PER_QUERY} Slim gathers per query (Sec. 3.1 query) over 1,000,000 13-byte "
+                              f"keys per launch; peak: random 32-bit loads on 64 MiB in this run"}
     peaks, psrc = measured_peaks()
     hbm_bytes = upd_timed * (KB + L2_OPS_PER_UPDATE * 4)
     roofline_hbm = {"bound": "hbm", "achieved": round(hbm_bytes / (chunk_ms / 1e3) / 1e9, 1),
@@ -561,7 +574,8 @@ def run_flows(args, ctx):
                           "insert_mops": round(args.steps * len(SWEEP) * N_INS / t_ins / 1e3, 1),
                           "delete_mops": round(args.steps * len(SWEEP) * n_del / t_del / 1e3, 1),
                           "export_query_mops": round(args.steps * len(SWEEP) * N_FLOWS / t_qry / 1e3, 1)},
-            "roofline": roofline, "roofline_hbm": roofline_hbm, "single_sketch": single,
+            "roofline": roofline, "roofline_hbm": roofline_hbm, "roofline_query": roofline_query,
+            "single_sketch": single,
             "cpu_baseline": cpu, "bit_exact_sample": exact, "e2e": e2e, "accuracy": accuracy,
             "gpu_launches": args.steps * launches_per_step, "clocks": clk,
         }
@@ -764,15 +778,17 @@ def run_outofl2(args, ctx):
         if evs is not None:
             evs[1].record(stream)
         slim, hdr = g.export_slim(slim_buf)
-        sf.query(slim, hdr, qq, out=out, stream=stream)
         if evs is not None:
             evs[2].record(stream)
+        sf.query(slim, hdr, qq, out=out, stream=stream)
+        if evs is not None:
+            evs[3].record(stream)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
     g.sync()
-    evs_all = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    evs_all = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(gpu_index_for(local))
     clocks.start()
@@ -796,7 +812,8 @@ def run_outofl2(args, ctx):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_max = float(t.item())
     t_upd = sum(e[0].elapsed_time(e[1]) for e in evs_all) / args.steps
-    t_qry = sum(e[1].elapsed_time(e[2]) for e in evs_all) / args.steps
+    t_qry = sum(e[1].elapsed_time(e[3]) for e in evs_all) / args.steps
+    t_q_only = sum(e[2].elapsed_time(e[3]) for e in evs_all) / args.steps
     value = world * (n + nq) / (ms_max / 1e3) / 1e6
 
     # Roofline.  Algorithmic bytes per update, every Fat access a random 32-byte sector of HBM
@@ -826,13 +843,23 @@ def run_outofl2(args, ctx):
                                else "fallback streaming copy rate",
                 "avg_launch_ms": round(t_upd, 3)}
     if traffic is not None:
-        sect = traffic / OOL2_SECTOR / (t_upd / 1e3) / 1e9
+        # the key and op stream is read sequentially; the rest of the DRAM traffic is random sectors
+        sect = (traffic - n * (OOL2_KB + 1)) / OOL2_SECTOR / (t_upd / 1e3) / 1e9
         roofline["dram_sectors"] = {
             "achieved_g_per_s": round(sect, 2), "peak_g_per_s": round(peaks_r["mix"], 2),
             "frac": round(sect / peaks_r["mix"], 4),
-            "note": "DRAM bytes the kernel moves (ncu, scaled) as 32-byte sectors per second, against random "
-                    "32-bit ops on a 1 GiB buffer (sf_bench_random_access kind 5, 1:1 reduce / load) in this run"}
+            "note": "DRAM bytes the kernel moves (ncu, scaled) less the sequential key and op stream, as 32-byte "
+                    "sectors per second, against random 32-bit ops on a 1 GiB buffer (sf_bench_random_access kind "
+                    "5, 1:1 reduce / load) in this run; that rate itself varied between 31 and 36 G/s across runs"}
     roofline["random_hbm_rates_g_ops"] = {k: round(v, 2) for k, v in peaks_r.items()}
+    # queries: d random gathers per key from the exported 64 MiB Slim, against random 32-bit loads
+    # on a 64 MiB buffer (measured in this run)
+    ld64 = l2_random_peaks(L, dev, stream)["ld"]
+    g_q = nq * OOL2_D / (t_q_only / 1e3) / 1e9
+    roofline_query = {"bound": "l2", "kernel": "query_kernel", "achieved": round(g_q, 2), "peak": round(ld64, 2),
+                      "unit": "G random L2 ops/s", "frac": round(g_q / ld64, 4),
+                      "M_queries_per_s": round(nq / t_q_only / 1e3, 1), "launch_us": round(t_q_only * 1e3, 1),
+                      "note": f"{OOL2_D} gathers per query from the 64 MiB Slim; 8-byte keys"}
 
     # ---- e2e: keys, ops and queries in pinned host memory, answers written back to it --------
     e2e = None
@@ -886,8 +913,8 @@ def run_outofl2(args, ctx):
                        "l2": f"inputs larger than L2 ({n * (OOL2_KB + 1) / 1e9:.1f} GB of keys and ops per step)",
                        "parallelism": f"replicas x{world}"},
             "breakdown": {"update_ms": round(t_upd, 3), "M_updates_per_s": round(n / t_upd / 1e3, 1),
-                          "export_query_ms": round(t_qry, 3), "M_queries_per_s": round(nq / t_qry / 1e3, 1)},
-            "roofline": roofline, "cpu_baseline": cpu,
+                          "export_query_ms": round(t_qry, 3), "M_queries_per_s": round(nq / t_q_only / 1e3, 1)},
+            "roofline": roofline, "roofline_query": roofline_query, "cpu_baseline": cpu,
             "bit_exact_first_two_chunks": exact, "e2e": e2e, "gpu_launches": args.steps * 2, "clocks": clk}
 
 
