@@ -125,7 +125,7 @@ sf_status sf_required_bytes(const sf_params* p, uint64_t* fat_bytes, uint64_t* s
     if (scratch_bytes) {
         const uint64_t cap = p->chunk > 1 ? sfk::dict_capacity(p->chunk) : 0;
         // S = 1 sketches wide enough for the dependency-graph path also hold its workspace
-        const uint64_t dag = (p->chunk == 1 && p->w >= sfk::kDagMinW) ? sfk::dag_workspace_bytes(p->d) : 0;
+        const uint64_t dag = (p->chunk == 1 && sfk::dag_eligible(p->w, p->z)) ? sfk::dag_workspace_bytes(p->d) : 0;
         *scratch_bytes = kCtrlBytes + cap * sizeof(sfk::DictEntry) + dag;
     }
     return SF_OK;
@@ -148,7 +148,7 @@ sf_status sf_create(const sf_params* p, void* fat_dev, void* slim_dev, void* scr
     s->ctrl = (uint32_t*)scratch_dev;
     s->dict = (sfk::DictEntry*)((uint8_t*)scratch_dev + kCtrlBytes);
     s->cap = p->chunk > 1 ? sfk::dict_capacity(p->chunk) : 0;
-    s->dag_ws = (p->chunk == 1 && p->w >= sfk::kDagMinW) ? (uint8_t*)scratch_dev + kCtrlBytes : nullptr;
+    s->dag_ws = (p->chunk == 1 && sfk::dag_eligible(p->w, p->z)) ? (uint8_t*)scratch_dev + kCtrlBytes : nullptr;
     uint64_t st = p->seed;
     for (uint32_t i = 0; i < SF_MAX_D; ++i) s->rs[i] = i < p->d ? splitmix64_next(&st) : 0;
     if (cudaGetDevice(&s->device) != cudaSuccess ||

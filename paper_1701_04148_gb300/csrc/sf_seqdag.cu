@@ -9,15 +9,21 @@
 //   2. per row, a stable radix sort of (bucket, position) gives every update its predecessor and
 //      successor in each of its buckets (the neighbouring entries of the sorted row);
 //   3. runs (Lemma 2): an update whose predecessor in every row is the same earlier update with
-//      the same Fat slots continues that update's run; pointer jumping finds each run's first
+//      the same Fat slots continues that update's run; a run is a block of consecutive entries
+//      of row 0's sorted order, so a prefix maximum over that order finds each run's first
 //      update (its head), which counts the run's length r and records its last member;
-//   4. a run can go once, in every row, the run before it in that bucket has gone: heads count
-//      their pending predecessors, and one block walks the graph frontier by frontier.  A run
-//      adds r to its d Fat counters with returning atomics: every earlier update on those
-//      counters has run and no later one can have, so the returned value plus r is the counter
-//      after the run, and F is their minimum; T = min(m + r, F) with m the minimum of its Slim
-//      counters, which rise to T where lower.  Runs of one frontier share no bucket, so they
-//      touch disjoint counters.
+//   4. the Fat only grows under insertions, so the value a Fat counter holds right after an
+//      update is its value at the start of the piece plus the number of the piece's updates on
+//      that counter up to and including this one, in stream order.  A second stable sort of
+//      every row, by counter (bucket x z + slot), gives those counts, and with them each run's
+//      Fat estimate F (the minimum over rows, after its last member) before anything runs; the
+//      whole piece's Fat increments are then added in parallel;
+//   5. a run can go once, in every row, the run before it in that bucket has gone: heads count
+//      their pending predecessors, and one block walks the graph frontier by frontier, with the
+//      pending counts (four bits per update) and, where it fits, the Slim in shared memory.  A
+//      run's Slim counters rise to T = min(m + r, F) where lower, m being their minimum when the
+//      run goes and r its length.  Runs of one frontier share no bucket, so they touch disjoint
+//      counters.
 // A piece's graph is only as deep as its longest chain of runs through shared buckets.
 #include "sf_internal.h"
 
@@ -30,15 +36,15 @@ constexpr int kDagTile = 1024;           // elements per radix tile (one block)
 constexpr int kDagTiles = kDagN / kDagTile;
 constexpr int kDagRadixBits = 8;
 constexpr int kDagBins = 1 << kDagRadixBits;
-constexpr int kDagExecThreads = 1024;
 
 // Workspace arrays of one piece (kDagN updates, d rows), carved out of the sketch scratch.
 struct DagWs {
     uint4* rec;                   // [N][4G] walk record of every run head (dag_npred_kernel)
+    uint32_t* cnt;                // [d][N] the Fat counter of each update, counted up to it
     uint32_t *hb, *fb;            // [d][N] bucket and slot of every update
     uint32_t *sk0, *sv0, *sk1, *sv1;  // [d][N] radix sort keys (buckets) and values (positions)
     uint32_t *pred, *succ;        // [d][N] previous / next update in the same bucket
-    uint32_t *par0, *par1;        // [N] run parent links (pointer jumping)
+    uint32_t *par0, *par1;        // [N] run parent links, then every update's run head
     uint32_t *rlen, *lastm;       // [N] run length and last member, at heads
     uint32_t *npred;              // [N] pending predecessors, at heads
     uint32_t *bad;                // [N] the key had no valid index (explicit-index mode)
@@ -47,13 +53,13 @@ struct DagWs {
     uint32_t *hist;               // [d][bins][tiles] digit counts, then offsets
 };
 
-// A walk record holds G = ceil(d / 4) uint4 groups each of buckets, Fat slots and successor
-// heads, then the run length: 4G uint4 (64 bytes for d <= 4, 128 for d <= 8).
+// A walk record holds G = ceil(d / 4) uint4 groups each of buckets and successor heads, then
+// {run length, Fat estimate}; records sit 4G uint4 apart (64 bytes for d <= 4, 128 for d <= 8).
 __host__ __device__ inline uint32_t dag_groups(uint32_t d) { return d <= 4 ? 1u : 2u; }
 
 __host__ __device__ inline uint64_t dag_bytes_for(uint32_t d) {
     const uint64_t N = kDagN;
-    return (16ull * dag_groups(d) * N + 8ull * d * N + 8ull * N + 64ull + (uint64_t)d * kDagBins * kDagTiles) * 4ull;
+    return (16ull * dag_groups(d) * N + 9ull * d * N + 8ull * N + 64ull + (uint64_t)d * kDagBins * kDagTiles) * 4ull;
 }
 
 DagWs dag_carve(void* base, uint32_t d) {
@@ -62,6 +68,8 @@ DagWs dag_carve(void* base, uint32_t d) {
     DagWs w;
     w.rec = reinterpret_cast<uint4*>(p);
     p += 16 * dag_groups(d) * N;
+    w.cnt = p;
+    p += d * N;
     w.hb = p;
     p += d * N;
     w.fb = p;
@@ -148,62 +156,87 @@ __global__ void __launch_bounds__(256) dag_hist_kernel(const uint32_t* __restric
 }
 
 // 2b. per row, exclusive scan of the counts in (digit, tile) order: the first output index of
-//     each tile's elements of each digit
+//     each tile's elements of each digit.  Warp q scans the q-th 1,024 counts 32 at a time with
+//     coalesced loads and shuffles; the 32 warp totals are scanned last.
 __global__ void __launch_bounds__(1024) dag_scan_kernel(uint32_t* __restrict__ hist) {
     constexpr uint32_t kLen = kDagBins * kDagTiles;
-    constexpr uint32_t kPer = kLen / 1024;
-    __shared__ uint32_t part[1024];
-    uint32_t* h = hist + (uint64_t)blockIdx.x * kLen;
-    const uint32_t t = threadIdx.x;
-    uint32_t sum = 0;
-    for (uint32_t q = 0; q < kPer; ++q) sum += h[t * kPer + q];
-    part[t] = sum;
+    constexpr uint32_t kPerWarp = kLen / 32;
+    static_assert(kPerWarp == 32 * 32, "one warp scans 32 steps of 32 counts");
+    __shared__ uint32_t s_tot[32];
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    uint32_t* hw = hist + (uint64_t)blockIdx.x * kLen + warp * kPerWarp;
+    uint32_t x[32];
+#pragma unroll
+    for (uint32_t q = 0; q < 32; ++q) x[q] = hw[q * 32 + lane];
+    uint32_t carry = 0;
+#pragma unroll
+    for (uint32_t q = 0; q < 32; ++q) {
+        uint32_t incl = x[q];
+#pragma unroll
+        for (uint32_t off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, off);
+            if (lane >= off) incl += y;
+        }
+        const uint32_t tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        x[q] = carry + incl - x[q];
+        carry += tot;
+    }
+    if (lane == 0) s_tot[warp] = carry;
     __syncthreads();
-    for (uint32_t off = 1; off < 1024; off <<= 1) {  // inclusive scan of the parts
-        const uint32_t v = t >= off ? part[t - off] : 0u;
-        __syncthreads();
-        part[t] += v;
-        __syncthreads();
+    if (warp == 0) {
+        const uint32_t v = s_tot[lane];
+        uint32_t incl = v;
+#pragma unroll
+        for (uint32_t off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, off);
+            if (lane >= off) incl += y;
+        }
+        s_tot[lane] = incl - v;
     }
-    uint32_t run = part[t] - sum;  // exclusive prefix of this thread's part
-    for (uint32_t q = 0; q < kPer; ++q) {
-        const uint32_t c = h[t * kPer + q];
-        h[t * kPer + q] = run;
-        run += c;
-    }
+    __syncthreads();
+    const uint32_t base = s_tot[warp];
+#pragma unroll
+    for (uint32_t q = 0; q < 32; ++q) hw[q * 32 + lane] = base + x[q];
 }
 
-// 2c. stable scatter of one tile of one row: warps in order, equal digits ranked by lane
+// 2c. stable scatter of one tile of one row.  Every warp ranks its elements among equal digits
+//     (by lane) and counts its digits; the counts of each digit are then scanned over the warps
+//     in order, on top of the tile's offset for that digit, so equal digits keep their order.
 __global__ void __launch_bounds__(kDagTile) dag_scatter_kernel(const uint32_t* __restrict__ kin,
                                                                const uint32_t* __restrict__ vin,
                                                                uint32_t* __restrict__ kout,
                                                                uint32_t* __restrict__ vout, uint32_t n,
                                                                uint32_t shift, const uint32_t* __restrict__ hist) {
-    __shared__ uint32_t next[kDagBins];
+    constexpr uint32_t kWarps = kDagTile / 32;
+    __shared__ uint32_t s_cnt[kWarps][kDagBins];  // per warp and digit: count, then first output index
     const uint32_t tile = blockIdx.x, row = blockIdx.y;
-    for (uint32_t b = threadIdx.x; b < kDagBins; b += blockDim.x)
-        next[b] = hist[((uint64_t)row * kDagBins + b) * kDagTiles + tile];
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    for (uint32_t b = lane; b < kDagBins; b += 32) s_cnt[warp][b] = 0u;
     const uint32_t e = tile * kDagTile + threadIdx.x;
     const bool valid = e < n;
     const uint32_t key = valid ? kin[row * kDagN + e] : 0u;
     const uint32_t val = valid ? vin[row * kDagN + e] : 0u;
     const uint32_t dig = (key >> shift) & (kDagBins - 1);
-    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const unsigned act = __ballot_sync(0xFFFFFFFFu, valid);
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, valid ? dig : 0x80000000u | lane) & act;
+    const uint32_t rank = (uint32_t)__popc(peers & ((1u << lane) - 1u));
+    __syncwarp();
+    if (valid && rank == 0u) s_cnt[warp][dig] = (uint32_t)__popc(peers);
     __syncthreads();
-    for (uint32_t wv = 0; wv < kDagTile / 32; ++wv) {
-        if (warp == wv) {
-            const unsigned act = __ballot_sync(0xFFFFFFFFu, valid);
-            const unsigned peers = __match_any_sync(0xFFFFFFFFu, valid ? dig : 0x80000000u | lane) & act;
-            if (valid) {
-                const uint32_t rank = (uint32_t)__popc(peers & ((1u << lane) - 1u));
-                const uint32_t dst = next[dig] + rank;
-                kout[row * kDagN + dst] = key;
-                vout[row * kDagN + dst] = val;
-            }
-            __syncwarp();
-            if (valid && lane == (uint32_t)(31 - __clz(peers))) next[dig] += (uint32_t)__popc(peers);
+    if (threadIdx.x < kDagBins) {
+        const uint32_t b = threadIdx.x;
+        uint32_t run = hist[((uint64_t)row * kDagBins + b) * kDagTiles + tile];
+        for (uint32_t wv = 0; wv < kWarps; ++wv) {
+            const uint32_t c = s_cnt[wv][b];
+            s_cnt[wv][b] = run;
+            run += c;
         }
-        __syncthreads();
+    }
+    __syncthreads();
+    if (valid) {
+        const uint32_t dst = s_cnt[warp][dig] + rank;
+        kout[row * kDagN + dst] = key;
+        vout[row * kDagN + dst] = val;
     }
 }
 
@@ -231,10 +264,66 @@ __global__ void __launch_bounds__(256) dag_run_kernel(DagWs w, uint32_t n, uint3
     w.par0[j] = cont ? p : j;
 }
 
-__global__ void __launch_bounds__(256) dag_jump_kernel(const uint32_t* __restrict__ a, uint32_t* __restrict__ b,
-                                                       uint32_t n) {
-    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < n) b[j] = a[a[j]];
+// 3c. run heads.  A run occupies consecutive entries of row 0's bucket order (each member's
+//     row-0 predecessor is the member before it), so an update's head is the last entry, at or
+//     before it in that order, that starts a run: a prefix maximum of the starting entries'
+//     indices, per tile (dag_headtile_kernel) and then with the maximum of the earlier tiles
+//     (dag_head_kernel).
+__device__ __forceinline__ uint32_t block_max_scan(uint32_t v, uint32_t* s_w) {
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (uint32_t off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, v, off);
+        if (lane >= off) v = max(v, y);
+    }
+    if (lane == 31) s_w[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t x = s_w[lane];
+#pragma unroll
+        for (uint32_t off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, off);
+            if (lane >= off) x = max(x, y);
+        }
+        s_w[lane] = x;
+    }
+    __syncthreads();
+    return warp > 0 ? max(v, s_w[warp - 1]) : v;
+}
+
+// 1 + the sorted index of the entry, if it starts a run, else 0
+__device__ __forceinline__ uint32_t run_start_mark(const uint32_t* __restrict__ sv0, const uint32_t* __restrict__ par,
+                                                   uint32_t q, uint32_t n) {
+    if (q >= n) return 0u;
+    const uint32_t pos = sv0[q];
+    return par[pos] == pos ? q + 1u : 0u;
+}
+
+__global__ void __launch_bounds__(kDagTile) dag_headtile_kernel(const uint32_t* __restrict__ sv0,
+                                                                const uint32_t* __restrict__ par, uint32_t n,
+                                                                uint32_t* __restrict__ agg) {
+    __shared__ uint32_t s_w[32];
+    const uint32_t v = block_max_scan(run_start_mark(sv0, par, blockIdx.x * kDagTile + threadIdx.x, n), s_w);
+    if (threadIdx.x == kDagTile - 1) agg[blockIdx.x] = v;
+}
+
+__global__ void __launch_bounds__(kDagTile) dag_head_kernel(const uint32_t* __restrict__ sv0,
+                                                            const uint32_t* __restrict__ par, uint32_t n,
+                                                            const uint32_t* __restrict__ agg,
+                                                            uint32_t* __restrict__ head) {
+    __shared__ uint32_t s_w[32];
+    __shared__ uint32_t s_carry;
+    if (threadIdx.x < 32) {
+        uint32_t c = 0;
+        for (uint32_t t = threadIdx.x; t < blockIdx.x; t += 32) c = max(c, agg[t]);
+#pragma unroll
+        for (uint32_t off = 16; off > 0; off >>= 1) c = max(c, __shfl_xor_sync(0xFFFFFFFFu, c, off));
+        if (threadIdx.x == 0) s_carry = c;
+    }
+    const uint32_t q = blockIdx.x * kDagTile + threadIdx.x;
+    uint32_t v = block_max_scan(run_start_mark(sv0, par, q, n), s_w);  // its barriers also publish s_carry
+    v = max(v, s_carry);
+    if (q < n) head[sv0[q]] = sv0[v - 1u];  // v >= 1: entry 0 of a row always starts a run
 }
 
 // 3c. run lengths and last members, at heads
@@ -246,26 +335,74 @@ __global__ void __launch_bounds__(256) dag_count_kernel(DagWs w, const uint32_t*
     atomicMax(&w.lastm[hd], j);
 }
 
-// 3d. pending predecessors of every head (one per row that has one), and its successors: the
+// 4a. sort keys of the Fat counters: bucket x z + slot in row order, w * z for an update without a
+//     valid index (it counts on no counter)
+__global__ void __launch_bounds__(256) dag_slotkey_kernel(DagWs w, uint32_t n, uint32_t z, uint32_t wz,
+                                                          uint32_t* __restrict__ kout, uint32_t* __restrict__ vout) {
+    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x, row = blockIdx.y;
+    if (j >= n) return;
+    kout[row * kDagN + j] = w.bad[j] ? wz : w.hb[row * kDagN + j] * z + w.fb[row * kDagN + j];
+    vout[row * kDagN + j] = j;
+}
+
+// 4b. counts: in a row sorted by counter (stable, so stream order within a counter), the update at
+//     sorted index q is the (q - first + 1)-th of the piece on its counter, where first is the
+//     counter's first sorted index (a binary search over the sorted keys)
+__global__ void __launch_bounds__(256) dag_rank_kernel(const uint32_t* __restrict__ sk, const uint32_t* __restrict__ sv,
+                                                       uint32_t* __restrict__ cnt, uint32_t n) {
+    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x, row = blockIdx.y;
+    if (q >= n) return;
+    const uint32_t* k = sk + row * kDagN;
+    const uint32_t key = k[q];
+    uint32_t lo = 0, hi = q;  // the first index in [lo, hi] whose key equals key
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (k[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    cnt[row * kDagN + sv[row * kDagN + q]] = q - lo + 1u;
+}
+
+// 4c. the piece's Fat increments, one atomic per counter: the last update of a counter in sorted
+//     order adds the counter's count
+__global__ void __launch_bounds__(256) dag_fatadd_kernel(SketchDesc s, const uint32_t* __restrict__ sk,
+                                                         const uint32_t* __restrict__ sv,
+                                                         const uint32_t* __restrict__ cnt, uint32_t n, uint32_t wz) {
+    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x, row = blockIdx.y;
+    if (q >= n) return;
+    const uint32_t* k = sk + row * kDagN;
+    const uint32_t key = k[q];
+    if (key >= wz || (q + 1 < n && k[q + 1] == key)) return;
+    atomicAdd(s.B + (uint64_t)row * wz + key, cnt[row * kDagN + sv[row * kDagN + q]]);
+}
+
+// 4d. pending predecessors of every head (one per row that has one), and its successors: the
 //     next update, in each row's bucket, after the run's last member -- always another run's
 //     head, since a run member's predecessors are all inside its run.  Everything the walk needs
-//     of a head goes into its 64-byte record: buckets, Fat slots, successor heads, and the run
-//     length (0 for an update that does nothing).  Heads without any predecessor start the walk.
-__global__ void __launch_bounds__(256) dag_npred_kernel(DagWs w, const uint32_t* __restrict__ head, uint32_t n,
-                                                        uint32_t d) {
+//     of a head goes into its record: buckets, successor heads, the run length (0 for an update
+//     that does nothing) and the Fat estimate after the run, min_i (B_i + count_i of the last
+//     member) with B the Fat at the start of the piece (read before dag_fatadd_kernel runs).
+//     Heads without any predecessor start the walk.
+__global__ void __launch_bounds__(256) dag_npred_kernel(SketchDesc s, DagWs w, const uint32_t* __restrict__ head,
+                                                        uint32_t n) {
     const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n || head[j] != j) return;
+    const uint32_t d = s.d;
     const uint32_t l = w.lastm[j];
-    uint32_t c = 0, hb[kMaxD], fb[kMaxD], sx[kMaxD];
+    const bool ok = !w.bad[j];
+    uint32_t c = 0, F = 0xFFFFFFFFu, hb[kMaxD], sx[kMaxD];
 #pragma unroll
     for (int i = 0; i < kMaxD; ++i) {
-        hb[i] = fb[i] = 0u;
+        hb[i] = 0u;
         sx[i] = kDagNone;
         if (i < (int)d) {
             c += w.pred[i * kDagN + j] != kDagNone ? 1u : 0u;
             hb[i] = w.hb[i * kDagN + j];
-            fb[i] = w.fb[i * kDagN + j];
             sx[i] = w.succ[i * kDagN + l];
+            if (ok) {
+                const uint32_t b0 = __ldcg(s.B + ((uint64_t)i * s.w + hb[i]) * s.z + w.fb[i * kDagN + j]);
+                F = min(F, b0 + w.cnt[i * kDagN + l]);
+            }
         }
     }
     const uint32_t G = dag_groups(d);
@@ -274,40 +411,71 @@ __global__ void __launch_bounds__(256) dag_npred_kernel(DagWs w, const uint32_t*
     for (uint32_t g = 0; g < 2; ++g) {
         if (g < G) {
             r[g] = make_uint4(hb[4 * g], hb[4 * g + 1], hb[4 * g + 2], hb[4 * g + 3]);
-            r[G + g] = make_uint4(fb[4 * g], fb[4 * g + 1], fb[4 * g + 2], fb[4 * g + 3]);
-            r[2 * G + g] = make_uint4(sx[4 * g], sx[4 * g + 1], sx[4 * g + 2], sx[4 * g + 3]);
+            r[G + g] = make_uint4(sx[4 * g], sx[4 * g + 1], sx[4 * g + 2], sx[4 * g + 3]);
         }
     }
-    r[3 * G] = make_uint4(w.bad[j] ? 0u : w.rlen[j], 0u, 0u, 0u);
+    r[2 * G] = make_uint4(ok ? w.rlen[j] : 0u, F, 0u, 0u);
     w.npred[j] = c;
     if (c == 0) w.q0[atomicAdd(&w.qcount[0], 1u)] = j;
 }
 
-// 4. the graph walk, one block; the Slim in shared memory (kSmemSlim) or in place.  The frontier
-//    queues live in shared memory up to kDagQCap entries, the rest in the global queues.  A
-//    level's cost is its longest chain of dependent memory round trips, so each head's record
-//    comes in four vector loads, and while a head's atomics are in flight the records of its
-//    successors are prefetched into L1 for the next level.
-constexpr uint32_t kDagQCap = 4096;
+// 5. the graph walk, one block, level by level.  A head is taken by P = 1, 2, 4 or 8 lanes
+//    (the power of two >= d), lane i for row i: it reads word i of the head's bucket and
+//    successor groups, its Slim counter and its successor's pending count, and the lanes of a
+//    head combine their Slim minimum with two shuffles, so a head costs a few instructions per
+//    lane and a warp's record loads touch one cache line per head.  Shared memory holds the
+//    pending counts (one byte per update of the piece: at most d <= 8 each), the frontier
+//    queues up to qcap heads (the rest in the global queues) and, with kSmemSlim, the Slim.
+constexpr int kDagWalkThreads = 1024;
 
 __device__ __forceinline__ void prefetch_l1(const void* p) {
     asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
 
-template <bool kSmemSlim>
-__global__ void __launch_bounds__(kDagExecThreads, 1) dag_exec_kernel(SketchDesc s, DagWs w, uint32_t n,
-                                                                      uint32_t* ctrl) {
-    extern __shared__ uint32_t sA[];
-    __shared__ uint32_t s_q[2][kDagQCap];
-    __shared__ uint32_t s_next;
-    const uint64_t slim_n = (uint64_t)s.d * s.w;
+template <int D>
+struct WalkLanes {
+    static constexpr int P = D <= 1 ? 1 : D <= 2 ? 2 : D <= 4 ? 4 : 8;
+    static constexpr int G = D <= 4 ? 1 : 2;  // uint4 groups of buckets (and of successors)
+};
+
+template <int D, bool kSmemSlim>
+__global__ void __launch_bounds__(kDagWalkThreads, 1) dag_walk_kernel(SketchDesc s, DagWs w, uint32_t n,
+                                                                      uint32_t qcap, uint32_t* ctrl) {
+    constexpr int P = WalkLanes<D>::P, G = WalkLanes<D>::G;
+    constexpr uint32_t kHeadsPerIter = kDagWalkThreads / P;
+    extern __shared__ uint32_t s_dyn[];
+    __shared__ uint32_t s_next[3];
+    // dynamic shared memory: queues [2][qcap], pending-count bytes, then the Slim
+    uint32_t* s_q = s_dyn;
+    uint32_t* s_np = s_q + 2ull * qcap;
+    const uint32_t np_words = (n + 3u) / 4u;
+    uint32_t* sA = s_np + np_words;
+    const uint64_t slim_n = (uint64_t)D * s.w;
     if (kSmemSlim) {
         for (uint64_t i = threadIdx.x; i < slim_n; i += blockDim.x) sA[i] = __ldcg(s.A + i);
     }
+    for (uint32_t t = threadIdx.x; t < np_words; t += blockDim.x) {
+        uint32_t v = 0;
+#pragma unroll
+        for (uint32_t b = 0; b < 4; ++b)
+            if (4 * t + b < n) v |= (__ldcg(w.npred + 4 * t + b) & 0xFFu) << (8 * b);
+        s_np[t] = v;
+    }
     uint32_t* A = kSmemSlim ? sA : s.A;
-    const uint32_t G = dag_groups(s.d);
+    const uint32_t row = threadIdx.x % P;            // this lane's row (idle when >= D)
+    const uint32_t slot = threadIdx.x / P;           // this lane's head within an iteration
+    const bool live_row = row < (uint32_t)D;
+    const uint32_t* recw = reinterpret_cast<const uint32_t*>(w.rec);
     uint32_t ncur = __ldcg(&w.qcount[0]);
-    for (uint32_t q = threadIdx.x; q < ncur && q < kDagQCap; q += blockDim.x) s_q[0][q] = __ldcg(w.q0 + q);
+    for (uint32_t q = threadIdx.x; q < ncur && q < qcap; q += blockDim.x) s_q[q] = __ldcg(w.q0 + q);
+    // Queue counters rotate over three words, so one barrier per level suffices: level L pushes
+    // into s_next[L % 3], every thread reads it after the level's barrier, and thread 0 clears
+    // s_next[(L + 1) % 3] during level L -- last read at the end of level L - 2, before the
+    // barrier of level L - 1.
+    if (threadIdx.x == 0) {
+        s_next[0] = 0u;
+        s_next[1] = 0u;
+    }
     uint32_t cb = 0;  // which queue holds the current frontier
     __syncthreads();
     for (uint32_t step = 0; ncur > 0; ++step) {
@@ -315,75 +483,51 @@ __global__ void __launch_bounds__(kDagExecThreads, 1) dag_exec_kernel(SketchDesc
             if (threadIdx.x == 0) atomicOr(ctrl + kCtrlErr, kErrTimeout);
             break;
         }
-        if (threadIdx.x == 0) s_next = 0u;
-        __syncthreads();
+        const uint32_t c_now = step % 3u;
+        if (threadIdx.x == 0) s_next[(step + 1u) % 3u] = 0u;
         const uint32_t nb = cb ^ 1u;
         uint32_t* gcur = cb ? w.q1 : w.q0;
         uint32_t* gnext = cb ? w.q0 : w.q1;
-        for (uint32_t q = threadIdx.x; q < ncur; q += blockDim.x) {
-            const uint32_t j = q < kDagQCap ? s_q[cb][q] : __ldcg(gcur + q);
-            const uint4* rj = w.rec + 4ull * G * j;
-            uint32_t hb[kMaxD], fb[kMaxD], sx[kMaxD];
-#pragma unroll
-            for (uint32_t g = 0; g < 2; ++g) {
-                uint4 h4 = make_uint4(0u, 0u, 0u, 0u), f4 = h4, x4 = make_uint4(kDagNone, kDagNone, kDagNone, kDagNone);
-                if (g < G) {
-                    h4 = __ldg(rj + g);
-                    f4 = __ldg(rj + G + g);
-                    x4 = __ldg(rj + 2 * G + g);
-                }
-                hb[4 * g] = h4.x, hb[4 * g + 1] = h4.y, hb[4 * g + 2] = h4.z, hb[4 * g + 3] = h4.w;
-                fb[4 * g] = f4.x, fb[4 * g + 1] = f4.y, fb[4 * g + 2] = f4.z, fb[4 * g + 3] = f4.w;
-                sx[4 * g] = x4.x, sx[4 * g + 1] = x4.y, sx[4 * g + 2] = x4.z, sx[4 * g + 3] = x4.w;
-            }
-            const uint32_t r = __ldg(&rj[3 * G].x);
-            // the run's Fat increments and its successors' pending counts, all in flight together
-            // (every return value is collected before any is used)
-            uint32_t old_v[kMaxD], left[kMaxD];
-#pragma unroll
-            for (int i = 0; i < kMaxD; ++i) {
-                old_v[i] = 0u;
-                left[i] = 0xFFFFFFFFu;
-                if (i < (int)s.d) {
-                    if (r != 0u) old_v[i] = atomicAdd(s.B + ((uint64_t)i * s.w + hb[i]) * s.z + fb[i], r);
-                    if (sx[i] != kDagNone) left[i] = atomicSub(&w.npred[sx[i]], 1u);
+        // every lane runs the same number of iterations (the shuffles need the whole warp)
+        for (uint32_t base = 0; base < ncur; base += kHeadsPerIter) {
+            const uint32_t hq = base + slot;
+            const bool live = hq < ncur;
+            uint32_t j = 0;
+            if (live) j = hq < qcap ? s_q[(uint64_t)cb * qcap + hq] : __ldcg(gcur + hq);
+            const uint32_t* rw = recw + 16ull * G * j;  // the record: 4G uint4 = 16G words
+            uint32_t hb = 0, sx = kDagNone, r = 0, F = 0, a = 0xFFFFFFFFu;
+            if (live) {
+                r = __ldg(rw + 8 * G);
+                F = __ldg(rw + 8 * G + 1);
+                if (live_row) {
+                    hb = __ldg(rw + row);
+                    sx = __ldg(rw + 4 * G + row);
                 }
             }
+            if (sx != kDagNone) prefetch_l1(recw + 16ull * G * sx);
+            if (live && live_row) a = A[(uint64_t)row * s.w + hb];
+            uint32_t m = a;
 #pragma unroll
-            for (int i = 0; i < kMaxD; ++i)
-                if (i < (int)s.d && sx[i] != kDagNone) prefetch_l1(w.rec + 4ull * G * sx[i]);
-            if (r != 0u) {
-                uint32_t F = 0xFFFFFFFFu, m = 0xFFFFFFFFu, a[kMaxD];
-#pragma unroll
-                for (int i = 0; i < kMaxD; ++i) {
-                    a[i] = 0u;
-                    if (i < (int)s.d) {
-                        a[i] = A[(uint64_t)i * s.w + hb[i]];
-                        m = min(m, a[i]);
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < kMaxD; ++i)
-                    if (i < (int)s.d) F = min(F, old_v[i] + r);
+            for (int off = 1; off < P; off <<= 1) m = min(m, __shfl_xor_sync(0xFFFFFFFFu, m, off));
+            if (live && live_row && r != 0u) {
                 const uint64_t mr = (uint64_t)m + r;
                 const uint32_t T = mr < (uint64_t)F ? (uint32_t)mr : F;
-#pragma unroll
-                for (int i = 0; i < kMaxD; ++i)
-                    if (i < (int)s.d && a[i] < T) A[(uint64_t)i * s.w + hb[i]] = T;
+                if (a < T) A[(uint64_t)row * s.w + hb] = T;
             }
-#pragma unroll
-            for (int i = 0; i < kMaxD; ++i) {
-                if (i < (int)s.d && left[i] == 1u) {  // the last pending predecessor of that head
-                    const uint32_t idx = atomicAdd(&s_next, 1u);
-                    if (idx < kDagQCap) s_q[nb][idx] = sx[i];
-                    else gnext[idx] = sx[i];
+            // one pending predecessor less for this row's successor; the last one queues it
+            if (sx != kDagNone) {
+                const uint32_t sh = 8u * (sx & 3u);
+                const uint32_t old = atomicSub(&s_np[sx >> 2], 1u << sh);
+                if (((old >> sh) & 0xFFu) == 1u) {
+                    const uint32_t idx = atomicAdd(&s_next[c_now], 1u);
+                    if (idx < qcap) s_q[(uint64_t)nb * qcap + idx] = sx;
+                    else gnext[idx] = sx;
                 }
             }
         }
         __syncthreads();
-        ncur = s_next;
+        ncur = s_next[c_now];
         cb = nb;
-        __syncthreads();
     }
     if (kSmemSlim) {
         __syncthreads();
@@ -391,61 +535,112 @@ __global__ void __launch_bounds__(kDagExecThreads, 1) dag_exec_kernel(SketchDesc
     }
 }
 
+template <int D>
+static cudaError_t launch_walk_d(const SketchDesc& s, const DagWs& w, uint32_t nc, int smem_limit, uint32_t* ctrl,
+                                 cudaStream_t st) {
+    // dynamic shared memory: the pending-count bytes of a full piece, queues of qcap heads per
+    // frontier (up to 2,048, at least 256) and the Slim when it fits beside them
+    const uint64_t np_bytes = kDagN;
+    const uint64_t slim_bytes = (uint64_t)D * s.w * 4ull;
+    const uint64_t budget = (uint64_t)smem_limit - 1024ull;  // static counters and slack
+    if (budget < np_bytes + 2ull * 256ull * 4ull) return cudaErrorInvalidValue;
+    const bool slim_in_smem = np_bytes + slim_bytes + 2ull * 256ull * 4ull <= budget;
+    uint64_t qcap = (budget - np_bytes - (slim_in_smem ? slim_bytes : 0ull)) / 8ull;
+    if (qcap > 2048) qcap = 2048;
+    qcap &= ~31ull;
+    const size_t dyn_max = (size_t)(2ull * qcap * 4ull + np_bytes + (slim_in_smem ? slim_bytes : 0ull));
+    const size_t dyn = (size_t)(2ull * qcap * 4ull + (uint64_t)((nc + 3u) / 4u) * 4ull +
+                                (slim_in_smem ? slim_bytes : 0ull));
+    cudaError_t e;
+    if (slim_in_smem) {
+        e = cudaFuncSetAttribute(dag_walk_kernel<D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
+        if (e != cudaSuccess) return e;
+        dag_walk_kernel<D, true><<<1, kDagWalkThreads, dyn, st>>>(s, w, nc, (uint32_t)qcap, ctrl);
+    } else {
+        e = cudaFuncSetAttribute(dag_walk_kernel<D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
+        if (e != cudaSuccess) return e;
+        dag_walk_kernel<D, false><<<1, kDagWalkThreads, dyn, st>>>(s, w, nc, (uint32_t)qcap, ctrl);
+    }
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_walk(const SketchDesc& s, const DagWs& w, uint32_t nc, int smem_limit, uint32_t* ctrl,
+                               cudaStream_t st) {
+    switch (s.d) {
+        case 1: return launch_walk_d<1>(s, w, nc, smem_limit, ctrl, st);
+        case 2: return launch_walk_d<2>(s, w, nc, smem_limit, ctrl, st);
+        case 3: return launch_walk_d<3>(s, w, nc, smem_limit, ctrl, st);
+        case 4: return launch_walk_d<4>(s, w, nc, smem_limit, ctrl, st);
+        case 5: return launch_walk_d<5>(s, w, nc, smem_limit, ctrl, st);
+        case 6: return launch_walk_d<6>(s, w, nc, smem_limit, ctrl, st);
+        case 7: return launch_walk_d<7>(s, w, nc, smem_limit, ctrl, st);
+        case 8: return launch_walk_d<8>(s, w, nc, smem_limit, ctrl, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 }  // namespace
 
 uint64_t dag_workspace_bytes(uint32_t d) { return dag_bytes_for(d); }
 
+// One stable LSD radix sort of every row: keys ki, values vi (both [d][N]), by the bits below
+// key_limit; ko, vo are the other buffers.  Returns the buffers holding the sorted rows.
+static cudaError_t dag_sort_rows(const DagWs& w, uint32_t d, uint32_t nc, uint64_t key_limit, uint32_t*& ki,
+                                 uint32_t*& vi, uint32_t*& ko, uint32_t*& vo, cudaStream_t st) {
+    const uint32_t tiles = (nc + kDagTile - 1) / kDagTile;
+    for (uint32_t shift = 0; shift < 32 && (shift == 0 || (key_limit >> shift) != 0); shift += kDagRadixBits) {
+        cudaError_t e = cudaMemsetAsync(w.hist, 0, (uint64_t)d * kDagBins * kDagTiles * 4ull, st);
+        if (e != cudaSuccess) return e;
+        dag_hist_kernel<<<dim3(tiles, d), 256, 0, st>>>(ki, nc, shift, w.hist);
+        dag_scan_kernel<<<d, 1024, 0, st>>>(w.hist);
+        dag_scatter_kernel<<<dim3(tiles, d), kDagTile, 0, st>>>(ki, vi, ko, vo, nc, shift, w.hist);
+        uint32_t* t = ki;
+        ki = ko;
+        ko = t;
+        t = vi;
+        vi = vo;
+        vo = t;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_seq_dag(const SketchDesc& s, const uint8_t* keys, uint64_t n, void* ws_base, uint32_t* ctrl,
                            int smem_limit, cudaStream_t st) {
     const DagWs w = dag_carve(ws_base, s.d);
-    const uint64_t slim_bytes = (uint64_t)s.d * s.w * 4ull;
-    const bool slim_in_smem = slim_bytes + 2 * kDagQCap * 4 + 1024 <= (uint64_t)smem_limit;
-    if (slim_in_smem) {
-        cudaError_t e = cudaFuncSetAttribute(dag_exec_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)slim_bytes);
-        if (e != cudaSuccess) return e;
-    }
+    const uint64_t wz64 = (uint64_t)s.w * s.z;
+    if (s.w < kDagMinW || wz64 >= (1ull << 32)) return cudaErrorInvalidValue;
+    const uint32_t wz = (uint32_t)wz64;
+    cudaError_t e = cudaSuccess;
     for (uint64_t base = 0; base < n; base += kDagN) {
         const uint32_t nc = (uint32_t)(n - base < (uint64_t)kDagN ? n - base : (uint64_t)kDagN);
         const uint32_t blocks = (nc + 255) / 256;
-        const uint32_t tiles = (nc + kDagTile - 1) / kDagTile;
         dag_hash_kernel<<<blocks, 256, 0, st>>>(s, keys + base * s.key_bytes, nc, w, ctrl);
-        // stable LSD radix sort of every row by bucket
+        // stable sort of every row by bucket: each update's neighbours in its buckets
         uint32_t *ki = w.sk0, *vi = w.sv0, *ko = w.sk1, *vo = w.sv1;
-        for (uint32_t shift = 0; shift < 32 && (shift == 0 || ((s.w - 1) >> shift) != 0); shift += kDagRadixBits) {
-            cudaError_t e = cudaMemsetAsync(w.hist, 0, (uint64_t)s.d * kDagBins * kDagTiles * 4ull, st);
-            if (e != cudaSuccess) return e;
-            dag_hist_kernel<<<dim3(tiles, s.d), 256, 0, st>>>(ki, nc, shift, w.hist);
-            dag_scan_kernel<<<s.d, 1024, 0, st>>>(w.hist);
-            dag_scatter_kernel<<<dim3(tiles, s.d), kDagTile, 0, st>>>(ki, vi, ko, vo, nc, shift, w.hist);
-            uint32_t* t = ki;
-            ki = ko;
-            ko = t;
-            t = vi;
-            vi = vo;
-            vo = t;
-        }
+        e = dag_sort_rows(w, s.d, nc, (uint64_t)s.w - 1u, ki, vi, ko, vo, st);
+        if (e != cudaSuccess) return e;
         DagWs ws = w;
         ws.sk0 = ki;  // the sorted row is in whichever buffer the last pass wrote
         ws.sv0 = vi;
         dag_adj_kernel<<<dim3(blocks, s.d), 256, 0, st>>>(ws, nc);
         dag_run_kernel<<<blocks, 256, 0, st>>>(ws, nc, s.d);
-        uint32_t *pa = w.par0, *pb = w.par1;
-        for (uint32_t span = 1; span < nc; span <<= 1) {
-            dag_jump_kernel<<<blocks, 256, 0, st>>>(pa, pb, nc);
-            uint32_t* t = pa;
-            pa = pb;
-            pb = t;
-        }
+        const uint32_t tiles = (nc + kDagTile - 1) / kDagTile;
+        dag_headtile_kernel<<<tiles, kDagTile, 0, st>>>(ws.sv0, w.par0, nc, w.hist);
+        dag_head_kernel<<<tiles, kDagTile, 0, st>>>(ws.sv0, w.par0, nc, w.hist, w.par1);
+        const uint32_t* pa = w.par1;  // the head of every update
         dag_count_kernel<<<blocks, 256, 0, st>>>(ws, pa, nc);
-        cudaError_t e = cudaMemsetAsync(w.qcount, 0, 16, st);
+        // stable sort of every row by Fat counter: each update's count on its counters (the
+        // spare key wz marks updates without a valid index, which only explicit indices have)
+        ki = w.sk0, vi = w.sv0, ko = w.sk1, vo = w.sv1;
+        dag_slotkey_kernel<<<dim3(blocks, s.d), 256, 0, st>>>(ws, nc, s.z, wz, ki, vi);
+        e = dag_sort_rows(w, s.d, nc, s.idx_table ? (uint64_t)wz : (uint64_t)wz - 1u, ki, vi, ko, vo, st);
         if (e != cudaSuccess) return e;
-        dag_npred_kernel<<<blocks, 256, 0, st>>>(ws, pa, nc, s.d);
-        if (slim_in_smem)
-            dag_exec_kernel<true><<<1, kDagExecThreads, (size_t)slim_bytes, st>>>(s, ws, nc, ctrl);
-        else
-            dag_exec_kernel<false><<<1, kDagExecThreads, 0, st>>>(s, ws, nc, ctrl);
-        e = cudaGetLastError();
+        dag_rank_kernel<<<dim3(blocks, s.d), 256, 0, st>>>(ki, vi, w.cnt, nc);
+        e = cudaMemsetAsync(w.qcount, 0, 16, st);
+        if (e != cudaSuccess) return e;
+        dag_npred_kernel<<<blocks, 256, 0, st>>>(s, ws, pa, nc);
+        dag_fatadd_kernel<<<dim3(blocks, s.d), 256, 0, st>>>(s, ki, vi, w.cnt, nc, wz);
+        e = launch_walk(s, ws, nc, smem_limit, ctrl, st);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

@@ -117,6 +117,16 @@ def test_one_at_a_time_insertions_graph_path(sf, d, w, z, kb, s_, n):
     _queries_match(sf, g, o, qk)
 
 
+def test_one_at_a_time_graph_path_wide_frontier(sf):
+    """Uniform keys over many more ids than one piece holds: most updates start with no
+    predecessor, so the first frontiers overflow the walk's shared-memory queues into the global
+    ones; two pieces."""
+    st, ids = wl.mixed_stream(200_000, 1_000_000, 0.0, 0.0, 8, seed=4242)
+    g, o = _run_both(sf, 4, 1 << 17, 16, 8, 3, 1, [(st.keys, None)])
+    _assert_same(g, o)
+    _queries_match(sf, g, o, ids[:50_000])
+
+
 def test_one_at_a_time_graph_path_pinned_keys_and_explicit_ids(sf):
     import torch
     st, ids = wl.mixed_stream(40_000, 2_000, 1.2, 0.0, 4, seed=77)
