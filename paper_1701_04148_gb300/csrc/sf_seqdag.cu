@@ -7,17 +7,18 @@
 // result.  For a call of insertions only, taken in pieces of up to kDagN updates:
 //   1. hash every update (parallel);
 //   2. per row, a stable radix sort of (bucket, position) gives every update its predecessor and
-//      successor in each of its buckets (the neighbouring entries of the sorted row);
+//      successor in each of its buckets (the neighbouring entries of the sorted row); the same
+//      launches sort every row a second time, by Fat counter (bucket x z + slot), for step 4;
 //   3. runs (Lemma 2): an update whose predecessor in every row is the same earlier update with
 //      the same Fat slots continues that update's run; a run is a block of consecutive entries
 //      of row 0's sorted order, so a prefix maximum over that order finds each run's first
 //      update (its head), which counts the run's length r and records its last member;
 //   4. the Fat only grows under insertions, so the value a Fat counter holds right after an
 //      update is its value at the start of the piece plus the number of the piece's updates on
-//      that counter up to and including this one, in stream order.  A second stable sort of
-//      every row, by counter (bucket x z + slot), gives those counts, and with them each run's
-//      Fat estimate F (the minimum over rows, after its last member) before anything runs; the
-//      whole piece's Fat increments are then added in parallel;
+//      that counter up to and including this one, in stream order.  The rows sorted by counter
+//      give those counts, and with them each run's Fat estimate F (the minimum over rows, after
+//      its last member) before anything runs; the whole piece's Fat increments are then added
+//      in parallel;
 //   5. a run can go once, in every row, the run before it in that bucket has gone: heads count
 //      their pending predecessors, and one block walks the graph frontier by frontier, with the
 //      pending counts (four bits per update) and, where it fits, the Slim in shared memory.  A
@@ -42,24 +43,26 @@ struct DagWs {
     uint4* rec;                   // [N][4G] walk record of every run head (dag_npred_kernel)
     uint32_t* cnt;                // [d][N] the Fat counter of each update, counted up to it
     uint32_t *hb, *fb;            // [d][N] bucket and slot of every update
-    uint32_t *sk0, *sv0, *sk1, *sv1;  // [d][N] radix sort keys (buckets) and values (positions)
+    uint32_t *sk0, *sv0, *sk1, *sv1;  // [2d][N] radix sort keys and values (positions): rows 0..d-1
+                                      // keyed by bucket, rows d..2d-1 by Fat counter
     uint32_t *pred, *succ;        // [d][N] previous / next update in the same bucket
     uint32_t *par0, *par1;        // [N] run parent links, then every update's run head
     uint32_t *rlen, *lastm;       // [N] run length and last member, at heads
-    uint32_t *npred;              // [N] pending predecessors, at heads
+    uint32_t *npred;              // [N / 8] pending predecessors of the heads, four bits each
     uint32_t *bad;                // [N] the key had no valid index (explicit-index mode)
     uint32_t *q0, *q1;            // [N] frontier queues
     uint32_t *qcount;             // [4] queue counters
-    uint32_t *hist;               // [d][bins][tiles] digit counts, then offsets
+    uint32_t *hist;               // [2d][bins][tiles] digit counts, then offsets
 };
 
-// A walk record holds G = ceil(d / 4) uint4 groups each of buckets and successor heads, then
-// {run length, Fat estimate}; records sit 4G uint4 apart (64 bytes for d <= 4, 128 for d <= 8).
+// A walk record holds one uint4 per row i, {bucket h_i, successor head in that bucket, run
+// length, Fat estimate}, so the lane of row i reads its part in one load; records sit 4G uint4
+// apart, G = ceil(d / 4) (64 bytes for d <= 4, 128 for d <= 8).
 __host__ __device__ inline uint32_t dag_groups(uint32_t d) { return d <= 4 ? 1u : 2u; }
 
 __host__ __device__ inline uint64_t dag_bytes_for(uint32_t d) {
     const uint64_t N = kDagN;
-    return (16ull * dag_groups(d) * N + 9ull * d * N + 8ull * N + 64ull + (uint64_t)d * kDagBins * kDagTiles) * 4ull;
+    return (16ull * dag_groups(d) * N + 13ull * d * N + 8ull * N + 64ull + 2ull * d * kDagBins * kDagTiles) * 4ull;
 }
 
 DagWs dag_carve(void* base, uint32_t d) {
@@ -75,13 +78,13 @@ DagWs dag_carve(void* base, uint32_t d) {
     w.fb = p;
     p += d * N;
     w.sk0 = p;
-    p += d * N;
+    p += 2 * d * N;
     w.sv0 = p;
-    p += d * N;
+    p += 2 * d * N;
     w.sk1 = p;
-    p += d * N;
+    p += 2 * d * N;
     w.sv1 = p;
-    p += d * N;
+    p += 2 * d * N;
     w.pred = p;
     p += d * N;
     w.succ = p;
@@ -126,17 +129,23 @@ __global__ void __launch_bounds__(256) dag_hash_kernel(SketchDesc s, const uint8
 #pragma unroll
         for (int i = 0; i < kMaxD; ++i) h[i] = f[i] = 0u;  // a placeholder bucket; the update does nothing
     }
+    // sort keys: the bucket (rows 0..d-1) and the Fat counter, bucket x z + slot (rows d..2d-1);
+    // an update without a valid index counts on no counter and takes the spare key w x z
+    const uint32_t wz = s.w * s.z;
     for (uint32_t i = 0; i < s.d; ++i) {
         w.hb[i * kDagN + j] = h[i];
         w.fb[i * kDagN + j] = f[i];
         w.sk0[i * kDagN + j] = h[i];
         w.sv0[i * kDagN + j] = j;
+        w.sk0[(s.d + i) * kDagN + j] = ok ? h[i] * s.z + f[i] : wz;
+        w.sv0[(s.d + i) * kDagN + j] = j;
         w.pred[i * kDagN + j] = kDagNone;
         w.succ[i * kDagN + j] = kDagNone;
     }
+    if (j < 4) w.qcount[j] = 0u;
     w.rlen[j] = 0u;
     w.lastm[j] = 0u;
-    w.npred[j] = 0u;
+    if ((j & 7u) == 0u) w.npred[j >> 3] = 0u;
     w.bad[j] = ok ? 0u : 1u;
 }
 
@@ -268,7 +277,7 @@ __global__ void __launch_bounds__(256) dag_run_kernel(DagWs w, uint32_t n, uint3
 //     row-0 predecessor is the member before it), so an update's head is the last entry, at or
 //     before it in that order, that starts a run: a prefix maximum of the starting entries'
 //     indices, per tile (dag_headtile_kernel) and then with the maximum of the earlier tiles
-//     (dag_head_kernel).
+//     (dag_head_kernel), which also counts every run's length and records its last member.
 __device__ __forceinline__ uint32_t block_max_scan(uint32_t v, uint32_t* s_w) {
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -310,7 +319,8 @@ __global__ void __launch_bounds__(kDagTile) dag_headtile_kernel(const uint32_t* 
 __global__ void __launch_bounds__(kDagTile) dag_head_kernel(const uint32_t* __restrict__ sv0,
                                                             const uint32_t* __restrict__ par, uint32_t n,
                                                             const uint32_t* __restrict__ agg,
-                                                            uint32_t* __restrict__ head) {
+                                                            uint32_t* __restrict__ head, uint32_t* __restrict__ rlen,
+                                                            uint32_t* __restrict__ lastm) {
     __shared__ uint32_t s_w[32];
     __shared__ uint32_t s_carry;
     if (threadIdx.x < 32) {
@@ -323,29 +333,16 @@ __global__ void __launch_bounds__(kDagTile) dag_head_kernel(const uint32_t* __re
     const uint32_t q = blockIdx.x * kDagTile + threadIdx.x;
     uint32_t v = block_max_scan(run_start_mark(sv0, par, q, n), s_w);  // its barriers also publish s_carry
     v = max(v, s_carry);
-    if (q < n) head[sv0[q]] = sv0[v - 1u];  // v >= 1: entry 0 of a row always starts a run
+    if (q < n) {
+        const uint32_t pos = sv0[q], hd = sv0[v - 1u];  // v >= 1: entry 0 of a row always starts a run
+        head[pos] = hd;
+        // the run's length and last member, at its head
+        atomicAdd(&rlen[hd], 1u);
+        atomicMax(&lastm[hd], pos);
+    }
 }
 
-// 3c. run lengths and last members, at heads
-__global__ void __launch_bounds__(256) dag_count_kernel(DagWs w, const uint32_t* __restrict__ head, uint32_t n) {
-    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    const uint32_t hd = head[j];
-    atomicAdd(&w.rlen[hd], 1u);
-    atomicMax(&w.lastm[hd], j);
-}
-
-// 4a. sort keys of the Fat counters: bucket x z + slot in row order, w * z for an update without a
-//     valid index (it counts on no counter)
-__global__ void __launch_bounds__(256) dag_slotkey_kernel(DagWs w, uint32_t n, uint32_t z, uint32_t wz,
-                                                          uint32_t* __restrict__ kout, uint32_t* __restrict__ vout) {
-    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x, row = blockIdx.y;
-    if (j >= n) return;
-    kout[row * kDagN + j] = w.bad[j] ? wz : w.hb[row * kDagN + j] * z + w.fb[row * kDagN + j];
-    vout[row * kDagN + j] = j;
-}
-
-// 4b. counts: in a row sorted by counter (stable, so stream order within a counter), the update at
+// 4a. counts: in a row sorted by counter (stable, so stream order within a counter), the update at
 //     sorted index q is the (q - first + 1)-th of the piece on its counter, where first is the
 //     counter's first sorted index (a binary search over the sorted keys)
 __global__ void __launch_bounds__(256) dag_rank_kernel(const uint32_t* __restrict__ sk, const uint32_t* __restrict__ sv,
@@ -363,7 +360,7 @@ __global__ void __launch_bounds__(256) dag_rank_kernel(const uint32_t* __restric
     cnt[row * kDagN + sv[row * kDagN + q]] = q - lo + 1u;
 }
 
-// 4c. the piece's Fat increments, one atomic per counter: the last update of a counter in sorted
+// 4b. the piece's Fat increments, one atomic per counter: the last update of a counter in sorted
 //     order adds the counter's count
 __global__ void __launch_bounds__(256) dag_fatadd_kernel(SketchDesc s, const uint32_t* __restrict__ sk,
                                                          const uint32_t* __restrict__ sv,
@@ -376,7 +373,7 @@ __global__ void __launch_bounds__(256) dag_fatadd_kernel(SketchDesc s, const uin
     atomicAdd(s.B + (uint64_t)row * wz + key, cnt[row * kDagN + sv[row * kDagN + q]]);
 }
 
-// 4d. pending predecessors of every head (one per row that has one), and its successors: the
+// 4c. pending predecessors of every head (one per row that has one), and its successors: the
 //     next update, in each row's bucket, after the run's last member -- always another run's
 //     head, since a run member's predecessors are all inside its run.  Everything the walk needs
 //     of a head goes into its record: buckets, successor heads, the run length (0 for an update
@@ -405,28 +402,30 @@ __global__ void __launch_bounds__(256) dag_npred_kernel(SketchDesc s, DagWs w, c
             }
         }
     }
-    const uint32_t G = dag_groups(d);
+    const uint32_t G = dag_groups(d), rl = ok ? w.rlen[j] : 0u;
     uint4* r = w.rec + 4ull * G * j;
 #pragma unroll
-    for (uint32_t g = 0; g < 2; ++g) {
-        if (g < G) {
-            r[g] = make_uint4(hb[4 * g], hb[4 * g + 1], hb[4 * g + 2], hb[4 * g + 3]);
-            r[G + g] = make_uint4(sx[4 * g], sx[4 * g + 1], sx[4 * g + 2], sx[4 * g + 3]);
-        }
-    }
-    r[2 * G] = make_uint4(ok ? w.rlen[j] : 0u, F, 0u, 0u);
-    w.npred[j] = c;
-    if (c == 0) w.q0[atomicAdd(&w.qcount[0], 1u)] = j;
+    for (int i = 0; i < kMaxD; ++i)
+        if (i < (int)d) r[i] = make_uint4(hb[i], sx[i], rl, F);
+    if (c != 0) atomicOr(&w.npred[j >> 3], c << (4u * (j & 7u)));
+    else w.q0[atomicAdd(&w.qcount[0], 1u)] = j;
 }
 
 // 5. the graph walk, one block, level by level.  A head is taken by P = 1, 2, 4 or 8 lanes
-//    (the power of two >= d), lane i for row i: it reads word i of the head's bucket and
-//    successor groups, its Slim counter and its successor's pending count, and the lanes of a
-//    head combine their Slim minimum with two shuffles, so a head costs a few instructions per
-//    lane and a warp's record loads touch one cache line per head.  Shared memory holds the
-//    pending counts (one byte per update of the piece: at most d <= 8 each), the frontier
-//    queues up to qcap heads (the rest in the global queues) and, with kSmemSlim, the Slim.
+//    (the power of two >= d), lane i for row i: it reads its row's 16 bytes of the head's
+//    record, its Slim counter and its successor's pending count, and the lanes of a head
+//    combine their Slim minimum with shuffles, so a head costs a few instructions per lane and
+//    a warp's record loads touch one cache line per head.  Shared memory holds the
+//    pending counts (four bits per update of the piece: at most d <= 8 each), the frontier
+//    queues up to qcap heads (the rest in the global queues) and, with kSmemSlim, the Slim;
+//    it stays small enough to leave the L1 room for the successors' records, prefetched there
+//    while their predecessors run.
 constexpr int kDagWalkThreads = 1024;
+
+// Words of the pending-count nibbles of n updates, rounded to whole uint4 (the Slim after them
+// stays 16-byte aligned).
+__host__ __device__ inline uint32_t walk_np_words(uint32_t n) { return ((n + 7u) / 8u + 3u) & ~3u; }
+static_assert(kMaxD <= 15, "a pending count fits four bits");
 
 __device__ __forceinline__ void prefetch_l1(const void* p) {
     asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
@@ -445,27 +444,28 @@ __global__ void __launch_bounds__(kDagWalkThreads, 1) dag_walk_kernel(SketchDesc
     constexpr uint32_t kHeadsPerIter = kDagWalkThreads / P;
     extern __shared__ uint32_t s_dyn[];
     __shared__ uint32_t s_next[3];
-    // dynamic shared memory: queues [2][qcap], pending-count bytes, then the Slim
+    // dynamic shared memory: queues [2][qcap], pending-count nibbles, then the Slim (both copied
+    // in with 16-byte loads)
     uint32_t* s_q = s_dyn;
     uint32_t* s_np = s_q + 2ull * qcap;
-    const uint32_t np_words = (n + 3u) / 4u;
+    const uint32_t np_words = walk_np_words(n);
     uint32_t* sA = s_np + np_words;
     const uint64_t slim_n = (uint64_t)D * s.w;
-    if (kSmemSlim) {
-        for (uint64_t i = threadIdx.x; i < slim_n; i += blockDim.x) sA[i] = __ldcg(s.A + i);
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(w.npred);
+        uint4* dst = reinterpret_cast<uint4*>(s_np);
+        for (uint32_t t = threadIdx.x; t < np_words / 4u; t += blockDim.x) dst[t] = __ldcg(src + t);
     }
-    for (uint32_t t = threadIdx.x; t < np_words; t += blockDim.x) {
-        uint32_t v = 0;
-#pragma unroll
-        for (uint32_t b = 0; b < 4; ++b)
-            if (4 * t + b < n) v |= (__ldcg(w.npred + 4 * t + b) & 0xFFu) << (8 * b);
-        s_np[t] = v;
+    if (kSmemSlim) {
+        const uint4* src = reinterpret_cast<const uint4*>(s.A);
+        uint4* dst = reinterpret_cast<uint4*>(sA);
+        for (uint64_t t = threadIdx.x; t < slim_n / 4u; t += blockDim.x) dst[t] = __ldcg(src + t);
+        for (uint64_t i = (slim_n & ~3ull) + threadIdx.x; i < slim_n; i += blockDim.x) sA[i] = __ldcg(s.A + i);
     }
     uint32_t* A = kSmemSlim ? sA : s.A;
     const uint32_t row = threadIdx.x % P;            // this lane's row (idle when >= D)
     const uint32_t slot = threadIdx.x / P;           // this lane's head within an iteration
     const bool live_row = row < (uint32_t)D;
-    const uint32_t* recw = reinterpret_cast<const uint32_t*>(w.rec);
     uint32_t ncur = __ldcg(&w.qcount[0]);
     for (uint32_t q = threadIdx.x; q < ncur && q < qcap; q += blockDim.x) s_q[q] = __ldcg(w.q0 + q);
     // Queue counters rotate over three words, so one barrier per level suffices: level L pushes
@@ -494,32 +494,40 @@ __global__ void __launch_bounds__(kDagWalkThreads, 1) dag_walk_kernel(SketchDesc
             const bool live = hq < ncur;
             uint32_t j = 0;
             if (live) j = hq < qcap ? s_q[(uint64_t)cb * qcap + hq] : __ldcg(gcur + hq);
-            const uint32_t* rw = recw + 16ull * G * j;  // the record: 4G uint4 = 16G words
             uint32_t hb = 0, sx = kDagNone, r = 0, F = 0, a = 0xFFFFFFFFu;
-            if (live) {
-                r = __ldg(rw + 8 * G);
-                F = __ldg(rw + 8 * G + 1);
-                if (live_row) {
-                    hb = __ldg(rw + row);
-                    sx = __ldg(rw + 4 * G + row);
-                }
+            if (live && live_row) {
+                const uint4 c = __ldg(w.rec + 4ull * G * j + row);  // {h_i, successor, r, F}
+                hb = c.x;
+                sx = c.y;
+                r = c.z;
+                F = c.w;
             }
-            if (sx != kDagNone) prefetch_l1(recw + 16ull * G * sx);
+            if (sx != kDagNone) prefetch_l1(w.rec + 4ull * G * sx);
             if (live && live_row) a = A[(uint64_t)row * s.w + hb];
             uint32_t m = a;
 #pragma unroll
             for (int off = 1; off < P; off <<= 1) m = min(m, __shfl_xor_sync(0xFFFFFFFFu, m, off));
-            if (live && live_row && r != 0u) {
+            if (live_row && r != 0u) {
                 const uint64_t mr = (uint64_t)m + r;
                 const uint32_t T = mr < (uint64_t)F ? (uint32_t)mr : F;
                 if (a < T) A[(uint64_t)row * s.w + hb] = T;
             }
-            // one pending predecessor less for this row's successor; the last one queues it
+            // one pending predecessor less for this row's successor; the last one queues it, in a
+            // slot reserved once per warp
+            bool rel = false;
             if (sx != kDagNone) {
-                const uint32_t sh = 8u * (sx & 3u);
-                const uint32_t old = atomicSub(&s_np[sx >> 2], 1u << sh);
-                if (((old >> sh) & 0xFFu) == 1u) {
-                    const uint32_t idx = atomicAdd(&s_next[c_now], 1u);
+                const uint32_t sh = 4u * (sx & 7u);
+                const uint32_t old = atomicSub(&s_np[sx >> 3], 1u << sh);
+                rel = ((old >> sh) & 0xFu) == 1u;
+            }
+            const unsigned relb = __ballot_sync(0xFFFFFFFFu, rel);
+            if (relb) {
+                const uint32_t lane = threadIdx.x & 31u, leader = (uint32_t)(__ffs(relb) - 1);
+                uint32_t first = 0;
+                if (lane == leader) first = atomicAdd(&s_next[c_now], (uint32_t)__popc(relb));
+                first = __shfl_sync(0xFFFFFFFFu, first, leader);
+                if (rel) {
+                    const uint32_t idx = first + (uint32_t)__popc(relb & ((1u << lane) - 1u));
                     if (idx < qcap) s_q[(uint64_t)nb * qcap + idx] = sx;
                     else gnext[idx] = sx;
                 }
@@ -531,16 +539,19 @@ __global__ void __launch_bounds__(kDagWalkThreads, 1) dag_walk_kernel(SketchDesc
     }
     if (kSmemSlim) {
         __syncthreads();
-        for (uint64_t i = threadIdx.x; i < slim_n; i += blockDim.x) s.A[i] = sA[i];
+        const uint4* src = reinterpret_cast<const uint4*>(sA);
+        uint4* dst = reinterpret_cast<uint4*>(s.A);
+        for (uint64_t t = threadIdx.x; t < slim_n / 4u; t += blockDim.x) dst[t] = src[t];
+        for (uint64_t i = (slim_n & ~3ull) + threadIdx.x; i < slim_n; i += blockDim.x) s.A[i] = sA[i];
     }
 }
 
 template <int D>
 static cudaError_t launch_walk_d(const SketchDesc& s, const DagWs& w, uint32_t nc, int smem_limit, uint32_t* ctrl,
                                  cudaStream_t st) {
-    // dynamic shared memory: the pending-count bytes of a full piece, queues of qcap heads per
+    // dynamic shared memory: the pending-count nibbles of a full piece, queues of qcap heads per
     // frontier (up to 2,048, at least 256) and the Slim when it fits beside them
-    const uint64_t np_bytes = kDagN;
+    const uint64_t np_bytes = walk_np_words(kDagN) * 4ull;
     const uint64_t slim_bytes = (uint64_t)D * s.w * 4ull;
     const uint64_t budget = (uint64_t)smem_limit - 1024ull;  // static counters and slack
     if (budget < np_bytes + 2ull * 256ull * 4ull) return cudaErrorInvalidValue;
@@ -549,8 +560,7 @@ static cudaError_t launch_walk_d(const SketchDesc& s, const DagWs& w, uint32_t n
     if (qcap > 2048) qcap = 2048;
     qcap &= ~31ull;
     const size_t dyn_max = (size_t)(2ull * qcap * 4ull + np_bytes + (slim_in_smem ? slim_bytes : 0ull));
-    const size_t dyn = (size_t)(2ull * qcap * 4ull + (uint64_t)((nc + 3u) / 4u) * 4ull +
-                                (slim_in_smem ? slim_bytes : 0ull));
+    const size_t dyn = (size_t)(2ull * qcap * 4ull + walk_np_words(nc) * 4ull + (slim_in_smem ? slim_bytes : 0ull));
     cudaError_t e;
     if (slim_in_smem) {
         e = cudaFuncSetAttribute(dag_walk_kernel<D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
@@ -583,17 +593,18 @@ static cudaError_t launch_walk(const SketchDesc& s, const DagWs& w, uint32_t nc,
 
 uint64_t dag_workspace_bytes(uint32_t d) { return dag_bytes_for(d); }
 
-// One stable LSD radix sort of every row: keys ki, values vi (both [d][N]), by the bits below
-// key_limit; ko, vo are the other buffers.  Returns the buffers holding the sorted rows.
-static cudaError_t dag_sort_rows(const DagWs& w, uint32_t d, uint32_t nc, uint64_t key_limit, uint32_t*& ki,
+// One stable LSD radix sort of `rows` rows: keys ki, values vi (both [rows][N]), by every bit up
+// to the highest of key_limit; ko, vo are the other buffers.  Returns the buffers holding the
+// sorted rows.
+static cudaError_t dag_sort_rows(const DagWs& w, uint32_t rows, uint32_t nc, uint64_t key_limit, uint32_t*& ki,
                                  uint32_t*& vi, uint32_t*& ko, uint32_t*& vo, cudaStream_t st) {
     const uint32_t tiles = (nc + kDagTile - 1) / kDagTile;
     for (uint32_t shift = 0; shift < 32 && (shift == 0 || (key_limit >> shift) != 0); shift += kDagRadixBits) {
-        cudaError_t e = cudaMemsetAsync(w.hist, 0, (uint64_t)d * kDagBins * kDagTiles * 4ull, st);
+        cudaError_t e = cudaMemsetAsync(w.hist, 0, (uint64_t)rows * kDagBins * kDagTiles * 4ull, st);
         if (e != cudaSuccess) return e;
-        dag_hist_kernel<<<dim3(tiles, d), 256, 0, st>>>(ki, nc, shift, w.hist);
-        dag_scan_kernel<<<d, 1024, 0, st>>>(w.hist);
-        dag_scatter_kernel<<<dim3(tiles, d), kDagTile, 0, st>>>(ki, vi, ko, vo, nc, shift, w.hist);
+        dag_hist_kernel<<<dim3(tiles, rows), 256, 0, st>>>(ki, nc, shift, w.hist);
+        dag_scan_kernel<<<rows, 1024, 0, st>>>(w.hist);
+        dag_scatter_kernel<<<dim3(tiles, rows), kDagTile, 0, st>>>(ki, vi, ko, vo, nc, shift, w.hist);
         uint32_t* t = ki;
         ki = ko;
         ko = t;
@@ -615,31 +626,26 @@ cudaError_t launch_seq_dag(const SketchDesc& s, const uint8_t* keys, uint64_t n,
         const uint32_t nc = (uint32_t)(n - base < (uint64_t)kDagN ? n - base : (uint64_t)kDagN);
         const uint32_t blocks = (nc + 255) / 256;
         dag_hash_kernel<<<blocks, 256, 0, st>>>(s, keys + base * s.key_bytes, nc, w, ctrl);
-        // stable sort of every row by bucket: each update's neighbours in its buckets
+        // one stable sort of 2d rows: by bucket (each update's neighbours in its buckets) and by
+        // Fat counter (each update's count on its counters); the spare counter key wz exists
+        // only with explicit indices
         uint32_t *ki = w.sk0, *vi = w.sv0, *ko = w.sk1, *vo = w.sv1;
-        e = dag_sort_rows(w, s.d, nc, (uint64_t)s.w - 1u, ki, vi, ko, vo, st);
+        e = dag_sort_rows(w, 2u * s.d, nc, s.idx_table ? (uint64_t)wz : (uint64_t)wz - 1u, ki, vi, ko, vo, st);
         if (e != cudaSuccess) return e;
         DagWs ws = w;
-        ws.sk0 = ki;  // the sorted row is in whichever buffer the last pass wrote
+        ws.sk0 = ki;  // the sorted rows are in whichever buffers the last pass wrote
         ws.sv0 = vi;
+        const uint32_t* kc = ki + (uint64_t)s.d * kDagN;  // rows sorted by Fat counter
+        const uint32_t* vc = vi + (uint64_t)s.d * kDagN;
         dag_adj_kernel<<<dim3(blocks, s.d), 256, 0, st>>>(ws, nc);
         dag_run_kernel<<<blocks, 256, 0, st>>>(ws, nc, s.d);
         const uint32_t tiles = (nc + kDagTile - 1) / kDagTile;
         dag_headtile_kernel<<<tiles, kDagTile, 0, st>>>(ws.sv0, w.par0, nc, w.hist);
-        dag_head_kernel<<<tiles, kDagTile, 0, st>>>(ws.sv0, w.par0, nc, w.hist, w.par1);
+        dag_head_kernel<<<tiles, kDagTile, 0, st>>>(ws.sv0, w.par0, nc, w.hist, w.par1, w.rlen, w.lastm);
         const uint32_t* pa = w.par1;  // the head of every update
-        dag_count_kernel<<<blocks, 256, 0, st>>>(ws, pa, nc);
-        // stable sort of every row by Fat counter: each update's count on its counters (the
-        // spare key wz marks updates without a valid index, which only explicit indices have)
-        ki = w.sk0, vi = w.sv0, ko = w.sk1, vo = w.sv1;
-        dag_slotkey_kernel<<<dim3(blocks, s.d), 256, 0, st>>>(ws, nc, s.z, wz, ki, vi);
-        e = dag_sort_rows(w, s.d, nc, s.idx_table ? (uint64_t)wz : (uint64_t)wz - 1u, ki, vi, ko, vo, st);
-        if (e != cudaSuccess) return e;
-        dag_rank_kernel<<<dim3(blocks, s.d), 256, 0, st>>>(ki, vi, w.cnt, nc);
-        e = cudaMemsetAsync(w.qcount, 0, 16, st);
-        if (e != cudaSuccess) return e;
+        dag_rank_kernel<<<dim3(blocks, s.d), 256, 0, st>>>(kc, vc, w.cnt, nc);
         dag_npred_kernel<<<blocks, 256, 0, st>>>(s, ws, pa, nc);
-        dag_fatadd_kernel<<<dim3(blocks, s.d), 256, 0, st>>>(s, ki, vi, w.cnt, nc, wz);
+        dag_fatadd_kernel<<<dim3(blocks, s.d), 256, 0, st>>>(s, kc, vc, w.cnt, nc, wz);
         e = launch_walk(s, ws, nc, smem_limit, ctrl, st);
         if (e != cudaSuccess) return e;
     }
