@@ -11,6 +11,7 @@
 
 #include "sf.h"
 #include "sf_internal.h"
+#include "sf_seqdag.h"
 
 #include "sf_handle.h"
 

@@ -100,9 +100,6 @@ cudaError_t launch_seq_update(const SeqArgs& a, cudaStream_t st, int smem_limit)
 // dag_workspace_bytes(d) bytes (4-byte aligned) owned by the sketch.
 constexpr uint32_t kDagN = 131072;
 constexpr uint32_t kDagMinW = 1024;
-// The graph path sorts every row by Fat counter (bucket x z + slot) with one spare key value, so
-// it also needs w * z < 2^32.
-inline bool dag_eligible(uint32_t w, uint32_t z) { return w >= kDagMinW && (uint64_t)w * z < (1ull << 32); }
 uint64_t dag_workspace_bytes(uint32_t d);
 cudaError_t launch_seq_dag(const SketchDesc& s, const uint8_t* keys, uint64_t n, void* ws_base, uint32_t* ctrl,
                            int smem_limit, cudaStream_t st);

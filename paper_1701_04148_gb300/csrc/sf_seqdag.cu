@@ -27,6 +27,7 @@
 //      counters.
 // A piece's graph is only as deep as its longest chain of runs through shared buckets.
 #include "sf_internal.h"
+#include "sf_seqdag.h"
 
 namespace sfk {
 
