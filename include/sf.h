@@ -145,7 +145,9 @@ sf_status sf_destroy(sf_sketch *s);
  * Explicit-index mode (params.flags & SF_FLAG_EXPLICIT_INDEX): keys are uint32 ids and the
  * device table holds, for id q and row i, h_i = table[(q*d + i)*2], f_i = table[(q*d + i)*2 + 1]
  * (h_i < w, f_i < z).  Used to replay worked examples with hand-chosen indices (Sec. 3.2).
- * Ids >= n_keys are rejected on the device (SF_ERR_INVALID at the next sf_sync).
+ * Ids >= n_keys are rejected on the device (SF_ERR_INVALID at the next sf_sync): such an update
+ * changes no counter, and the others apply as they would with its operation removed from its
+ * chunk (its stream position still counts towards the chunk boundaries).
  */
 sf_status sf_set_index_table(sf_sketch *s, const uint32_t *table_dev, uint32_t n_keys);
 

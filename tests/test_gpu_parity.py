@@ -151,6 +151,32 @@ def test_one_at_a_time_graph_path_pinned_keys_and_explicit_ids(sf):
     _assert_same(g, o)
 
 
+@pytest.mark.parametrize("w,S", [(2048, 1), (500, 1), (2048, 4096)])
+def test_explicit_ids_out_of_range_are_skipped_and_reported(sf, w, S):
+    """Ids beyond the index table are reported (SF_ERR_INVALID at the next sync) and change no
+    counter: the sketch equals the oracle's with those updates' operations set to 0 (the graph
+    path, the one-warp window path and the chunked path)."""
+    import torch
+    gen = np.random.default_rng(17 + w + S)
+    n_keys = 300
+    table = np.stack([gen.integers(0, w, (n_keys, 4)), gen.integers(0, 16, (n_keys, 4))], axis=2).astype(np.uint32)
+    ids = gen.integers(0, n_keys + 25, 20_000).astype(np.uint32)
+    valid = ids < n_keys
+    assert 0 < int((~valid).sum()) < len(ids)
+    g = sf.Sketch(4, w, 16, 4, 0, S, explicit_index=True)
+    g.set_index_table(torch.from_numpy(table.view(np.int32)).cuda())
+    g.insert(torch.from_numpy(ids.view(np.int32)).cuda())
+    assert g.sync_status() == sf.SF_ERR_INVALID
+    o = oracle.Sketch(4, w, 16, 4, 0)
+    hh, ff, ident = oracle.explicit_indices(table, np.where(valid, ids, 0).astype(np.uint32))
+    ops = valid.astype(np.int8)
+    if S == 1:
+        o.seq_apply(hh, ff, ops)
+    else:
+        o.chunk_apply(hh, ff, ops, S, ids.view(np.uint8).reshape(-1, 4))
+    _assert_same(g, o)
+
+
 @pytest.mark.parametrize("n", [1, 31, 32, 33, 64, 65, 97])
 def test_one_at_a_time_short_streams(sf, n):
     """S = 1 on lengths around the 32-update window and the two-window key prefetch."""
