@@ -921,7 +921,7 @@ def run_outofl2(args, ctx):
 def run_l2curve(args, ctx):
     """Random 32-bit loads, reductions and the 1:1 mix (sf_bench_random_access kinds 2, 0, 5;
     2^28 operations, best of three) over buffers of 32-160 MiB: where the L2 stops holding a
-    random working set."""
+    random working set; then the returning atomic forms (kinds 1, 3, 4) at 64 MiB and 1 GiB."""
     import torch
     L, dev, stream = ctx["L"], ctx["dev"], ctx["stream"]
     mib = 1 << 20
@@ -945,7 +945,28 @@ def run_l2curve(args, ctx):
                 best = max(best, (1 << 28) / a.elapsed_time(b) / 1e6)
             row[name] = round(best, 1)
         rows.append(row)
-    del buf
+    # the returning forms (atomicAdd with its result used, 32-bit CAS) and atomicMax beside the
+    # plain reduction, in L2 (64 MiB) and in HBM (1 GiB)
+    atomics = []
+    big = torch.zeros((1024 * mib) // 4, dtype=torch.int32, device=dev)
+    for size, b in ((64, buf), (1024, big)):
+        n = size * mib // 4
+        row = {"mib": size}
+        for name, kind in (("red", 0), ("atom_ret", 1), ("red_max", 3), ("cas32", 4)):
+            L.sf_bench_random_access(b.data_ptr(), n, 1 << 26, kind, 0, h_st)
+            best = 0.0
+            for _ in range(3):
+                a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                rc = L.sf_bench_random_access(b.data_ptr(), n, 1 << 28, kind, 0, h_st)
+                e.record(stream)
+                torch.cuda.synchronize()
+                if rc != 0:
+                    raise SystemExit(f"sf_bench_random_access failed: {rc}")
+                best = max(best, (1 << 28) / a.elapsed_time(e) / 1e6)
+            row[name] = round(best, 1)
+        atomics.append(row)
+    del buf, big
     # one grid barrier of the persistent update kernel's kind (cooperative, one block per SM)
     scr = torch.zeros(64, dtype=torch.int32, device=dev)
     L.sf_bench_grid_barrier(scr.data_ptr(), 100, h_st)
@@ -956,7 +977,7 @@ def run_l2curve(args, ctx):
     torch.cuda.synchronize()
     if rc != 0:
         raise SystemExit(f"sf_bench_grid_barrier failed: {rc}")
-    return {"workload": "l2curve", "unit": "G random 32-bit ops/s", "rows": rows,
+    return {"workload": "l2curve", "unit": "G random 32-bit ops/s", "rows": rows, "atomics": atomics,
             "grid_barrier_us": round(a.elapsed_time(b) * 1e3 / 2000, 3)}
 
 
