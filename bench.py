@@ -921,7 +921,7 @@ def run_outofl2(args, ctx):
 def run_l2curve(args, ctx):
     """Random 32-bit loads, reductions and the 1:1 mix (sf_bench_random_access kinds 2, 0, 5;
     2^28 operations, best of three) over buffers of 32-160 MiB: where the L2 stops holding a
-    random working set; then the returning atomic forms (kinds 1, 3, 4) at 64 MiB and 1 GiB."""
+    random working set; then the returning atomic forms (kinds 1, 3, 4, 6) at 64 MiB and 1 GiB."""
     import torch
     L, dev, stream = ctx["L"], ctx["dev"], ctx["stream"]
     mib = 1 << 20
@@ -952,7 +952,7 @@ def run_l2curve(args, ctx):
     for size, b in ((64, buf), (1024, big)):
         n = size * mib // 4
         row = {"mib": size}
-        for name, kind in (("red", 0), ("atom_ret", 1), ("red_max", 3), ("cas32", 4)):
+        for name, kind in (("red", 0), ("atom_ret", 1), ("red_max", 3), ("cas32", 4), ("cas128", 6)):
             L.sf_bench_random_access(b.data_ptr(), n, 1 << 26, kind, 0, h_st)
             best = 0.0
             for _ in range(3):

@@ -25,11 +25,14 @@ extern "C" {
 #define SF_BENCH_MIX_RED_LD 5u /* even warps atomicAdd (result unused), odd warps 32-bit load bypassing
                                   L1: the 1:1 read-modify-write / load mix of the sketch update (on a
                                   GB300 this schedule measured above alternating the two in one thread) */
+#define SF_BENCH_CAS128    6u  /* 128-bit CAS on the 16-byte-aligned group holding the word (result
+                                  used): the update's dictionary claim                            */
 
 /*
  * Issues total_ops random 32-bit operations of `kind` on buf_dev[0 .. n_words) (device,
  * caller-owned, contents overwritten; n_words a power of two or at most 2^32, else
- * SF_ERR_INVALID) on cuda_stream.  Addresses come from a 64-bit LCG per thread (uniform over the
+ * SF_ERR_INVALID; for SF_BENCH_CAS128 also a multiple of 4, with buf_dev 16-byte aligned) on
+ * cuda_stream.  Addresses come from a 64-bit LCG per thread (uniform over the
  * buffer).  grid_blocks = 0 picks 8 blocks of
  * 256 threads per SM.  The caller times the call with CUDA events.
  */

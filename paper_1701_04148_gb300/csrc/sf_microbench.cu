@@ -29,6 +29,12 @@ __global__ void __launch_bounds__(256) random_access_kernel(uint32_t* __restrict
                 if (threadIdx.x & 32u) acc += __ldcg(buf + idx);
                 else atomicAdd(buf + idx, 1u);
                 break;
+            case SF_BENCH_CAS128: {
+                unsigned long long ol, oh;
+                cas128(reinterpret_cast<unsigned long long*>(buf + (idx & ~3ull)), 0ull, 0ull, x, tid, ol, oh);
+                acc += (uint32_t)(ol ^ oh);
+                break;
+            }
             default: acc += atomicCAS(buf + idx, 0u, (uint32_t)tid); break;
         }
     }
@@ -55,7 +61,8 @@ extern "C" {
 
 sf_status sf_bench_random_access(uint32_t* buf_dev, uint64_t n_words, uint64_t total_ops, uint32_t kind,
                                  uint32_t grid_blocks, void* cuda_stream) {
-    if (!buf_dev || n_words == 0 || kind > SF_BENCH_MIX_RED_LD) return SF_ERR_INVALID;
+    if (!buf_dev || n_words == 0 || kind > SF_BENCH_CAS128) return SF_ERR_INVALID;
+    if (kind == SF_BENCH_CAS128 && (((uintptr_t)buf_dev & 15u) != 0 || (n_words & 3u) != 0)) return SF_ERR_INVALID;
     if ((n_words & (n_words - 1)) != 0 && n_words > (1ull << 32)) return SF_ERR_INVALID;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
