@@ -496,8 +496,10 @@ __global__ void __launch_bounds__(kDagWalkThreads, 1) dag_walk_kernel(SketchDesc
         const uint32_t nb = cb ^ 1u;
         uint32_t* gcur = cb ? w.q1 : w.q0;
         uint32_t* gnext = cb ? w.q0 : w.q1;
-        // every lane runs the same number of iterations (the shuffles need the whole warp)
-        for (uint32_t base = 0; base < ncur; base += kHeadsPerIter) {
+        // the lanes of a warp run the same iterations (the shuffles need the whole warp); a warp
+        // whose first head slot is past the frontier has nothing left to do in this level
+        const uint32_t warp_first_slot = (threadIdx.x & ~31u) / P;
+        for (uint32_t base = 0; base + warp_first_slot < ncur; base += kHeadsPerIter) {
             const uint32_t hq = base + slot;
             const bool live = hq < ncur;
             uint32_t j = 0;
