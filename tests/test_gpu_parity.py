@@ -117,6 +117,16 @@ def test_one_at_a_time_insertions_graph_path(sf, d, w, z, kb, s_, n):
     _queries_match(sf, g, o, qk)
 
 
+@pytest.mark.parametrize("d,z", [(2, 16), (5, 3), (6, 16), (7, 5)])
+def test_one_at_a_time_graph_path_every_row_count(sf, d, z):
+    """The graph walk is compiled for each d: the row counts the shapes above do not reach, with
+    Zipf-hot keys (long runs) over two calls."""
+    st, ids = wl.mixed_stream(30_000, 3_000, 1.2, 0.0, 4, seed=600 + d)
+    g, o = _run_both(sf, d, 1024 + 64 * d, z, 4, 11, 1, [(st.keys[:10_001], None), (st.keys[10_001:], None)])
+    _assert_same(g, o)
+    _queries_match(sf, g, o, ids)
+
+
 def test_one_at_a_time_graph_path_wide_frontier(sf):
     """Uniform keys over many more ids than one piece holds: most updates start with no
     predecessor, so the first frontiers overflow the walk's shared-memory queues into the global
@@ -226,7 +236,8 @@ def test_key_widths(sf, kb):
         _queries_match(sf, g, o, pool)
 
 
-@pytest.mark.parametrize("d,w,z", [(1, 1, 1), (2, 5, 3), (5, 300, 7), (8, 4096, 16), (4, 1 << 12, 64)])
+@pytest.mark.parametrize("d,w,z", [(1, 1, 1), (2, 5, 3), (5, 300, 7), (6, 777, 9), (7, 1500, 16), (8, 4096, 16),
+                                   (4, 1 << 12, 64)])
 def test_shapes(sf, d, w, z):
     st, ids = wl.mixed_stream(12_345, 2_000, 0.9, 0.25, 4, seed=d * 100 + z)
     for S in (1, 3, 4096):
