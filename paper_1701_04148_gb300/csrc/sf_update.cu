@@ -169,20 +169,24 @@ __device__ __forceinline__ uint32_t slack_of(uint32_t Fl, uint32_t m) {
 // Global part of phase 1 for one (block- or warp-) leader: Fat increments of the net count,
 // dictionary claim/lookup (one 128-bit CAS per probe), counts, chunk-start Slim minimum.  Returns
 // the slot this thread claimed, or kNoSlot.  With keep_own, a claimer leaves its counts, m and
-// mask in *own instead of writing them to the entry.  In insertion-only launches (ins_only) the
-// Fat increments return the old values, which give the leader's slack.
+// mask in *own instead of writing them to the entry.  In insertion-only launches (ins_only) of a
+// spread-out round (spread: the block saw few repeated keys in its previous round) a single
+// insertion's Fat increments return the old values, which give the leader's slack.
 template <int D>
 __device__ __forceinline__ uint32_t phase1_global(const SketchRun& R, uint32_t* ctrl, const LaneWork<D>& L,
                                                   uint32_t ci, uint32_t cd, bool keep_own, bool ins_only,
-                                                  OwnCounts* own, unsigned long long keep,
+                                                  OwnCounts* own, bool spread, unsigned long long keep,
                                                   unsigned long long stream) {
     const SketchDesc& s = R.s;
     const int32_t net = (int32_t)ci - (int32_t)cd;
-    // A single insertion takes the returning increment (it is the common leader of spread-out
-    // streams, whose claimer can then skip the chunk-end Fat read); a merged group of a hot key
-    // keeps the non-returning one, so the leader never waits on a serialised hot counter.
+    // In a spread-out round a single insertion takes the returning increment: its claimer can
+    // then often skip the chunk-end Fat read.  In a skewed round the plain reduction is cheaper
+    // than the reads the slack saves (a returning atomic runs at two thirds of the reduction rate
+    // in L2); measured on the Zipf sweep, the returning form was 5-7 % faster at s <= 0.5 and
+    // 2-8 % slower at s >= 1.  A merged group of a hot key always keeps the non-returning form,
+    // so its leader never waits on a serialised hot counter.
     uint32_t Fl = 0u;  // 0: no slack
-    if (ins_only && ci == 1u) {
+    if (spread && ins_only && ci == 1u) {
         Fl = 0xFFFFFFFFu;
 #pragma unroll
         for (int i = 0; i < D; ++i) Fl = min(Fl, atom_add_pol(fat_ptr(s, i, L.h[i], L.f[i]), 1u, keep) + 1u);
@@ -435,7 +439,7 @@ __global__ void __launch_bounds__(kChunkBlock, 1) chunk_update_kernel(const __gr
             if (do_global) {
                 OwnCounts own;
                 const uint32_t slot =
-                    phase1_global<D>(R, a.ctrl, L, ci, cd, single, ins_only, &own, pol_keep, pol_stream);
+                    phase1_global<D>(R, a.ctrl, L, ci, cd, single, ins_only, &own, !use_merge, pol_keep, pol_stream);
                 if (slot != kNoSlot) {
                     if (single) {
                         my_slot = slot;
