@@ -78,3 +78,17 @@ def test_oracle_and_cuda_sources_share_nothing():
         if p.endswith((".cu", ".cuh", ".h", ".py")):
             txt = open(p).read()
             assert "import oracle" not in txt and "from oracle" not in txt and "sf_oracle" not in txt, p
+
+
+def test_one_at_a_time_workspace_only_where_the_graph_path_applies(lib_path):
+    """Chunk-1 sketches reserve the dependency-graph workspace when they are at least 1,024 wide
+    and w * z stays below 2^32 (the per-counter sort key has a spare value); others use the
+    window kernel and need only the control words."""
+    import paper_1701_04148_gb300 as sf
+    sf.load(lib_path)
+    _, _, graph = sf.required_bytes(sf.make_params(4, 4096, 16, 4, 1, 1))
+    _, _, narrow = sf.required_bytes(sf.make_params(4, 1000, 16, 4, 1, 1))
+    _, _, wide = sf.required_bytes(sf.make_params(1, 1 << 28, 16, 4, 1, 1))       # w * z = 2^32
+    _, _, just_under = sf.required_bytes(sf.make_params(1, (1 << 28) - 1, 16, 4, 1, 1))
+    assert narrow < 4096 and wide < 4096
+    assert graph > 30_000_000 and just_under > 10_000_000
