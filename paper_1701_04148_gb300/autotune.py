@@ -30,6 +30,13 @@ def chunk_sizes(ns, rounds: int, s_min: int = 2, s_max: int = SF_MAX_CHUNK):
     return [min(s_max, max(s_min, -(-int(n) // rounds))) for n in ns]
 
 
+def choose_rounds(results: dict, tolerance: float) -> int:
+    """The largest round count (smallest chunks, closest to one-at-a-time semantics) whose
+    throughput is within `tolerance` of the best candidate's."""
+    top = max(results.values())
+    return max(R for R, v in results.items() if v >= (1.0 - tolerance) * top)
+
+
 def shape_key(widths, ns, d: int, z: int, key_bytes: int) -> str:
     h = hashlib.sha256()
     h.update(json.dumps([list(map(int, widths)), list(map(int, ns)), d, z, key_bytes]).encode())
@@ -74,8 +81,7 @@ def tune(make_sketches, streams, ns, candidates=(16, 64, 256, 1024), tolerance: 
         for sk in sks:
             sk.close()
         del sks
-    top = max(results.values())
-    chosen = max(R for R, v in results.items() if v >= (1.0 - tolerance) * top)
+    chosen = choose_rounds(results, tolerance)
     chunks = chunk_sizes(ns, chosen)
     plan = {"rounds": chosen, "chunks": chunks, "graph": graph,
             "round_slots": sum((c + 31) // 32 * 32 for c in chunks),

@@ -79,3 +79,4 @@ def test_two_gloo_ranks_reproduce_the_single_rank_results():
         o.update(st.keys.numpy(), st.ops.numpy(), S=max(2, p["n"] // 8))
         want = int(np.uint64(o.A.astype(np.uint64).sum()) * np.uint64(1000003) + np.uint64(o.B.sum()))
         assert merged[i] == want
+
