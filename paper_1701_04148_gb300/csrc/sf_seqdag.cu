@@ -449,7 +449,7 @@ __global__ void __launch_bounds__(kDagWalkThreads, 1) dag_walk_kernel(SketchDesc
                                                                       uint32_t qcap, uint32_t* ctrl) {
     constexpr int P = WalkLanes<D>::P, G = WalkLanes<D>::G;
     constexpr uint32_t kHeadsPerIter = kDagWalkThreads / P;
-    extern __shared__ uint32_t s_dyn[];
+    extern __shared__ __align__(16) uint32_t s_dyn[];  // read and written as uint4 as well
     __shared__ uint32_t s_next[3];
     __shared__ uint4 s_warm[kDagWalkThreads];  // destinations of the L1-warming copies
     // dynamic shared memory: queues [2][qcap], pending-count nibbles, then the Slim (both copied
