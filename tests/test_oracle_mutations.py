@@ -10,6 +10,7 @@ import oracle
 import tests.test_oracle_pins as pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "sf_oracle.c")
+W_MAX_PIN = pins.W_MAX
 
 # (name, exact text in sf_oracle.c, replacement)
 MUTATIONS = [
@@ -27,6 +28,12 @@ MUTATIONS = [
      "M[(t - c0) * d + i] = *fat_at(B, w, z, i, h[t * d + i], f[t * d + i]);"),
     ("hash-h-from-low-bits", "*h = (uint32_t)((hi * (uint64_t)w) >> 32);", "*h = (uint32_t)((lo * (uint64_t)w) >> 32);"),
     ("hash-drops-second-word", "H = osf_mix64(H ^ x1);", "H = osf_mix64(H);"),
+    ("hash-reduce-mod", "*h = (uint32_t)((hi * (uint64_t)w) >> 32);", "*h = (uint32_t)(hi % w);"),
+    ("hash-f-reduce-mod", "*f = (uint32_t)((lo * (uint64_t)z) >> 32);", "*f = (uint32_t)(lo % z);"),
+    ("hash-swaps-words", "H = osf_mix64(H ^ x1);", "H = osf_mix64(osf_mix64(x1 ^ row_seed) ^ x0);"),
+    ("hash-tail-big-endian", "uint64_t x1 = load_le(key + 8, key_bytes - 8);",
+     "uint64_t x1 = 0; for (uint32_t b = 8; b < key_bytes; b++) x1 = (x1 << 8) | key[b];"),
+    ("hash-seed-added-not-xored", "uint64_t H = osf_mix64(x0 ^ row_seed);", "uint64_t H = osf_mix64(x0 + row_seed);"),
     ("mix-wrong-shift", "z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;", "z = (z ^ (z >> 28)) * 0x94D049BB133111EBULL;"),
     ("query-max", "if (v < m) m = v;\n        }\n        out[t] = m;", "if (m == UINT32_MAX || v > m) m = v;\n        }\n        out[t] = m;"),
     ("fat-transposed-index", "return &B[((uint64_t)i * w + j) * z + k];", "return &B[((uint64_t)i * z + k) * w + j];"),
@@ -48,6 +55,10 @@ def _pins_pass() -> bool:
         pins.test_mix64_inverts_with_the_published_constants,
         lambda: pins.test_power_of_two_reduction_takes_the_top_bits(4096, 16),
         pins.test_13_byte_keys_use_all_bytes,
+        lambda: pins.test_multiply_shift_partitions_the_32_bit_range_in_order(1000),
+        lambda: pins.test_multiply_shift_partitions_the_32_bit_range_in_order(W_MAX_PIN),
+        lambda: pins.test_short_keys_hash_as_one_mix_of_the_key_xor_the_row_seed(4),
+        lambda: pins.test_long_keys_fold_the_second_word_in_after_the_first_mix(13),
         lambda: pins.test_worked_example_sec32("seq"),
         lambda: pins.test_worked_example_sec32("chunk1"),
         lambda: pins.test_brute_force_tiny_streams_against_literal_transcription(

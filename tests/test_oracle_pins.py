@@ -97,6 +97,103 @@ def test_13_byte_keys_use_all_bytes():
         assert not np.array_equal(h0, h2), f"byte {b} does not reach the hash"
 
 
+W_MAX = 0xFFFFFFFF
+
+
+def _published_1234567():
+    g = json.load(open(os.path.join(GOLD, "splitmix64_vectors.json")))
+    v = next(v for v in g["vectors"] if v["seed"] == 1234567)
+    return [int(x) for x in v["outputs_dec"]]
+
+
+def _le(row) -> int:
+    return sum(int(b) << (8 * i) for i, b in enumerate(row))
+
+
+def _key8(x0: int) -> np.ndarray:
+    return np.array([[(x0 >> (8 * b)) & 0xFF for b in range(8)]], dtype=np.uint8)
+
+
+def _hash_read_back(keys: np.ndarray, seed: int, d: int):
+    """H_i of every key, read back from the oracle's indices at w = z = 2^32 - 1, where the
+    reduction returns max(x - 1, 0) of each 32-bit half (pinned by the partition test below).
+    Keys with a half in {0, 1} (ambiguous; probability 2^-31 each) come back as None."""
+    h, f = oracle.index_keys(keys, seed, d, W_MAX, W_MAX)
+    out = []
+    for t in range(len(keys)):
+        row = []
+        for i in range(d):
+            hi, lo = int(h[t, i]), int(f[t, i])
+            row.append(None if hi == 0 or lo == 0 else ((hi + 1) << 32) | (lo + 1))
+        out.append(row)
+    return out
+
+
+@pytest.mark.parametrize("w", [3, 7, 1000, 40_000, 65_537, 393_217, 2**31 - 1, W_MAX])
+def test_multiply_shift_partitions_the_32_bit_range_in_order(w):
+    """Multiply-shift range reduction (Lemire, ACM TOMACS 2019) splits [0, 2^32) into w contiguous
+    runs in increasing order; run j starts at ceil(j * 2^32 / w).  So the first input of run j maps
+    to j and the input just before it to j - 1.  Checked at run starts spread over the range, for
+    the bucket h (top half of H) and, with z = w, the slot f (low half), on 8-byte keys built to
+    hash to chosen H through the inverse of mix64 derived above and the row seed (the first
+    SplitMix64 output of the seed, pinned by the published vectors)."""
+    seed = 1234567
+    s0 = _published_1234567()[0]
+    rng = np.random.default_rng(w % 1000003)
+    js = sorted({1, 2, w // 3, w // 2, w - 1} | {int(x) for x in rng.integers(1, w, 40)})
+    targets, want = [], []
+    for j in js:
+        t = (j * 2**32 + w - 1) // w  # first input of run j
+        targets += [(t << 32) | t, ((t - 1) << 32) | (t - 1)]
+        want += [j, j - 1]
+    targets += [0, M64]
+    want += [0, w - 1]
+    keys = np.concatenate([_key8(_inverse_mix64(H) ^ s0) for H in targets])
+    h, f = oracle.index_keys(keys, seed, 1, w, w)
+    assert [int(x) for x in h[:, 0]] == want
+    assert [int(x) for x in f[:, 0]] == want
+
+
+@pytest.mark.parametrize("kb", [1, 3, 4, 8])
+def test_short_keys_hash_as_one_mix_of_the_key_xor_the_row_seed(kb):
+    """Keys of at most 8 bytes: H_i = mix64(x0 ^ s_i), x0 = the key bytes little-endian.  So
+    mix64^-1(H_i) ^ x0 is the same for every key and equals s_i, the i-th published SplitMix64
+    output of the sketch seed (five rows, five published outputs)."""
+    rng = np.random.default_rng(kb)
+    keys = rng.integers(0, 256, (300, kb), dtype=np.uint8)
+    pub = _published_1234567()
+    H = _hash_read_back(keys, 1234567, 5)
+    seen = 0
+    for t in range(len(keys)):
+        for i in range(5):
+            if H[t][i] is not None:
+                assert _inverse_mix64(H[t][i]) ^ _le(keys[t]) == pub[i], (t, i)
+                seen += 1
+    assert seen > 1400
+
+
+@pytest.mark.parametrize("kb", [9, 13, 15])
+def test_long_keys_fold_the_second_word_in_after_the_first_mix(kb):
+    """Keys of 9..15 bytes: H_i = mix64(mix64(x0 ^ s_i) ^ x1), x0 = bytes 0..7 and x1 = bytes 8..
+    little-endian.  So mix64^-1(H_i) ^ x1 does not depend on the tail and equals the hash of the
+    8-byte key x0 alone (both hashes read back from the oracle): a swapped or reordered word, a
+    big-endian tail or a dropped fold all break it."""
+    rng = np.random.default_rng(100 + kb)
+    d = 4
+    for _ in range(20):
+        head = rng.integers(0, 256, (1, 8), dtype=np.uint8)
+        tails = rng.integers(0, 256, (12, kb - 8), dtype=np.uint8)
+        tails[0] = 0
+        keys = np.concatenate([np.repeat(head, len(tails), 0), tails], axis=1)
+        H8 = _hash_read_back(head, 77, d)[0]
+        H = _hash_read_back(keys, 77, d)
+        for t in range(len(keys)):
+            for i in range(d):
+                if H[t][i] is None or H8[i] is None:
+                    continue
+                assert _inverse_mix64(H[t][i]) ^ _le(tails[t]) == H8[i], (t, i)
+
+
 # ---------------------------------------------------------------------------------------
 # the worked example of Sec. 3.2 (Fig. 3)
 # ---------------------------------------------------------------------------------------
