@@ -1,29 +1,38 @@
-"""Collector serving loop (sfc_*): answers equal sf_query_batch on the same Slim whether a request
-runs alone or inside a mix of concurrent requests; queries bind to the sketch version current at
-submit; uploads are admitted by the memory budget."""
+"""Collector serving loop (sfc_*): every answer equals the CPU oracle's point query (Sec. 3.1:
+the minimum of the key's d Slim counters) on the exact Slim contents the request is bound to,
+whether a request runs alone or inside a mix of concurrent requests; queries bind to the sketch
+version current at submit; uploads are admitted by the memory budget."""
 import threading
 
 import numpy as np
 import pytest
 
+import oracle
 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 
 
 def _make_slim(sf, w, seed, n_updates, key_bytes=4):
-    import torch
+    """A Slim exported from a GPU sketch fed a turnstile stream; returns (slim, header, distinct keys)."""
     sk = sf.Sketch(4, w, 16, key_bytes, seed, 512)
-    st, ids = wl.mixed_stream(n_updates, max(64, 4 * w), 1.0, 0.1, key_bytes, seed=seed, device="cuda")
-    sk.update(st.keys, st.ops)
+    if key_bytes == 13:
+        ins, dels, ids = wl.flows_with_deletes(n_updates, max(64, 4 * w), 1.0, 0.1, seed=seed, device="cuda")
+        sk.insert(ins)
+        sk.delete(dels)
+    else:
+        st, ids = wl.mixed_stream(n_updates, max(64, 4 * w), 1.0, 0.1, key_bytes, seed=seed, device="cuda")
+        sk.update(st.keys, st.ops)
     slim, hdr = sk.export_slim()
     sk.sync()
     return slim, hdr, ids
 
 
 def _reference(sf, slim, hdr, keys_np):
-    import torch
-    return sf.query(slim, hdr, torch.from_numpy(keys_np).cuda()).cpu().numpy().view(np.uint32)
+    """The oracle's query (Sec. 3.1) on these Slim counters, read back from the device."""
+    o = oracle.Sketch(hdr.d, hdr.w, 1, hdr.key_bytes, hdr.seed)
+    o.A[...] = slim.cpu().numpy().view(np.uint32).reshape(hdr.d, hdr.w)
+    return o.query(keys_np)
 
 
 def test_answers_alone_and_in_the_mix(sf):
@@ -106,3 +115,68 @@ def test_budget_admission(sf):
     bad = sf.SlimHeader(0xDEAD, 1, 4, 16384, 4, 1, 0)
     assert col.upload(3, s1, bad) == sf.SF_ERR_VERSION
     col.close()
+
+
+def test_answers_match_the_oracle_across_key_widths_and_replacement(sf):
+    """Mixed key widths (4, 8, 13 bytes) and widths that are not powers of two, requests of
+    1..16,384 keys from four threads, then a replace-in-place upload with requests bound to the
+    old and the new version in flight together: every answer equals the oracle's."""
+    rng = np.random.default_rng(17)
+    shapes = [(1024, 4), (3000, 8), (777, 13), (65536, 13), (12288, 4), (40000, 8)]
+    slims = [_make_slim(sf, w, 50 + i, 30_000, kb) for i, (w, kb) in enumerate(shapes)]
+    col = sf.Collector(budget_bytes=32 << 20, max_sketches=8, n_streams=4, max_batch_keys=1 << 15, max_wait_us=200)
+    for i, (slim, hdr, _) in enumerate(slims):
+        assert col.upload(i, slim, hdr) == sf.SF_OK
+
+    def request(i, n, version):
+        slim, hdr, ids = version
+        ids = ids.cpu().numpy()
+        present = ids[rng.integers(0, len(ids), n - n // 5)]
+        absent = rng.integers(0, 256, (n // 5, hdr.key_bytes), dtype=np.uint8)
+        keys = np.ascontiguousarray(np.concatenate([present, absent])[rng.permutation(n)])
+        return i, keys, _reference(sf, slim, hdr, keys)
+
+    reqs = [request(int(i), int(2 ** rng.uniform(0, 14)), slims[int(i)]) for i in rng.integers(0, len(slims), 240)]
+    outs = [None] * len(reqs)
+
+    def client(lo, hi):
+        tickets = []
+        for r in range(lo, hi):
+            i, keys, want = reqs[r]
+            outs[r] = np.zeros(len(want), np.uint32)
+            tickets.append(col.submit(i, keys, outs[r]))
+        for t in tickets:
+            assert col.wait(t) == sf.SF_OK
+
+    th = [threading.Thread(target=client, args=(k * 60, (k + 1) * 60)) for k in range(4)]
+    for x in th:
+        x.start()
+    for x in th:
+        x.join()
+    for r, (i, keys, want) in enumerate(reqs):
+        assert np.array_equal(outs[r], want), (r, shapes[i])
+
+    # replace sketch 3 (13-byte keys, w = 65,536) in place while requests on the old version run
+    newer = _make_slim(sf, 65536, 53, 90_000, 13)
+    old_reqs = [request(3, 4096, slims[3]) for _ in range(6)]
+    old_out = [np.zeros(4096, np.uint32) for _ in old_reqs]
+    old_t = [col.submit(3, k, o) for (_, k, _), o in zip(old_reqs, old_out)]
+    assert col.upload(3, newer[0], newer[1]) == sf.SF_OK
+    new_reqs = [request(3, 4096, newer) for _ in range(6)]
+    new_out = [np.zeros(4096, np.uint32) for _ in new_reqs]
+    new_t = [col.submit(3, k, o) for (_, k, _), o in zip(new_reqs, new_out)]
+    for t in old_t + new_t:
+        assert col.wait(t) == sf.SF_OK
+    for (_, _, want), got in zip(old_reqs + new_reqs, old_out + new_out):
+        assert np.array_equal(got, want)
+    col.close()
+
+
+def test_slim_queries_of_the_library_match_the_oracle(sf):
+    """sf_query_batch (the one-Slim query kernel) on the same Slims, for every key width."""
+    import torch
+    for i, (w, kb) in enumerate([(1000, 4), (5000, 8), (777, 13)]):
+        slim, hdr, ids = _make_slim(sf, w, 70 + i, 20_000, kb)
+        keys = ids.cpu().numpy()
+        got = sf.query(slim, hdr, torch.from_numpy(keys).cuda()).cpu().numpy().view(np.uint32)
+        assert np.array_equal(got, _reference(sf, slim, hdr, keys))
