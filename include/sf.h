@@ -358,11 +358,16 @@ sf_status sfc_destroy(sfc *c);
  *     different threads) race and corrupt each other's result: serialise them;
  *   - the call zeroes the array's control words and dictionary itself before its kernel runs;
  *   - the first call on a device looks up the array's device address (cudaGetSymbolAddress, with
- *     that device current); make that first call before capturing any CUDA stream.
+ *     that device current) and keeps it for the life of the process; make that first call before
+ *     capturing any CUDA stream.  The kept address does not survive cudaDeviceReset (which reloads
+ *     the library's device code): do not call this entry point on a device after resetting it.
  * No device memory is allocated: no cudaMalloc/cudaFree, no allocating library call.  If err_dev
- * (device, 4 bytes) is not NULL it receives the device-side error bits of this call (0 = none;
- * bit 0 = a Fat counter went negative, i.e. a delete of an item never inserted; bit 1 = a device
- * wait timed out).  Asynchronous on cuda_stream.
+ * (device, 4 bytes) is not NULL it receives the device-side error bits of this call: 0 = none;
+ * bit 0 (1) = a Fat counter went negative, i.e. a delete of an item never inserted; bit 1 (2) = a
+ * device wait timed out; bit 3 (8) = the per-chunk dictionary overflowed (cannot happen within
+ * the chunk limit above, since the dictionary holds four slots per update of a chunk); bit 2 (4)
+ * is the explicit-index key-id check, which this entry point never runs.  Any non-zero value
+ * means the counters are unspecified.  Asynchronous on cuda_stream.
  */
 #define SF_NOALLOC_MAX_CHUNK 16384u
 sf_status sf_update_batch_noalloc(const sf_params *p, uint32_t *fat_dev, uint32_t *slim_dev,

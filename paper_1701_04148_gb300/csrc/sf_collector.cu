@@ -108,13 +108,6 @@ struct Slot {  // one in-flight batch
     std::vector<std::shared_ptr<Request>> members;
 };
 
-uint64_t splitmix64_step(uint64_t* st) {
-    uint64_t z = (*st += 0x9E3779B97F4A7C15ull);
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-
 struct Layout {
     uint64_t keys_bytes, out_bytes, reqs_bytes, slot_bytes;
 };
@@ -341,8 +334,7 @@ sf_status sfc_upload(sfc* c, uint32_t sketch_id, const uint32_t* counters, const
     }
     v->bytes = bytes;
     v->hdr = *hdr;
-    uint64_t st = hdr->seed;
-    for (uint32_t i = 0; i < SF_MAX_D; ++i) v->rs[i] = i < hdr->d ? splitmix64_step(&st) : 0;
+    sfk::row_seeds(hdr->seed, hdr->d, v->rs);
     v->refs = 1;
     int cur = -1;
     cudaGetDevice(&cur);

@@ -34,6 +34,21 @@ inline sf_status sf_device_access(const void* p, const void** out) {
     }
 }
 
+// Range checks of sf_params shared by every entry point that takes one (sf_required_bytes,
+// sf_create, sf_update_batch_noalloc), so they accept the same parameters.
+inline bool sf_params_ok(const sf_params* p) {
+    if (!p) return false;
+    if (p->d < 1 || p->d > SF_MAX_D) return false;
+    if (p->w < 1 || p->w > 0x7FFFFFFFu) return false;
+    if (p->z < 1 || p->z > SF_MAX_Z) return false;
+    if (p->key_bytes < 1 || p->key_bytes > SF_MAX_KEY_BYTES) return false;
+    if (p->chunk < 1 || p->chunk > SF_MAX_CHUNK) return false;
+    if ((p->flags & ~(SF_FLAG_EXPLICIT_INDEX | SF_FLAG_SF4_DELETE)) != 0) return false;
+    if ((p->flags & SF_FLAG_EXPLICIT_INDEX) && p->key_bytes != 4) return false;
+    if ((uint64_t)p->d * p->w * p->z > (1ull << 40)) return false;
+    return true;
+}
+
 // Makes `dev` the current device for the scope of a call and restores the caller's device on
 // every return path.
 struct DeviceGuard {

@@ -28,6 +28,7 @@ constexpr uint32_t noalloc_capacity(uint32_t S) {
 static_assert(kNoAllocCtrlBytes + (uint64_t)noalloc_capacity(SF_NOALLOC_MAX_CHUNK) * sizeof(sfk::DictEntry) <=
                   kNoAllocScratchBytes,
               "the largest dictionary must fit the fixed scratch array");
+static_assert(sfk::kClaimLoad <= 8, "two halves of claim entries must fit the dictionary bytes of 4 S DictEntry slots");
 
 // The shared scratch: control words (error bits, barrier counter) then the key dictionary.
 static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
@@ -35,13 +36,6 @@ static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes]
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_scratch_dev[kMaxDevices] = {};  // device address of g_noalloc_scratch, per device
-
-uint64_t splitmix64_step(uint64_t* st) {
-    uint64_t z = (*st += 0x9E3779B97F4A7C15ull);
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
 
 // Device address of the scratch array on the current device.  Host code cannot pass the symbol
 // itself to a kernel: on the host it names a host-side stand-in, not device memory.
@@ -62,10 +56,9 @@ sf_status scratch_address(int dev, void** out) {
 extern "C" sf_status sf_update_batch_noalloc(const sf_params* p, uint32_t* fat_dev, uint32_t* slim_dev,
                                              const void* keys_dev, const int8_t* ops_dev, uint64_t n,
                                              uint32_t* err_dev, void* cuda_stream) {
-    if (!p || !fat_dev || !slim_dev) return SF_ERR_INVALID;
-    if (p->d < 1 || p->d > SF_MAX_D || p->w < 1 || p->w > 0x7FFFFFFFu || p->z < 1 || p->z > SF_MAX_Z ||
-        p->key_bytes < 1 || p->key_bytes > SF_MAX_KEY_BYTES || (p->flags & ~SF_FLAG_SF4_DELETE) != 0)
-        return SF_ERR_INVALID;
+    if (!fat_dev || !slim_dev) return SF_ERR_INVALID;
+    // the same parameter range as sf_create, minus the explicit-index mode, and chunks that fit the array
+    if (!sf_params_ok(p) || (p->flags & SF_FLAG_EXPLICIT_INDEX)) return SF_ERR_INVALID;
     if (p->chunk < 2 || p->chunk > SF_NOALLOC_MAX_CHUNK) return SF_ERR_INVALID;  // beyond the fixed scratch
     if (((uintptr_t)fat_dev & 15u) || ((uintptr_t)slim_dev & 15u)) return SF_ERR_INVALID;
     if (n == 0) return SF_OK;
@@ -102,8 +95,7 @@ extern "C" sf_status sf_update_batch_noalloc(const sf_params* p, uint32_t* fat_d
     one.s.w = p->w;
     one.s.z = p->z;
     one.s.key_bytes = p->key_bytes;
-    uint64_t seed = p->seed;
-    for (uint32_t i = 0; i < SF_MAX_D; ++i) one.s.rs[i] = i < p->d ? splitmix64_step(&seed) : 0;
+    sfk::row_seeds(p->seed, p->d, one.s.rs);
     one.s.idx_table = nullptr;
     one.s.n_ids = 0;
     one.s.sf4_delete = (p->flags & SF_FLAG_SF4_DELETE) ? 1u : 0u;
@@ -114,6 +106,7 @@ extern "C" sf_status sf_update_batch_noalloc(const sf_params* p, uint32_t* fat_d
     one.n = n;
     one.dict = (sfk::DictEntry*)((uint8_t*)scratch + kNoAllocCtrlBytes);
     one.cap_mask = cap - 1u;
+    one.claim_mask = sfk::claim_capacity(p->chunk) - 1u;
     // the barrier counter was just zeroed, so this launch starts from barrier 0
     if (sfk::launch_chunk_update(one, (uint32_t*)scratch, 0, sfk::chunk_claims_cap(sfk::round_up32(p->chunk), grid),
                                  grid, stream) != cudaSuccess)
