@@ -6,6 +6,7 @@ import pytest
 
 import oracle
 import workloads as wl
+from paper_1701_04148_gb300 import shard
 
 pytestmark = pytest.mark.gpu
 
@@ -70,6 +71,37 @@ def test_batch_matches_oracle_on_sampled_sketches(sf):
         o.update(st.keys.cpu().numpy(), st.ops.cpu().numpy(), S=_chunk_for(p, 17))
         assert np.array_equal(sks[i].fat.cpu().numpy().view(np.uint32).reshape(o.B.shape), o.B)
         assert np.array_equal(sks[i].slim.cpu().numpy().view(np.uint32).reshape(o.A.shape), o.A)
+
+
+@pytest.mark.parametrize("world,rank", [(2, 1), (3, 0)])
+def test_one_ranks_share_of_a_sharded_batch(sf, world, rank):
+    """The sharded many-sketch batch: one rank's share (shard.owned) of a batch of independent
+    sketches, updated by one batched launch on this GPU, equals one sf_update_batch call per
+    sketch, and sampled sketches of the share equal the oracle's chunked semantics."""
+    import torch
+    plan = _plan(30, seed=31, w_log2=(7.0, 11.0), n_log10=(2.5, 4.5))
+    mine = shard.owned([p["n"] for p in plan], world, rank)
+    assert 0 < len(mine) < len(plan)
+    share = [plan[i] for i in mine]
+    streams = _streams(share)
+    chunks = [_chunk_for(p, 9) for p in share]
+    bsk = [sf.Sketch(4, p["w"], 16, 4, p["seed"], c) for p, c in zip(share, chunks)]
+    psk = [sf.Sketch(4, p["w"], 16, 4, p["seed"], c) for p, c in zip(share, chunks)]
+    b = sf.Batch(len(share))
+    b.update([(sk, st.keys, st.ops) for sk, (st, _) in zip(bsk, streams)])
+    for sk, (st, _) in zip(psk, streams):
+        sk.update(st.keys, st.ops)
+    assert b.sync() == sf.SF_OK
+    for sk in psk:
+        sk.sync()
+    for i in range(len(share)):
+        assert torch.equal(bsk[i].fat, psk[i].fat) and torch.equal(bsk[i].slim, psk[i].slim), i
+    for i in sorted({0, len(share) // 2, len(share) - 1}):
+        p, (st, _) = share[i], streams[i]
+        o = oracle.Sketch(4, p["w"], 16, 4, p["seed"])
+        o.update(st.keys.cpu().numpy(), st.ops.cpu().numpy(), S=chunks[i])
+        assert np.array_equal(bsk[i].fat.cpu().numpy().view(np.uint32).reshape(o.B.shape), o.B), mine[i]
+        assert np.array_equal(bsk[i].slim.cpu().numpy().view(np.uint32).reshape(o.A.shape), o.A), mine[i]
 
 
 def test_batch_with_13_byte_keys_and_empty_items(sf):
