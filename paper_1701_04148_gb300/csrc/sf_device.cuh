@@ -77,6 +77,44 @@ __device__ __forceinline__ Key load_key(const uint8_t* __restrict__ keys, uint64
     return k;
 }
 
+// Per-warp load of up to 32 packed keys of a width other than 4 or 8 bytes: the warp reads the
+// 16-byte-aligned granules covering its keys with vector loads into shared memory (streaming,
+// evict-first: each key byte is read once), and reads a granule that straddles either end of the
+// caller's buffer byte by byte, so no byte outside [keys, keys + n*kb) is ever touched.
+__device__ __forceinline__ Key load_key_staged(const uint8_t* __restrict__ keys, uint64_t total_bytes,
+                                               uint64_t first, uint32_t nvalid, uint32_t kb, uint32_t lane,
+                                               uint4* stage) {
+    const uintptr_t kaddr = reinterpret_cast<uintptr_t>(keys);
+    const uint8_t* kal = reinterpret_cast<const uint8_t*>(kaddr & ~(uintptr_t)15);
+    const uint64_t lo = kaddr & 15u, hi = lo + total_bytes;  // valid bytes, relative to kal
+    const uint64_t b0 = lo + first * kb, b1 = b0 + (uint64_t)nvalid * kb;
+    const uint64_t g0 = b0 & ~15ull;
+    const uint32_t ngran = (uint32_t)((b1 - g0 + 15) >> 4);  // <= 31 for kb <= 15
+    if (lane < ngran) {
+        const uint64_t gb = g0 + 16ull * lane;
+        uint4 v;
+        if (gb >= lo && gb + 16 <= hi) {
+            v = __ldcs(reinterpret_cast<const uint4*>(kal + gb));
+        } else {
+            uint32_t w[4] = {0u, 0u, 0u, 0u};
+            for (uint32_t q = 0; q < 16; ++q)
+                if (gb + q >= lo && gb + q < hi) w[q >> 2] |= (uint32_t)__ldg(kal + gb + q) << (8 * (q & 3));
+            v = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        stage[lane] = v;
+    }
+    __syncwarp();
+    Key k{0ull, 0ull};
+    if (lane < nvalid) {
+        const uint8_t* sb = reinterpret_cast<const uint8_t*>(stage) + (b0 - g0) + (uint64_t)lane * kb;
+        const uint32_t n0 = kb < 8 ? kb : 8;
+        for (uint32_t b = 0; b < n0; ++b) k.x0 |= (uint64_t)sb[b] << (8 * b);
+        for (uint32_t b = 8; b < kb; ++b) k.x1 |= (uint64_t)sb[b] << (8 * (b - 8));
+    }
+    __syncwarp();
+    return k;
+}
+
 __device__ __forceinline__ uint64_t row_hash(const Key& k, uint32_t kb, uint64_t seed) {
     uint64_t H = mix64(k.x0 ^ seed);
     if (kb > 8) H = mix64(H ^ k.x1);
@@ -93,10 +131,11 @@ __device__ __forceinline__ uint32_t reduce_lo(uint64_t H, uint32_t range) {
 
 // Row indices of one key for D rows (D = 0: the runtime s.d rows, at most kMaxD).  Returns
 // false for a bad key id or table entry in explicit-index mode.  probe receives a well-mixed
-// 32-bit value for the dictionary; its low bits are independent of the top bits h/f use.
+// 64-bit value of the key for the dictionaries (row 0's hash, or a mix of the explicit id): its
+// low half picks a slot, its high half serves as a fingerprint.
 template <int D>
 __device__ __forceinline__ bool key_indices(const SketchDesc& s, const Key& k, uint32_t* h, uint32_t* f,
-                                            uint32_t* probe) {
+                                            uint64_t* probe) {
     constexpr int N = D ? D : kMaxD;
     if (s.idx_table) {
         const uint64_t id = k.x0;
@@ -110,7 +149,7 @@ __device__ __forceinline__ bool key_indices(const SketchDesc& s, const Key& k, u
                 f[i] = __ldg(row + 2 * i + 1);
                 ok &= (h[i] < s.w) && (f[i] < s.z);  // a bad table entry must not index out of bounds
             }
-        *probe = (uint32_t)mix64(id);
+        *probe = mix64(id);
         return ok;
     }
     uint64_t H0 = 0;
@@ -122,7 +161,7 @@ __device__ __forceinline__ bool key_indices(const SketchDesc& s, const Key& k, u
             h[i] = reduce_hi(H, s.w);
             f[i] = reduce_lo(H, s.z);
         }
-    *probe = (uint32_t)H0;
+    *probe = H0;
     return true;
 }
 

@@ -236,6 +236,27 @@ def test_key_widths(sf, kb):
         _queries_match(sf, g, o, pool)
 
 
+@pytest.mark.parametrize("kb", [3, 13, 15])
+def test_queries_with_staged_keys_unaligned_and_ragged(sf, kb):
+    """Point queries (Sec. 3.1) whose keys are staged warp-cooperatively (widths other than 4 and 8
+    bytes): key buffers starting at every offset 0..15 bytes past a 16-byte boundary, lengths that
+    leave a ragged last warp (1, 31, 33, 100,003 keys), answers equal the oracle's."""
+    import torch
+    gen = torch.Generator().manual_seed(200 + kb)
+    pool = torch.unique(torch.randint(0, 256, (4000, kb), dtype=torch.uint8, generator=gen), dim=0)
+    keys = pool[wl.sample_ranks(60_000, pool.shape[0], 1.0, gen)].contiguous()
+    g, o = _run_both(sf, 4, 3001, 16, kb, 5, 4096, [(keys, None)])
+    slim, hdr = g.export_slim()
+    q = pool[torch.randint(0, pool.shape[0], (100_003 + 16,), generator=gen)].contiguous()
+    flat = q.view(-1).cuda()
+    for off in range(16):
+        for n in (1, 31, 33, 100_003):
+            dev = flat[off: off + n * kb]          # starts off bytes past the allocation's alignment
+            want = o.query(q.view(-1)[off: off + n * kb].view(n, kb).numpy())
+            got = _np_u32(sf.query(slim, hdr, dev.view(n, kb)))
+            assert np.array_equal(got, want), (off, n)
+
+
 @pytest.mark.parametrize("d,w,z", [(1, 1, 1), (2, 5, 3), (5, 300, 7), (6, 777, 9), (7, 1500, 16), (8, 4096, 16),
                                    (4, 1 << 12, 64)])
 def test_shapes(sf, d, w, z):
