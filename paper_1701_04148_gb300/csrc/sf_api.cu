@@ -19,26 +19,6 @@ namespace {
 
 constexpr uint64_t kCtrlBytes = 256;
 
-uint64_t splitmix64_next(uint64_t* st) {
-    uint64_t z = (*st += 0x9E3779B97F4A7C15ull);
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-
-bool params_ok(const sf_params* p) {
-    if (!p) return false;
-    if (p->d < 1 || p->d > SF_MAX_D) return false;
-    if (p->w < 1 || p->w > 0x7FFFFFFFu) return false;
-    if (p->z < 1 || p->z > SF_MAX_Z) return false;
-    if (p->key_bytes < 1 || p->key_bytes > SF_MAX_KEY_BYTES) return false;
-    if (p->chunk < 1 || p->chunk > SF_MAX_CHUNK) return false;
-    if ((p->flags & ~(SF_FLAG_EXPLICIT_INDEX | SF_FLAG_SF4_DELETE)) != 0) return false;
-    if ((p->flags & SF_FLAG_EXPLICIT_INDEX) && p->key_bytes != 4) return false;
-    if ((uint64_t)p->d * p->w * p->z > (1ull << 40)) return false;
-    return true;
-}
-
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 sfk::SketchDesc desc_of(const sf_sketch* s) {
@@ -93,6 +73,7 @@ sf_status run_update(sf_sketch* s, const void* keys_in, const int8_t* ops_in, in
         one.flat_base = 0;
         one.dict = s->dict;
         one.cap_mask = s->cap - 1u;
+        one.claim_mask = sfk::claim_capacity(s->p.chunk) - 1u;
         e = sfk::launch_chunk_update(one, s->ctrl, s->bar_epoch, s->claims_cap, s->chunk_grid, s->stream);
         if (e == cudaSuccess) s->bar_epoch += 2ull * ((n + s->p.chunk - 1) / s->p.chunk);
     }
@@ -120,7 +101,7 @@ const char* sf_status_str(sf_status s) {
 
 sf_status sf_required_bytes(const sf_params* p, uint64_t* fat_bytes, uint64_t* slim_bytes,
                             uint64_t* scratch_bytes) {
-    if (!params_ok(p)) return SF_ERR_INVALID;
+    if (!sf_params_ok(p)) return SF_ERR_INVALID;
     if (fat_bytes) *fat_bytes = (uint64_t)p->d * p->w * p->z * 4ull;
     if (slim_bytes) *slim_bytes = (uint64_t)p->d * p->w * 4ull;
     if (scratch_bytes) {
@@ -136,7 +117,7 @@ sf_status sf_create(const sf_params* p, void* fat_dev, void* slim_dev, void* scr
                     void* cuda_stream, sf_sketch** out) {
     if (!out) return SF_ERR_INVALID;
     *out = nullptr;
-    if (!params_ok(p)) return SF_ERR_INVALID;
+    if (!sf_params_ok(p)) return SF_ERR_INVALID;
     if (!fat_dev || !slim_dev || !scratch_dev) return SF_ERR_INVALID;
     if (!aligned16(fat_dev) || !aligned16(slim_dev) || !aligned16(scratch_dev)) return SF_ERR_INVALID;
     sf_sketch* s = new (std::nothrow) sf_sketch();
@@ -150,8 +131,7 @@ sf_status sf_create(const sf_params* p, void* fat_dev, void* slim_dev, void* scr
     s->dict = (sfk::DictEntry*)((uint8_t*)scratch_dev + kCtrlBytes);
     s->cap = p->chunk > 1 ? sfk::dict_capacity(p->chunk) : 0;
     s->dag_ws = (p->chunk == 1 && sfk::dag_eligible(p->w, p->z)) ? (uint8_t*)scratch_dev + kCtrlBytes : nullptr;
-    uint64_t st = p->seed;
-    for (uint32_t i = 0; i < SF_MAX_D; ++i) s->rs[i] = i < p->d ? splitmix64_next(&st) : 0;
+    sfk::row_seeds(p->seed, p->d, s->rs);
     if (cudaGetDevice(&s->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&s->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device) != cudaSuccess) {
@@ -246,8 +226,7 @@ sf_status sf_query_batch(const sf_slim_view* v, const void* keys_dev, uint64_t n
     q.s.w = h.w;
     q.s.z = 0xFFFFFFFFu;  // a query never reads the Fat: f_i is not bounded by any z here
     q.s.key_bytes = h.key_bytes;
-    uint64_t st = h.seed;
-    for (uint32_t i = 0; i < SF_MAX_D; ++i) q.s.rs[i] = i < h.d ? splitmix64_next(&st) : 0;
+    sfk::row_seeds(h.seed, h.d, q.s.rs);
     q.s.idx_table = h.hash_id == SF_HASH_EXPLICIT ? v->index_table : nullptr;
     q.s.n_ids = v->n_index_keys;
     q.keys = (const uint8_t*)keys_dev;

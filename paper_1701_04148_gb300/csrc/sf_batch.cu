@@ -205,6 +205,7 @@ sf_status sf_batch_update(sf_batch* b, uint32_t n_items, const sf_batch_item* it
     uint64_t rounds_all = 0;
     for (const auto& gr : groups) {
         uint64_t flat = 0, rounds = 0;
+        uint32_t max_chunk = 0;
         bool may_ins = false, may_del = false;
         for (uint32_t row = gr.first; row < gr.second; ++row) {
             const uint32_t i = b->order[row];
@@ -227,7 +228,9 @@ sf_status sf_batch_update(sf_batch* b, uint32_t n_items, const sf_batch_item* it
             R.flat_base = flat;  // slots are numbered per launch group
             R.dict = s->dict;
             R.cap_mask = s->cap - 1u;
+            R.claim_mask = sfk::claim_capacity(R.S) - 1u;
             flat += sfk::round_up32(R.S);
+            max_chunk = R.S > max_chunk ? R.S : max_chunk;
             const uint64_t nr = (R.n + R.S - 1) / R.S;
             rounds = nr > rounds ? nr : rounds;
             if (R.n) {
@@ -249,6 +252,7 @@ sf_status sf_batch_update(sf_batch* b, uint32_t n_items, const sf_batch_item* it
         a.timeout_ns = sfk::kBarrierTimeoutNs;
         a.may_ins = may_ins;
         a.may_del = may_del;
+        a.max_chunk = max_chunk;
         // claim lists in shared memory when they fit, else in the batch scratch (launches run in order)
         a.claims_global =
             ((uint64_t)a.claims_cap * sizeof(uint2) > (uint64_t)sfk::kMaxClaimSmem) ? b->claims_dev : nullptr;

@@ -20,7 +20,7 @@ struct SketchRun {
     uint64_t flat_base;    // first slot of this sketch in every round's flat slot range (multiple of 32)
     DictEntry* dict;       // this sketch's chunk dictionary
     uint32_t cap_mask;     // its capacity - 1 (power of two)
-    uint32_t pad;
+    uint32_t claim_mask;   // entries - 1 of each half of the same bytes as 8-byte claim entries (single-iteration launches)
 };
 
 struct BatchArgs {
@@ -36,9 +36,29 @@ struct BatchArgs {
     int32_t may_ins;        // some update of the launch may be an insertion
     int32_t may_del;        // ... a deletion
     uint2* claims_global;   // per-block claim lists in global memory (claims_cap each), or nullptr: shared memory
+    uint32_t max_chunk;     // largest S of the launch's sketches
 };
 
 inline uint64_t round_up32(uint64_t x) { return (x + 31) & ~31ull; }
+
+// Row seeds of a sketch (the hash reading of sf.h): the first d outputs of SplitMix64 started at
+// `seed` (Steele, Lea, Flood, OOPSLA 2014) -- the state advances by the golden gamma and each
+// output is the state passed through the generator's finaliser.  Entries d..kMaxD-1 are 0.
+// Every host path that hands row seeds to a kernel (sketch handles, queries on an exported Slim,
+// collector uploads, the allocation-free update) derives them here, so they cannot drift apart.
+inline void row_seeds(uint64_t seed, uint32_t d, uint64_t* rs) {
+    uint64_t st = seed;
+    for (uint32_t i = 0; i < (uint32_t)kMaxD; ++i) {
+        if (i >= d) {
+            rs[i] = 0;
+            continue;
+        }
+        uint64_t z = (st += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        rs[i] = z ^ (z >> 31);
+    }
+}
 
 struct SeqArgs {
     SketchDesc s;
@@ -89,6 +109,25 @@ inline uint64_t claims_global_bytes(uint64_t max_round_slots) {
     return (max_round_slots + 1024ull * kChunkBlock) * 8ull;
 }
 int chunk_update_blocks_per_sm(uint32_t d);
+// A launch whose rounds give every worker lane at most one update, with chunks of at most
+// kClaimMaxChunk updates, runs the single-iteration kernel, which builds each chunk's dictionary one round ahead
+// (8-byte claim entries with 16-bit positions and counts).  Both kernels pass two grid barriers per
+// round.
+constexpr uint32_t kClaimMaxChunk = 65536;
+inline bool chunk_rounds_single(uint64_t flat_len, uint32_t max_chunk, int grid) {
+    // warp 0 of each block only passes the grid barriers, so the workers hold kChunkBlock - 32 slots
+    return flat_len <= (uint64_t)grid * (uint64_t)(kChunkBlock - 32) && max_chunk <= kClaimMaxChunk;
+}
+// Entries per half of the claim dictionary: a power of two >= kClaimLoad S (load factor <= 1/8).  Two
+// halves of 8-byte entries take 16 x that many bytes: no more than the DictEntry dictionary of a
+// sketch (32 B x pow2 >= 16 S) or of the allocation-free entry point (32 B x pow2 >= 4 S).
+constexpr uint32_t kClaimLoad = 8;
+inline uint32_t claim_capacity(uint32_t S) {
+    uint64_t need = (uint64_t)kClaimLoad * (uint64_t)S;
+    uint64_t cap = 64;
+    while (cap < need) cap <<= 1;
+    return (uint32_t)cap;
+}
 uint32_t chunk_claims_cap(uint64_t flat_len, int grid);
 // Single sketch: a batch of one.
 cudaError_t launch_chunk_update(const SketchRun& one, uint32_t* ctrl, uint64_t bar_base, uint32_t claims_cap,

@@ -29,44 +29,6 @@ namespace sfk {
 
 namespace {
 
-// Per-warp load of up to 32 packed keys of a width other than 4 or 8 bytes: the warp reads the
-// 16-byte-aligned granules covering its keys with vector loads into shared memory (streaming,
-// evict-first: each key byte is read once), and reads a granule that straddles either end of the
-// caller's buffer byte by byte, so no byte outside [keys, keys + n*kb) is ever touched.
-__device__ __forceinline__ Key load_key_staged(const uint8_t* __restrict__ keys, uint64_t total_bytes,
-                                               uint64_t first, uint32_t nvalid, uint32_t kb, uint32_t lane,
-                                               uint4* stage) {
-    const uintptr_t kaddr = reinterpret_cast<uintptr_t>(keys);
-    const uint8_t* kal = reinterpret_cast<const uint8_t*>(kaddr & ~(uintptr_t)15);
-    const uint64_t lo = kaddr & 15u, hi = lo + total_bytes;  // valid bytes, relative to kal
-    const uint64_t b0 = lo + first * kb, b1 = b0 + (uint64_t)nvalid * kb;
-    const uint64_t g0 = b0 & ~15ull;
-    const uint32_t ngran = (uint32_t)((b1 - g0 + 15) >> 4);  // <= 31 for kb <= 15
-    if (lane < ngran) {
-        const uint64_t gb = g0 + 16ull * lane;
-        uint4 v;
-        if (gb >= lo && gb + 16 <= hi) {
-            v = __ldcs(reinterpret_cast<const uint4*>(kal + gb));
-        } else {
-            uint32_t w[4] = {0u, 0u, 0u, 0u};
-            for (uint32_t q = 0; q < 16; ++q)
-                if (gb + q >= lo && gb + q < hi) w[q >> 2] |= (uint32_t)__ldg(kal + gb + q) << (8 * (q & 3));
-            v = make_uint4(w[0], w[1], w[2], w[3]);
-        }
-        stage[lane] = v;
-    }
-    __syncwarp();
-    Key k{0ull, 0ull};
-    if (lane < nvalid) {
-        const uint8_t* sb = reinterpret_cast<const uint8_t*>(stage) + (b0 - g0) + (uint64_t)lane * kb;
-        const uint32_t n0 = kb < 8 ? kb : 8;
-        for (uint32_t b = 0; b < n0; ++b) k.x0 |= (uint64_t)sb[b] << (8 * b);
-        for (uint32_t b = 8; b < kb; ++b) k.x1 |= (uint64_t)sb[b] << (8 * (b - 8));
-    }
-    __syncwarp();
-    return k;
-}
-
 constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
 
 __device__ __forceinline__ void ld_entry(const DictEntry* ep, unsigned long long& k0, unsigned long long& k1,
@@ -82,7 +44,7 @@ template <int D>
 struct LaneWork {
     Key k;
     int op;
-    uint32_t probe;
+    uint64_t probe;
     uint32_t h[D], f[D];
 };
 
@@ -200,7 +162,7 @@ __device__ __forceinline__ uint32_t phase1_global(const SketchRun& R, uint32_t* 
         for (int i = 0; i < D; ++i) av[i] = ld_cg_pol(slim_ptr(s, i, L.h[i]), keep);
     }
     const unsigned long long tag = L.k.x1 | kKeyTag;
-    uint32_t slot = L.probe & R.cap_mask;
+    uint32_t slot = (uint32_t)L.probe & R.cap_mask;
     bool found = false, claimed = false;
     for (uint32_t p = 0; p <= R.cap_mask; ++p) {
         unsigned long long ol, oh;
@@ -397,7 +359,7 @@ __global__ void __launch_bounds__(kChunkBlock, 1) chunk_update_kernel(const __gr
             uint32_t ci = wg.ci, cd = wg.cd;
             int role = 0;  // 1: owner of a merge slot, 2: merged into an owner, 3: unmerged
             uint32_t ms = 0;
-            const uint32_t ftag = (L.probe ^ (k * 0x9E3779B9u)) | 1u;
+            const uint32_t ftag = ((uint32_t)L.probe ^ (k * 0x9E3779B9u)) | 1u;
             if (use_merge) __syncthreads();
             if (use_merge && wg.leader) {
                 ms = (ftag >> 5) & (kMergeSlots - 1);
@@ -492,7 +454,8 @@ __global__ void __launch_bounds__(kChunkBlock, 1) chunk_update_kernel(const __gr
                 unsigned long long k0, k1, c01, c23;
                 ld_entry(ep, k0, k1, c01, c23);
                 const Key key{k0, k1 & ~kKeyTag};
-                uint32_t h[D], f[D], probe;
+                uint32_t h[D], f[D];
+                uint64_t probe;
                 key_indices<D>(R.s, key, h, f, &probe);
                 const uint32_t c_ins = (uint32_t)c01, ms = (uint32_t)(c23 >> 32);
                 const uint32_t F = c_ins ? fat_estimate<D>(R.s, h, f, c_ins, ins_only ? (ms >> 8) : 0u, pol_keep)
@@ -522,10 +485,437 @@ __global__ void __launch_bounds__(kChunkBlock, 1) chunk_update_kernel(const __gr
     }
 }
 
+// ---- single-iteration rounds: the dictionary is built one round ahead --------------------------
+//
+// When a round gives every lane at most one update (the chunks of one round fit 32 x the warps of
+// the grid) and no chunk exceeds 65,536 updates, each chunk's key dictionary is built one round
+// early.  While round r waits at its first grid barrier -- the L2 is idle then -- the warps group
+// the already loaded and hashed updates of chunk r+1 (warp match, block merge) and claim its
+// distinct keys in the other half of the dictionary (the halves alternate by chunk parity).  Phase 1
+// of chunk r+1 then only increments the Fat and reads the chunk-start Slim, and phase 2 collects
+// (and clears) what the key's other leaders added to its entry together with the Fat estimate.  The
+// key bytes of chunk r+2 are copied to shared memory (cp.async) during phase 2 of round r and hashed
+// while round r waits at its second barrier.  The semantics are those of the multi-iteration kernel
+// above; only where the dictionary and key work happens differs.
+//
+// Entry: 8 bytes, a claim word and the counts the key's other leaders add (inserts in the low 16
+// bits, deletes in the high 16: with at most 65,536 updates per chunk the others of a key hold at
+// most 65,535).  The claim word is 0x80000000 | (15-bit fingerprint << 16) | the position of the
+// claiming update in its chunk.  A leader whose CAS meets its own fingerprint compares its key with
+// the claimer's, read back from the (immutable) key stream at that position, so the dictionary is
+// exact whatever the fingerprints.
+struct alignas(8) ClaimEntry {
+    uint32_t claim;
+    uint32_t counts;
+};
+
+// One lane's update of a chunk after grouping and claiming.
+template <int D>
+struct Pending {
+    LaneWork<D> L;
+    uint32_t ci, cd;  // counts of the group this lane carries to global memory (0 if it carries none)
+    uint32_t slot;    // dictionary slot this lane claimed, kNoSlot if it claimed none
+    bool lead;        // this lane increments the Fat for its group
+};
+
+// What a claimer carries from phase 1 to phase 2 of its chunk.
+template <int D>
+struct Claimed {
+    uint32_t h[D], f[D];
+    uint32_t ci, cd, m, mask, slot;
+    bool on;
+};
+
+// The single-iteration kernel's block: warp 0 only passes the grid barriers; warps 1.. (the workers)
+// hold the updates.  The thread that arrives at a grid barrier stalls until every earlier access of
+// its block has reached L2 (the arrival is a release); keeping that thread out of the workers lets
+// them run the work that overlaps the barrier at once.
+constexpr int kWorkers = kChunkBlock - 32;
+
+__device__ __forceinline__ void workers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kWorkers) : "memory"); }
+
+// Grid barrier whose latency the workers fill with `work` (which must touch nothing that other blocks
+// access before the barrier and read after it): all threads pass __syncthreads -- the block's earlier
+// accesses are then ordered before the arrival -- thread 0 arrives and waits (bounded, as in
+// grid_barrier), warps 1.. run work(); the block goes on when both are done.
+template <class Work>
+__device__ __forceinline__ bool grid_barrier_overlapped(uint32_t* ctrl, unsigned long long target, uint64_t timeout_ns,
+                                                        Work&& work) {
+    __shared__ int s_ok_ov;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long* cnt = reinterpret_cast<unsigned long long*>(ctrl + kCtrlBarrier64);
+        red_release_gpu_add_u64(cnt, 1ull);
+        int ok = 1;
+        if (ld_acquire_gpu_u64(cnt) < target) {
+            const uint64_t t0 = globaltimer_ns();
+            while (ld_acquire_gpu_u64(cnt) < target) {
+                if (globaltimer_ns() - t0 > timeout_ns) {
+                    atomicOr(ctrl + kCtrlErr, kErrTimeout);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        s_ok_ov = ok;
+    } else if (threadIdx.x >= 32) {
+        work();
+    }
+    __syncthreads();
+    return s_ok_ov != 0;
+}
+
+// Group the updates of one chunk (warp match, then the block merge when enabled) and claim each
+// distinct key's dictionary entry (in `E`, the chunk's half of the sketch's dictionary, claim_mask + 1
+// entries).  Leaders that find their key already claimed add their counts to its entry.  Runs
+// between a grid barrier's arrival and its wait: it touches no counter, only the chunk's half.
+template <int D>
+__device__ __forceinline__ void group_and_claim(const SketchRun& R, uint32_t* ctrl, const LaneWork<D>& L, bool live,
+                                                uint32_t k, uint64_t base, uint32_t pos, ClaimEntry* E,
+                                                bool use_merge, MergeTable& mt, uint32_t* s_act, uint32_t* s_lead,
+                                                uint32_t lane, Pending<D>& P) {
+    P.L = L;
+    P.ci = P.cd = 0u;
+    P.slot = kNoSlot;
+    P.lead = false;
+    // every lane takes part (lanes without an update carry op 0 and join no group)
+    const WarpGroup wg = warp_group<D>(L, R.s.key_bytes, lane);
+    {
+        const unsigned act_b = __ballot_sync(kFull, live && L.op != 0);
+        const unsigned lead_b = __ballot_sync(kFull, wg.leader);
+        if (lane == 0 && act_b) {
+            atomicAdd(s_act, (uint32_t)__popc(act_b));
+            atomicAdd(s_lead, (uint32_t)__popc(lead_b));
+        }
+    }
+    bool do_global = wg.leader;
+    uint32_t ci = wg.ci, cd = wg.cd;
+    int role = 0;  // 1: owner of a merge slot, 2: merged into an owner, 3: unmerged
+    uint32_t ms = 0;
+    const uint32_t ftag = ((uint32_t)L.probe ^ (k * 0x9E3779B9u)) | 1u;
+    if (use_merge) workers_sync();
+    if (use_merge && wg.leader) {
+        ms = (ftag >> 5) & (kMergeSlots - 1);
+        role = 3;
+        for (int p = 0; p < kMergeSlots; ++p) {
+            const uint32_t old = atomicCAS(&mt.tag[ms], 0u, ftag);
+            if (old == 0u) {
+                role = 1;
+                mt.key[ms] = make_ulonglong2(L.k.x0, L.k.x1);
+                mt.run[ms] = k;
+                mt.ci[ms] = ci;
+                mt.cd[ms] = cd;
+                break;
+            }
+            if (old == ftag) {
+                role = 2;
+                break;
+            }
+            ms = (ms + 1) & (kMergeSlots - 1);
+        }
+    }
+    if (use_merge) workers_sync();
+    if (role == 2) {
+        const ulonglong2 o = mt.key[ms];
+        if (o.x == L.k.x0 && o.y == L.k.x1 && mt.run[ms] == k) {
+            atomicAdd(&mt.ci[ms], ci);
+            atomicAdd(&mt.cd[ms], cd);
+            do_global = false;
+        } else {
+            role = 3;
+        }
+    }
+    if (use_merge) workers_sync();
+    if (role == 1) {
+        ci = mt.ci[ms];
+        cd = mt.cd[ms];
+        mt.tag[ms] = 0u;  // free for the next grouping (after its worker barrier)
+    }
+    if (!do_global) return;
+    P.lead = true;
+    P.ci = ci;
+    P.cd = cd;
+    const uint32_t fp = 0x8000u | (uint32_t)(L.probe >> 49);  // 15 bits of the key's 64-bit probe
+    const uint32_t mine = (fp << 16) | pos;
+    const uint32_t kb = R.s.key_bytes;
+    uint32_t slot = (uint32_t)L.probe & R.claim_mask;
+    for (uint32_t p = 0; p <= R.claim_mask; ++p) {
+        const uint32_t old = atomicCAS(&E[slot].claim, 0u, mine);
+        if (old == 0u) {
+            P.slot = slot;
+            return;
+        }
+        if ((old >> 16) == fp) {
+            // same fingerprint: the claimer's key is the update at its stored position of this chunk
+            const Key o = load_key(R.keys, base + (old & 0xFFFFu), kb);
+            if (o.x0 == L.k.x0 && o.x1 == L.k.x1) {
+                atomicAdd(&E[slot].counts, ci | (cd << 16));
+                return;
+            }
+        }
+        slot = (slot + 1u) & R.claim_mask;
+    }
+    atomicOr(ctrl + kCtrlErr, kErrDictFull);
+    P.lead = false;  // dropped: reported as an error
+}
+
+// Asynchronous staging of one warp's packed bytes: the 16-byte granules covering elements
+// [first, first + nvalid) of kb bytes each of a caller buffer of `total` bytes.  Granules inside the
+// buffer go by cp.async (to be awaited by stage_take); a granule that straddles either end of the
+// buffer is read byte by byte at once, so no byte outside the buffer is touched.
+struct StageRange {
+    const uint8_t* kal;  // the buffer's address rounded down to 16 bytes
+    uint64_t lo, hi;     // valid bytes [lo, hi) relative to kal
+    uint64_t b0, g0;     // first wanted byte, first granule (relative to kal)
+    uint32_t ngran;
+};
+
+__device__ __forceinline__ StageRange stage_range(const uint8_t* p, uint64_t total, uint64_t first, uint32_t nvalid,
+                                                  uint32_t kb) {
+    StageRange g;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    g.kal = reinterpret_cast<const uint8_t*>(a & ~(uintptr_t)15);
+    g.lo = a & 15u;
+    g.hi = g.lo + total;
+    g.b0 = g.lo + first * kb;
+    g.g0 = g.b0 & ~15ull;
+    g.ngran = (uint32_t)((g.b0 + (uint64_t)nvalid * kb - g.g0 + 15) >> 4);  // <= 31 for kb <= 15
+    return g;
+}
+
+__device__ __forceinline__ void stage_issue(const StageRange& g, uint32_t lane, uint4* stage) {
+    if (lane < g.ngran) {
+        const uint64_t gb = g.g0 + 16ull * lane;
+        if (gb >= g.lo && gb + 16 <= g.hi) {
+            const uint32_t dst = (uint32_t)__cvta_generic_to_shared(stage + lane);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(g.kal + gb) : "memory");
+        } else {
+            uint32_t w[4] = {0u, 0u, 0u, 0u};
+            for (uint32_t q = 0; q < 16; ++q)
+                if (gb + q >= g.lo && gb + q < g.hi) w[q >> 2] |= (uint32_t)__ldg(g.kal + gb + q) << (8 * (q & 3));
+            stage[lane] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// Element `lane` (< nvalid) of a range staged by stage_issue, once the copies have landed.
+__device__ __forceinline__ Key stage_take(const StageRange& g, uint32_t nvalid, uint32_t kb, uint32_t lane,
+                                          const uint4* stage) {
+    Key k{0ull, 0ull};
+    if (lane < nvalid) {
+        const uint8_t* sb = reinterpret_cast<const uint8_t*>(stage) + (g.b0 - g.g0) + (uint64_t)lane * kb;
+        const uint32_t n0 = kb < 8 ? kb : 8;
+        for (uint32_t b = 0; b < n0; ++b) k.x0 |= (uint64_t)sb[b] << (8 * b);
+        for (uint32_t b = 8; b < kb; ++b) k.x1 |= (uint64_t)sb[b] << (8 * (b - 8));
+    }
+    return k;
+}
+
+template <int D>
+__global__ void __launch_bounds__(kChunkBlock, 1) chunk_single_kernel(const __grid_constant__ BatchArgs a) {
+    __shared__ uint4 s_stage[kChunkBlock / 32][32];
+    __shared__ uint4 s_ops[kChunkBlock / 32][4];
+    __shared__ MergeTable s_merge;
+    __shared__ uint32_t s_act, s_lead;
+    __shared__ int s_use_merge;
+    const SketchRun* runs = a.runs ? a.runs : &a.one;
+    const unsigned long long pol_keep = l2_policy_keep();
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t wib = threadIdx.x >> 5;  // warp 0: barrier warp; 1..: workers
+    // worker warps are numbered across blocks first, so a short round spreads over every SM
+    const uint64_t gwarp = wib ? (uint64_t)(wib - 1) * gridDim.x + blockIdx.x : 0ull;
+    uint4* stage = s_stage[wib];
+    uint4* stage_ops = s_ops[wib];
+    unsigned long long target = (a.bar_base + 1ull) * gridDim.x;
+    const uint64_t j = gwarp * 32 + lane;  // this lane's flat slot, the same in every round
+    const bool has_slot = wib != 0 && gwarp * 32 < a.flat_len;
+    const uint32_t k = has_slot ? find_run(runs, a.n_runs, gwarp * 32) : 0u;
+    const SketchRun& R = runs[k];
+    const uint64_t o = has_slot ? j - R.flat_base : 0;        // the lane's offset inside its chunk
+    const uint64_t wo = has_slot ? gwarp * 32 - R.flat_base : 0;  // the warp's
+    const uint32_t kb = R.s.key_bytes;
+    ClaimEntry* const dict2 = reinterpret_cast<ClaimEntry*>(R.dict);  // two halves of claim_mask + 1 entries
+
+    for (int i = threadIdx.x; i < kMergeSlots; i += blockDim.x) s_merge.tag[i] = 0u;
+    if (threadIdx.x == 0) {
+        s_act = 0u;
+        s_lead = 0u;
+        s_use_merge = 1;
+    }
+    __syncthreads();
+
+    // updates of the warp in chunk r: [base + wo, base + wo + nvalid); 0 when the warp has none there
+    auto warp_span = [&](uint64_t r, uint64_t* first) -> uint32_t {
+        const uint64_t base = r * (uint64_t)R.S;
+        if (!has_slot || wo >= R.S || base >= R.n) return 0u;
+        const uint64_t len = min((uint64_t)R.S, R.n - base);
+        if (wo >= len) return 0u;
+        *first = base + wo;
+        return (uint32_t)min((uint64_t)32, len - wo);
+    };
+    // start copying the warp's key (and operation) bytes of chunk r to shared memory
+    auto fetch_round = [&](uint64_t r) {
+        uint64_t first = 0;
+        const uint32_t nv = warp_span(r, &first);
+        if (nv == 0u) return;
+        stage_issue(stage_range(R.keys, R.n * kb, first, nv, kb), lane, stage);
+        if (R.ops) stage_issue(stage_range(reinterpret_cast<const uint8_t*>(R.ops), R.n, first, nv, 1u), lane, stage_ops);
+    };
+    // wait for those bytes, then decode and hash the lane's update; true when the lane has one
+    auto hash_round = [&](uint64_t r, LaneWork<D>& L) -> bool {
+        L.k = Key{0ull, 0ull};
+        L.op = 0;
+        L.probe = 0;
+        uint64_t first = 0;
+        const uint32_t nv = warp_span(r, &first);
+        if (nv == 0u) return false;
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncwarp();
+        L.k = stage_take(stage_range(R.keys, R.n * kb, first, nv, kb), nv, kb, lane, stage);
+        int op = R.op_const;
+        if (R.ops)
+            op = (int)(int8_t)stage_take(stage_range(reinterpret_cast<const uint8_t*>(R.ops), R.n, first, nv, 1u), nv,
+                                         1u, lane, stage_ops).x0;
+        __syncwarp();
+        if (lane < nv) {
+            L.op = op;
+            if (L.op != 0 && !key_indices<D>(R.s, L.k, L.h, L.f, &L.probe)) {
+                atomicOr(a.ctrl + kCtrlErr, kErrBadKey);
+                L.op = 0;
+            }
+        }
+        return lane < nv;
+    };
+    // group and claim chunk r (its dictionary half r & 1); every worker thread takes part
+    auto claim_round = [&](uint64_t r, const LaneWork<D>& L, bool live, Pending<D>& P) {
+        workers_sync();
+        if (threadIdx.x == 32) {
+            s_use_merge = (s_act > 0u) ? (16u * (s_act - s_lead) >= s_act) : s_use_merge;
+            s_act = 0u;
+            s_lead = 0u;
+        }
+        workers_sync();
+        group_and_claim<D>(R, a.ctrl, L, live, k, r * (uint64_t)R.S, (uint32_t)o,
+                           dict2 + (r & 1ull) * (R.claim_mask + 1ull), s_use_merge != 0, s_merge, &s_act, &s_lead,
+                           lane, P);
+    };
+
+    if (a.n_rounds == 0) return;
+    // chunk 0 is hashed and claimed before the first round; the counts other leaders add to its
+    // entries are read in its phase 2, behind round 0's first barrier
+    Pending<D> P;
+    P.lead = false;
+    P.slot = kNoSlot;
+    P.ci = P.cd = 0u;
+    LaneWork<D> N;
+    bool n_live = false;
+    if (wib != 0) {
+        fetch_round(0);
+        const bool live0 = hash_round(0, N);
+        if (a.n_rounds > 1) fetch_round(1);
+        claim_round(0, N, live0, P);
+        n_live = a.n_rounds > 1 ? hash_round(1, N) : false;
+    }
+
+    for (uint64_t r = 0; r < a.n_rounds; ++r) {
+        // ---- phase 1: Fat increments and the chunk-start Slim minimum -----------------------
+        Claimed<D> C;
+        C.on = P.slot != kNoSlot;
+        C.ci = P.ci;
+        C.cd = P.cd;
+        C.slot = P.slot;
+        C.m = C.mask = 0u;
+        if (P.lead) {
+            const SketchDesc& s = R.s;
+            const int32_t net = (int32_t)P.ci - (int32_t)P.cd;
+            if (net != 0) {
+#pragma unroll
+                for (int i = 0; i < D; ++i) red_add_pol(fat_ptr(s, i, P.L.h[i], P.L.f[i]), (uint32_t)net, pol_keep);
+            }
+            if (C.on) {
+                if (P.ci || a.may_ins) {
+                    uint32_t av[D];
+#pragma unroll
+                    for (int i = 0; i < D; ++i) av[i] = ld_cg_pol(slim_ptr(s, i, P.L.h[i]), pol_keep);
+                    uint32_t m = 0xFFFFFFFFu, ms = 0u;
+#pragma unroll
+                    for (int i = 0; i < D; ++i) m = min(m, av[i]);
+#pragma unroll
+                    for (int i = 0; i < D; ++i) ms |= (av[i] == m ? 1u : 0u) << i;
+                    C.m = m;
+                    C.mask = ms;
+                }
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    C.h[i] = P.L.h[i];
+                    C.f[i] = P.L.f[i];
+                }
+            }
+        }
+        // ---- barrier 1; meanwhile the workers group and claim chunk r + 1 -----------------
+        if (!grid_barrier_overlapped(a.ctrl, target, a.timeout_ns, [&] {
+                if (r + 1 < a.n_rounds) claim_round(r + 1, N, n_live, P);
+            }))
+            return;
+        target += gridDim.x;
+
+        // ---- phase 2: the key's other leaders' counts, the Fat estimate, Slim raises/clamps --
+        if (r + 2 < a.n_rounds) fetch_round(r + 2);
+        if (C.on) {
+            const SketchDesc& s = R.s;
+            ClaimEntry* e = dict2 + (r & 1ull) * (R.claim_mask + 1ull) + C.slot;
+            uint32_t cnt;
+            asm volatile("ld.global.cg.u32 %0, [%1];" : "=r"(cnt) : "l"(&e->counts));
+            uint32_t F = C.ci ? fat_min<D>(s, C.h, C.f, pol_keep) : 0xFFFFFFFFu;
+            asm volatile("st.global.cg.u64 [%0], %1;" ::"l"(e), "l"(0ull) : "memory");
+            const uint32_t c_ins = C.ci + (cnt & 0xFFFFu), c_del = C.cd + (cnt >> 16);
+            if (c_ins) {
+                if (!C.ci) F = fat_min<D>(s, C.h, C.f, pol_keep);  // only other leaders inserted
+                const uint64_t mc = (uint64_t)C.m + c_ins;
+                const uint32_t T = mc < (uint64_t)F ? (uint32_t)mc : F;
+                if (T > C.m) {
+#pragma unroll
+                    for (int i = 0; i < D; ++i)
+                        if (((C.mask >> i) & 1u) || c_ins > 1u) red_max_pol(slim_ptr(s, i, C.h[i]), T, pol_keep);
+                }
+            }
+            if (c_del) {
+                bool under = false;
+#pragma unroll
+                for (int i = 0; i < D; ++i)
+                    red_min_pol(slim_ptr(s, i, C.h[i]), bucket_bound_cg(s, i, C.h[i], C.f[i], &under, pol_keep, true),
+                                pol_keep);
+                if (under) atomicOr(a.ctrl + kCtrlErr, kErrUnderflow);
+            }
+        }
+
+        // ---- barrier 2; meanwhile the workers hash chunk r + 2 ----------------------------
+        if (!grid_barrier_overlapped(a.ctrl, target, a.timeout_ns, [&] {
+                if (r + 2 < a.n_rounds) n_live = hash_round(r + 2, N);
+            }))
+            return;
+        target += gridDim.x;
+    }
+}
+
 }  // namespace
 
 template <int D>
 static cudaError_t launch_batch_d(const BatchArgs& a, int grid, cudaStream_t st) {
+    if (chunk_rounds_single(a.flat_len, a.max_chunk, grid)) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)grid);
+        cfg.blockDim = dim3(kChunkBlock);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, chunk_single_kernel<D>, a);
+    }
     const size_t smem = a.claims_global ? 0 : (size_t)a.claims_cap * sizeof(uint2);
     cudaError_t e = cudaFuncSetAttribute(chunk_update_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
@@ -606,6 +996,7 @@ cudaError_t launch_chunk_update(const SketchRun& one, uint32_t* ctrl, uint64_t b
     a.timeout_ns = kBarrierTimeoutNs;
     a.may_ins = one.ops != nullptr || one.op_const > 0;
     a.may_del = one.ops != nullptr || one.op_const < 0;
+    a.max_chunk = one.S;
     return launch_batch_update(a, one.s.d, grid, st);
 }
 
