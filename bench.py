@@ -117,12 +117,12 @@ def measured_peaks():
 
 def l2_random_peaks(L, dev, stream):
     """Best of three rates (G ops/s) of sf_bench_random_access on a 64 MiB buffer: 32-bit loads
-    (kind 2) and the 1:1 reduce/load mix (kind 5)."""
+    (kind 2), RED.ADD (kind 0) and the 1:1 reduce/load mix (kind 5)."""
     import torch
     buf = torch.zeros(1 << 24, dtype=torch.int32, device=dev)
     h_st = int(stream.cuda_stream)
     out = {}
-    for name, kind in (("ld", 2), ("mix", 5)):
+    for name, kind in (("ld", 2), ("red", 0), ("mix", 5)):
         L.sf_bench_random_access(buf.data_ptr(), buf.numel(), 1 << 28, kind, 0, h_st)
         best = 0.0
         for _ in range(3):
@@ -234,11 +234,14 @@ def main():
                     help="all: the flows line with the batched and serving results embedded; profile: the small "
                          "fixed case the committed ncu summaries capture (two insert launches, the second profiled)")
     ap.add_argument("--profile-zipf", type=float, default=0.0)
+    ap.add_argument("--flows-mode", choices=["single", "batched"], default="single",
+                    help="flows step: one insert and one delete call per sketch (the single-sketch path, "
+                         "default) or one batched launch over the six sketches per call")
     ap.add_argument("--print-kernel-sha", action="store_true",
                     help="print the chunk kernel's source hash (the key of the committed traffic record) and exit")
     ap.add_argument("--profile-inserts", type=int, default=2_000_000)
     ap.add_argument("--batch-sketches", type=int, default=1024)
-    ap.add_argument("--serve-seconds", type=float, default=8.0)
+    ap.add_argument("--serve-seconds", type=float, default=6.0, help="serve: seconds of each open-loop load (70 %%, 90 %%)")
     ap.add_argument("--ool2-updates", type=int, default=1_000_000_000,
                     help="outofl2: stream length (10^9 in the measured configuration)")
     args = ap.parse_args()
@@ -336,13 +339,16 @@ def run_flows(args, ctx):
     answers = [torch.empty(N_FLOWS, dtype=torch.int32, device=dev) for _ in SWEEP]
     n_del = inputs[0][1].shape[0]
     ops_per_step = len(SWEEP) * (N_INS + n_del + N_FLOWS)
-    # the sketches of the sweep are independent: each update call is one batched launch over all
-    # of them (same per-sketch semantics as one call per sketch; see the batched-update tests)
+    # single mode: each sketch gets its own insert call and delete call (the single-sketch path);
+    # batched mode: the sketches of the sweep are independent, so each update call can also be one
+    # batched launch over all of them (same per-sketch semantics; see the batched-update tests)
+    batched = args.flows_mode == "batched"
     del_ops = [torch.full((n_del,), -1, dtype=torch.int8, device=dev) for _ in SWEEP]
     slots = len(SWEEP) * ((S + 31) // 32 * 32)
     b_ins = sf.Batch(len(SWEEP), graph=True, stream=stream, max_round_slots=slots)
     b_del = sf.Batch(len(SWEEP), graph=True, stream=stream, max_round_slots=slots)
-    launches_per_step = 2 + len(SWEEP)  # one batched insert and one batched delete launch, a query per sketch
+    # update launches plus a query per sketch
+    launches_per_step = (2 if batched else 2 * len(SWEEP)) + len(SWEEP)
 
     def step(evs=None, host=None, direct=False):
         """One step.  host: pinned host copies of the inputs (and answer buffers).  direct=False
@@ -364,10 +370,18 @@ def run_flows(args, ctx):
             sk.reset()
         if evs is not None:
             evs[0].record(stream)
-        b_ins.update([(sk, inp[0], None) for sk, inp in zip(sketches, src)])
+        if batched:
+            b_ins.update([(sk, inp[0], None) for sk, inp in zip(sketches, src)])
+        else:
+            for sk, inp in zip(sketches, src):
+                sk.insert(inp[0])
         if evs is not None:
             evs[1].record(stream)
-        b_del.update([(sk, inp[1], o) for sk, inp, o in zip(sketches, src, del_ops)])
+        if batched:
+            b_del.update([(sk, inp[1], o) for sk, inp, o in zip(sketches, src, del_ops)])
+        else:
+            for sk, inp in zip(sketches, src):
+                sk.delete(inp[1])
         if evs is not None:
             evs[2].record(stream)
         hdrs = [sketches[idx].export_slim(slims[idx])[1] for idx in range(len(SWEEP))]
@@ -427,21 +441,23 @@ def run_flows(args, ctx):
     best = l2_random_peaks(L, dev, stream)
     upd_timed = args.steps * len(SWEEP) * (N_INS + n_del)
     chunk_ms = t_ins + t_del
-    launches_chunk = args.steps * 2
+    launches_chunk = args.steps * (2 if batched else 2 * len(SWEEP))
     achieved = upd_timed * L2_OPS_PER_UPDATE / (chunk_ms / 1e3) / 1e9
     tr = traffic_record()
     traffic = None
-    if tr is not None and "flows_batched" in tr:
-        # DRAM bytes of this workload's own batched launches (one insert and one delete launch per
-        # step), averaged per launch like `achieved`
-        fb = tr["flows_batched"]
-        per = [fb[k]["dram_bytes_read"] + fb[k]["dram_bytes_write"] for k in ("insert_launch", "delete_launch")]
-        traffic = round(sum(per) / len(per))
-    roofline = {"bound": "l2", "kernel": "chunk_update_kernel", "achieved": round(achieved, 2),
+    rec_key = "flows_batched" if batched else "flows_single"
+    if tr is not None and rec_key in tr:
+        # DRAM bytes of this workload's own update launches (insert and delete launches of one step),
+        # averaged per launch like `achieved`
+        fb = tr[rec_key]
+        traffic = round(fb["dram_bytes_per_step"] / fb["launches_per_step"])
+    roofline = {"bound": "l2", "kernel": "chunk_update_kernel" if batched else "chunk_single_kernel",
+                "achieved": round(achieved, 2),
                 "peak": round(best["mix"], 2), "unit": "G random L2 ops/s", "frac": round(achieved / best["mix"], 4),
                 "traffic": traffic,
                 "peak_source": "measured in this run: random 32-bit ops on a 64 MiB L2-resident buffer, 1:1 "
                                "read-modify-write / load mix (the update's own mix)",
+                "peak_red_only": round(best["red"], 2), "frac_of_red_only": round(achieved / best["red"], 4),
                 "peak_load_only": round(best["ld"], 2), "frac_of_load_only": round(achieved / best["ld"], 4),
                 "ops_per_update": L2_OPS_PER_UPDATE,
                 "avg_launch_ms": round(chunk_ms / launches_chunk, 4)}
@@ -504,31 +520,64 @@ def run_flows(args, ctx):
         staged["transfer"] = "cudaMemcpyAsync of the keys to device buffers, kernels, copy of the answers back"
         e2e["staged"] = staged
 
-    # ---- the single-sketch path (one call per sketch), measured after the timed region ------
-    single = None
+    # ---- both update forms on the same inputs, measured after the timed region -------------
+    # single: one sf_insert_batch and one sf_delete_batch call per sketch (the single-sketch path);
+    # batched: one batched launch over the six sketches per call.  Best of two passes each.
+    single = batched_form = roofline_single = None
     if rank == 0:
-        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in SWEEP]
-        for idx, sk in enumerate(sketches):
-            sk.reset()
-            ev[idx][0].record(stream)
-            sk.insert(inputs[idx][0])
-            ev[idx][1].record(stream)
-            sk.delete(inputs[idx][1])
-            ev[idx][2].record(stream)
-        torch.cuda.synchronize()
+        def per_sketch_pass():
+            ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in SWEEP]
+            for idx, sk in enumerate(sketches):
+                sk.reset()
+                ev[idx][0].record(stream)
+                sk.insert(inputs[idx][0])
+                ev[idx][1].record(stream)
+                sk.delete(inputs[idx][1])
+                ev[idx][2].record(stream)
+            torch.cuda.synchronize()
+            return ev
+
+        def batched_pass():
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            for sk in sketches:
+                sk.reset()
+            ev[0].record(stream)
+            b_ins.update([(sk, inp[0], None) for sk, inp in zip(sketches, inputs)])
+            ev[1].record(stream)
+            b_del.update([(sk, inp[1], o) for sk, inp, o in zip(sketches, inputs, del_ops)])
+            ev[2].record(stream)
+            torch.cuda.synchronize()
+            return ev
+
+        passes = [per_sketch_pass() for _ in range(2)]
+        ev = min(passes, key=lambda e: sum(x[0].elapsed_time(x[2]) for x in e))
         ti = sum(e[0].elapsed_time(e[1]) for e in ev)
         td = sum(e[1].elapsed_time(e[2]) for e in ev)
+        ins_ops = len(SWEEP) * N_INS * L2_OPS_PER_UPDATE / (ti / 1e3) / 1e9
         single = {"insert_mops": round(len(SWEEP) * N_INS / ti / 1e3, 1),
                   "delete_mops": round(len(SWEEP) * n_del / td / 1e3, 1),
                   "insert_mops_per_zipf_s": {str(x): round(N_INS / ev[i][0].elapsed_time(ev[i][1]) / 1e3, 1)
                                              for i, x in enumerate(SWEEP)},
                   "roofline_frac": round(len(SWEEP) * (N_INS + n_del) * L2_OPS_PER_UPDATE / ((ti + td) / 1e3) / 1e9
                                          / best["mix"], 4),
-                  "insert_roofline_frac": round(len(SWEEP) * N_INS * L2_OPS_PER_UPDATE / (ti / 1e3) / 1e9
-                                                / best["mix"], 4),
-                  "insert_roofline_frac_of_load_only": round(len(SWEEP) * N_INS * L2_OPS_PER_UPDATE / (ti / 1e3)
-                                                             / 1e9 / best["ld"], 4),
                   "note": "one sf_insert_batch / sf_delete_batch call per sketch, same inputs"}
+        roofline_single = {
+            "path": "C2 insert path: one sf_insert_batch of 32,000,000 13-byte keys per sketch (chunk 65,536, "
+                    "d=4, w=2^18, z=16), the six Zipf exponents",
+            "kernel": "chunk_single_kernel", "bound": "l2", "unit": "G random L2 ops/s",
+            "ops_per_insert": L2_OPS_PER_UPDATE, "insert_G_per_s": round(len(SWEEP) * N_INS / ti / 1e6, 3),
+            "achieved": round(ins_ops, 2), "peak": round(best["mix"], 2), "frac": round(ins_ops / best["mix"], 4),
+            "peak_red_only": round(best["red"], 2), "frac_of_red_only": round(ins_ops / best["red"], 4),
+            "peak_load_only": round(best["ld"], 2), "frac_of_load_only": round(ins_ops / best["ld"], 4),
+            "peak_source": "measured in this run (sf_bench_random_access on 64 MiB): the 1:1 reduce/load mix, "
+                           "RED.ADD alone and loads alone"}
+        bpasses = [batched_pass() for _ in range(2)]
+        bev = min(bpasses, key=lambda e: e[0].elapsed_time(e[2]))
+        bi, bd = bev[0].elapsed_time(bev[1]), bev[1].elapsed_time(bev[2])
+        batched_form = {"insert_mops": round(len(SWEEP) * N_INS / bi / 1e3, 1),
+                        "delete_mops": round(len(SWEEP) * n_del / bd / 1e3, 1),
+                        "updates_vs_single": round((ti + td) / (bi + bd), 3),
+                        "note": "one batched launch over the six sketches per call (sf_batch_update), same inputs"}
         for sk in sketches:
             sk.sync()
 
@@ -570,12 +619,13 @@ def run_flows(args, ctx):
                        "chunk": S, "inserts_per_s": N_INS, "deletes_per_s": n_del, "flows": N_FLOWS,
                        "zipf_s": list(SWEEP), "l2": "inputs larger than L2 (2.7 GB of keys per step)",
                        "parallelism": f"replicas x{world}"},
-            "breakdown": {"mode": "the six sweep sketches updated by one batched launch per call",
+            "breakdown": {"mode": ("the six sweep sketches updated by one batched launch per call" if batched else
+                                   "one insert call and one delete call per sketch (the single-sketch path)"),
                           "insert_mops": round(args.steps * len(SWEEP) * N_INS / t_ins / 1e3, 1),
                           "delete_mops": round(args.steps * len(SWEEP) * n_del / t_del / 1e3, 1),
                           "export_query_mops": round(args.steps * len(SWEEP) * N_FLOWS / t_qry / 1e3, 1)},
-            "roofline": roofline, "roofline_hbm": roofline_hbm, "roofline_query": roofline_query,
-            "single_sketch": single,
+            "roofline": roofline, "roofline_single_sketch": roofline_single, "roofline_hbm": roofline_hbm,
+            "roofline_query": roofline_query, "single_sketch": single, "batched_form": batched_form,
             "cpu_baseline": cpu, "bit_exact_sample": exact, "e2e": e2e, "accuracy": accuracy,
             "gpu_launches": args.steps * launches_per_step, "clocks": clk,
         }
@@ -1127,11 +1177,12 @@ def run_batch(args, ctx):
     cache = os.path.join(ROOT, "paper_1701_04148_gb300", "_build", "autotune_cache.json")
     key = autotune.shape_key(ws, ns, 4, 16, 4) + "-" + torch.cuda.get_device_name(dev).replace(" ", "_")
     t1 = time.time()
-    tuned = autotune.tune(make, streams, ns, candidates=(32, 64, 256, 1024), cache_path=cache, cache_key=key)
+    tuned = autotune.tune(make, streams, ns, cache_path=cache, cache_key=key, widths=ws, d=4, z=16)
     tune_s = time.time() - t1
     chunks = tuned["chunks"]
     bsk, psk = make(chunks), make(chunks)
-    batch = sf.Batch(len(bsk), graph=True, stream=stream, max_round_slots=tuned["round_slots"])
+    batch = sf.Batch(len(bsk), graph=True, stream=stream, max_round_slots=tuned["round_slots"],
+                     block_threads=tuned["block_threads"], group_bytes=tuned["group_bytes"])
     items = [(sk, k, o) for sk, (k, o) in zip(bsk, streams)]
 
     def batched_step():
@@ -1175,7 +1226,12 @@ def run_batch(args, ctx):
            "updates_per_step": total_all, "value": round(total_all / (tb / 1e3) / 1e6, 2), "unit": "M updates/s",
            "plain_value": round(total_all / (tp / 1e3) / 1e6, 2), "batched_vs_plain_speedup": round(tp / tb, 3),
            "ms_per_step_batched": round(tb, 3), "ms_per_step_plain": round(tp, 3), "rounds": tuned["rounds"],
-           "autotune_updates_per_s": tuned["trials"], "graph": info, "status": st_b,
+           "block_threads": tuned["block_threads"], "group_bytes": tuned["group_bytes"],
+           "autotune_updates_per_s": tuned["trials"], "autotune_block": tuned["trials_block"],
+           "autotune_group": tuned["trials_group"], "autotune_best_rounds_bracketed": tuned["best_rounds_bracketed"],
+           "autotune_rounds_skipped_for_memory": tuned["rounds_skipped_for_memory"],
+           "sketch_bytes": autotune.sketch_bytes(ws, chunks, 4, 16),
+           "graph": info, "status": st_b,
            "launch_groups": {"groups": info["groups_last"], "group_bytes": info["group_bytes"],
                              "rule": "sketches whose counters fit the budget packed into L2-sized launch "
                                      "groups, larger ones share one launch"},
@@ -1197,8 +1253,8 @@ def run_batch(args, ctx):
 def run_serve(args, ctx):
     """Collector serving loop: 4,096 resident Slims (widths log-uniform 2^10..2^18, d=4) filled from
     u32 Zipf streams, a 40 GB admission budget, open-loop Poisson query batches of round(2^U(0,16))
-    keys (80 % Zipf-hot present, 20 % uniform absent) at ~70 % of the measured capacity, with
-    replace-in-place uploads during the run; then a 1 GB budget where admission binds; and the plain
+    keys (80 % Zipf-hot present, 20 % uniform absent) at ~70 % and ~90 % of the measured capacity,
+    with replace-in-place uploads during the runs; then a 1 GB budget where admission binds; and the plain
     path (one sf_query_batch per request, copies included) for comparison."""
     import threading
 
@@ -1274,40 +1330,48 @@ def run_serve(args, ctx):
     cap = col.stats(reset=True)
     cap_keys_s = cap["keys"] / dt
 
-    # open loop at ~70 % of capacity, Poisson arrivals, replace-in-place uploads at 20/s
-    rate = 0.7 * cap_keys_s / mean_keys
-    gaps = wl.poisson_gaps(int(rate * args.serve_seconds) + 1, rate, torch.Generator().manual_seed(5)).numpy()
-    arrivals = np.cumsum(gaps)
-    stop = threading.Event()
-    uploads = [0]
+    # open loop at ~70 % and ~90 % of capacity: Poisson arrivals, replace-in-place uploads at 20/s
+    def open_loop(frac, seconds, seed):
+        rate = frac * cap_keys_s / mean_keys
+        gaps = wl.poisson_gaps(int(rate * seconds) + 1, rate, torch.Generator().manual_seed(seed)).numpy()
+        arrivals = np.cumsum(gaps)
+        stop = threading.Event()
+        uploads = [0]
 
-    def uploader():
-        r2 = np.random.default_rng(99)
-        while not stop.is_set():
-            k = int(r2.integers(n_sk))
-            if col.upload(k, slims[k], hdrs[k]) == sf.SF_OK:
-                uploads[0] += 1
-            time.sleep(0.05)
+        def uploader():
+            r2 = np.random.default_rng(99 + seed)
+            while not stop.is_set():
+                k = int(r2.integers(n_sk))
+                if col.upload(k, slims[k], hdrs[k]) == sf.SF_OK:
+                    uploads[0] += 1
+                time.sleep(0.05)
 
-    th = threading.Thread(target=uploader)
-    th.start()
-    tickets = []
-    t_start = time.perf_counter()
-    for q, at in enumerate(arrivals):
-        while True:
-            now = time.perf_counter() - t_start
-            if now >= at:
-                break
-            if at - now > 2e-4:
-                time.sleep((at - now) - 1e-4)
-        k, keys, out = pool[q % len(pool)]
-        tickets.append(col.submit(k, keys, out))
-    for x in tickets:
-        col.wait(x)
-    stop.set()
-    th.join()
-    open_stats = col.stats(reset=True)
-    offered = len(arrivals) / (time.perf_counter() - t_start)
+        th = threading.Thread(target=uploader)
+        th.start()
+        tickets = []
+        t_start = time.perf_counter()
+        for q, at in enumerate(arrivals):
+            while True:
+                now = time.perf_counter() - t_start
+                if now >= at:
+                    break
+                if at - now > 2e-4:
+                    time.sleep((at - now) - 1e-4)
+            k, keys, out = pool[q % len(pool)]
+            tickets.append(col.submit(k, keys, out))
+        for x in tickets:
+            col.wait(x)
+        stop.set()
+        th.join()
+        st_ = col.stats(reset=True)
+        return {"load_fraction_of_capacity": frac, "p50_ms": round(st_["p50_us"] / 1e3, 4),
+                "p99_ms": round(st_["p99_us"] / 1e3, 4), "mean_ms": round(st_["mean_us"] / 1e3, 4),
+                "queries_per_s": round(st_["qps"], 1),
+                "offered_requests_per_s": round(len(arrivals) / (time.perf_counter() - t_start), 1),
+                "requests": int(st_["requests"]), "uploads_during_run": uploads[0]}
+
+    loads = [open_loop(0.7, args.serve_seconds, 5), open_loop(0.9, args.serve_seconds, 6)]
+    open70 = loads[0]
 
     # check a sample of answers against sf_query_batch (alone) on the same Slims
     exact = True
@@ -1335,12 +1399,12 @@ def run_serve(args, ctx):
     tst = tight.stats()
     tight.close()
     return {"workload": "collector-serving", "sketches": n_sk, "slim_bytes": slim_bytes,
-            "p50_ms": round(open_stats["p50_us"] / 1e3, 4), "p99_ms": round(open_stats["p99_us"] / 1e3, 4),
-            "mean_ms": round(open_stats["mean_us"] / 1e3, 4), "queries_per_s": round(open_stats["qps"], 1),
-            "offered_requests_per_s": round(offered, 1), "load_fraction_of_capacity": 0.7,
+            "p50_ms": open70["p50_ms"], "p99_ms": open70["p99_ms"], "mean_ms": open70["mean_ms"],
+            "queries_per_s": open70["queries_per_s"], "offered_requests_per_s": open70["offered_requests_per_s"],
+            "load_fraction_of_capacity": 0.7, "load_sweep": loads,
             "capacity_keys_per_s": round(cap_keys_s, 1), "capacity_p99_ms": round(cap["p99_us"] / 1e3, 4),
             "plain_keys_per_s": round(plain_keys_s, 1), "served_vs_plain_speedup": round(cap_keys_s / plain_keys_s, 2),
-            "uploads_during_run": uploads[0], "mean_keys_per_request": round(mean_keys, 1),
+            "uploads_during_run": open70["uploads_during_run"], "mean_keys_per_request": round(mean_keys, 1),
             "answers_equal_alone": exact, "budget_1GB": {"admitted": admitted, "rejected": tst["rejected_uploads"]},
             "budget_40GB_admitted": n_sk, "build_s": round(build_s, 1)}
 

@@ -257,6 +257,15 @@ sf_status sf_batch_sync(sf_batch *b);
  * on the grouping (each sketch's updates are the same); only the speed does.
  */
 sf_status sf_batch_set_group_bytes(sf_batch *b, uint64_t bytes);
+/*
+ * Launch shape of sf_batch_update (no counterpart in the paper): `threads` per block, 512 (the
+ * default), 256 or 128, with 512 / threads co-resident blocks per SM, so each shape runs the same
+ * number of threads; smaller blocks mean finer-grained block merges and grid-barrier arrivals.
+ * Results do not depend on the shape, only the speed does (the batch autotuner picks it).
+ * SF_ERR_INVALID for another value.
+ */
+sf_status sf_batch_set_block_threads(sf_batch *b, uint32_t threads);
+
 /* The group budget and the number of launches the last sf_batch_update used. */
 sf_status sf_batch_groups(const sf_batch *b, uint32_t *groups_last, uint64_t *group_bytes);
 

@@ -101,6 +101,7 @@ _SIGS = {
     "sf_batch_update": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]),
     "sf_batch_sync": (ctypes.c_int32, [ctypes.c_void_p]),
     "sf_batch_set_group_bytes": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64]),
+    "sf_batch_set_block_threads": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint32]),
     "sf_batch_groups": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32),
                                          ctypes.POINTER(ctypes.c_uint64)]),
     "sf_batch_info": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32),
@@ -331,9 +332,10 @@ class Batch:
     """Many sketches updated by one persistent launch (sf_batch_*), CUDA graph replay by default."""
 
     def __init__(self, max_sketches: int, graph: bool = True, stream=None, device=None,
-                 max_round_slots: int = 1 << 22, group_bytes: int | None = None):
+                 max_round_slots: int = 1 << 22, group_bytes: int | None = None, block_threads: int | None = None):
         """group_bytes: counter footprint per launch group (None: the library default, 3/4 of L2;
-        0: every sketch of a call in one launch)."""
+        0: every sketch of a call in one launch).  block_threads: threads per block of the launches,
+        512 (default), 256 or 128."""
         torch = _torch()
         L = load()
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
@@ -349,6 +351,8 @@ class Batch:
         self._keep = None
         if group_bytes is not None:
             check(L.sf_batch_set_group_bytes(self.handle, int(group_bytes)), "sf_batch_set_group_bytes")
+        if block_threads is not None:
+            check(L.sf_batch_set_block_threads(self.handle, int(block_threads)), "sf_batch_set_block_threads")
 
     def update(self, items):
         """items: list of (Sketch, keys tensor, ops tensor or None)."""

@@ -1,20 +1,23 @@
 """Autotuner for the batched many-sketch update.
 
-What it tunes:
-- The round count R of a batch. Every sketch k gets the chunk size `S_k = ceil(N_k / R)`
-  (at least 2, at most SF_MAX_CHUNK), so every stream spreads over about R rounds of one launch.
-- Whether the launch is replayed from a CUDA graph.
+What it tunes, in three stages on the real batch:
+1. The round count R. Every sketch k gets the chunk size `S_k = ceil(N_k / R)` (at least 2, at most
+   SF_MAX_CHUNK), so every stream spreads over about R rounds of one launch. Chunk size is part of the
+   semantics: it is recorded in the plan and in each sketch's parameters, and the CPU oracle takes it
+   as an input. The largest R (smallest chunks, closest to one-at-a-time semantics) whose throughput
+   is within `tolerance` of the best candidate is kept.  Candidates run from 8 to 1024.  Throughput
+   grows with the chunk size (fewer rounds, fewer grid barriers), so the fastest candidate is the
+   smallest R that fits: a candidate whose sketches would need more device memory than `mem_budget`
+   (each chunk slot reserves its dictionary entries in the sketch's scratch) is skipped, and the plan
+   records whether the fastest tried R lay inside the range or at its end.
+2. The launch shape at that R: threads per block (512, 256 or 128, with 512 / threads blocks per SM,
+   so every shape runs the same number of threads). The fastest shape is kept; shapes are not
+   semantic.
+3. The launch-group budget at that R and shape: the default (3/4 of L2), half of L2, or one launch
+   for every sketch. The fastest is kept; grouping is not semantic either.
 
-Chunk size is part of the semantics: it is recorded in the plan and in each sketch's
-parameters, and the CPU oracle takes it as an input. The block shape is fixed by the kernel's
-register budget (512 threads, one block per SM); the tile is a warp-iteration of 32 updates.
-
-How it chooses:
-- It times each candidate on the real batch: one warm-up call, then `trials` calls. Sketches
-  are re-initialised between calls.
-- It keeps the largest R (smallest chunks, closest to one-at-a-time semantics) whose throughput
-  is within `tolerance` of the best candidate.
-- The plan is cached as JSON, keyed by a hash of the batch shape.
+How it times: one warm-up call, then `trials` calls per candidate, sketches re-initialised between
+calls. The plan is cached as JSON, keyed by a hash of the batch shape.
 """
 from __future__ import annotations
 
@@ -24,6 +27,8 @@ import os
 import time
 
 SF_MAX_CHUNK = 1 << 20
+ROUND_CANDIDATES = (8, 16, 32, 64, 256, 1024)
+BLOCK_CANDIDATES = (512, 256, 128)
 
 
 def chunk_sizes(ns, rounds: int, s_min: int = 2, s_max: int = SF_MAX_CHUNK):
@@ -37,16 +42,63 @@ def choose_rounds(results: dict, tolerance: float) -> int:
     return max(R for R, v in results.items() if v >= (1.0 - tolerance) * top)
 
 
+def choose_fastest(results: dict, order):
+    """The fastest candidate of a non-semantic choice; on a tie the one listed first in `order`."""
+    top = max(results.values())
+    return next(c for c in order if c in results and results[c] == top)
+
+
+def bracketed(results: dict) -> bool:
+    """True when the fastest round count is not at either end of the candidates tried."""
+    best = max(results, key=lambda R: results[R])
+    return min(results) < best < max(results)
+
+
 def shape_key(widths, ns, d: int, z: int, key_bytes: int) -> str:
     h = hashlib.sha256()
     h.update(json.dumps([list(map(int, widths)), list(map(int, ns)), d, z, key_bytes]).encode())
     return h.hexdigest()[:24]
 
 
-def tune(make_sketches, streams, ns, candidates=(16, 64, 256, 1024), tolerance: float = 0.05, trials: int = 1,
-         graph: bool = True, cache_path: str | None = None, cache_key: str | None = None, log=None):
+def _time_batch(sf, torch, sks, streams, graph, slots, trials, block=None, group=None):
+    b = sf.Batch(len(sks), graph=graph, max_round_slots=slots, block_threads=block, group_bytes=group)
+    items = [(sk, k, o) for sk, (k, o) in zip(sks, streams)]
+    for sk in sks:
+        sk.reset()
+    b.update(items)
+    b.sync()
+    best = float("inf")
+    for _ in range(trials):
+        for sk in sks:
+            sk.reset()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.update(items)
+        b.sync()
+        best = min(best, time.perf_counter() - t0)
+    b.close()
+    return best
+
+
+def sketch_bytes(widths, chunks, d: int, z: int) -> int:
+    """Device bytes of the batch's sketches (Fat, Slim and the chunk dictionary of sf_required_bytes)."""
+    import paper_1701_04148_gb300 as sf
+    total = 0
+    for w, c in zip(widths, chunks):
+        fb, sb, xb = sf.required_bytes(sf.make_params(d, int(w), z, 4, 0, int(c)))
+        total += fb + sb + xb
+    return total
+
+
+def tune(make_sketches, streams, ns, candidates=ROUND_CANDIDATES, blocks=BLOCK_CANDIDATES, group_budgets=None,
+         tolerance: float = 0.05, trials: int = 1, graph: bool = True, cache_path: str | None = None,
+         cache_key: str | None = None, log=None, widths=None, d: int = 4, z: int = 16, mem_budget: int | None = None):
     """make_sketches(chunks) -> list of Sketch; streams: list of (keys, ops) device tensors.
-    Returns {"rounds": R, "chunks": [S_k], "graph": bool, "trials": {R: updates/s}}."""
+    group_budgets: launch-group budgets to try (None entries: the library default); by default the
+    default, half of L2 and 0 (one launch).  widths (with d, z): the sketches' widths, to skip round
+    counts whose sketches exceed mem_budget bytes (default: a quarter of the device's free memory, so
+    that a caller can hold a second set of the tuned sketches beside its inputs).
+    Returns {"rounds", "chunks", "block_threads", "group_bytes", "graph", "trials", ...}."""
     import torch
 
     import paper_1701_04148_gb300 as sf
@@ -55,37 +107,57 @@ def tune(make_sketches, streams, ns, candidates=(16, 64, 256, 1024), tolerance: 
         cache = json.load(open(cache_path))
         if cache_key in cache:
             return cache[cache_key]
+    if group_budgets is None:
+        l2 = torch.cuda.get_device_properties(torch.cuda.current_device()).L2_cache_size
+        group_budgets = (None, l2 // 2, 0)
     total = sum(int(n) for n in ns)
-    results = {}
+    say = log or (lambda m: None)
+    if mem_budget is None:
+        mem_budget = torch.cuda.mem_get_info()[0] // 4
+    skipped = []
+
+    # stage 1: round count at the default shape and grouping
+    by_rounds = {}
     for R in candidates:
         chunks = chunk_sizes(ns, R)
+        if widths is not None and sketch_bytes(widths, chunks, d, z) > mem_budget:
+            skipped.append(R)
+            say(f"autotune: R={R} skipped (sketches above the memory budget)")
+            continue
         slots = sum((c + 31) // 32 * 32 for c in chunks)
         sks = make_sketches(chunks)
-        b = sf.Batch(len(sks), graph=graph, max_round_slots=slots)
-        items = [(sk, k, o) for sk, (k, o) in zip(sks, streams)]
-        b.update(items)
-        b.sync()
-        best = float("inf")
-        for _ in range(trials):
-            for sk in sks:
-                sk.reset()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            b.update(items)
-            b.sync()
-            best = min(best, time.perf_counter() - t0)
-        results[R] = total / best
-        if log:
-            log(f"autotune: R={R} -> {results[R] / 1e9:.3f} G updates/s")
-        b.close()
+        by_rounds[R] = total / _time_batch(sf, torch, sks, streams, graph, slots, trials)
+        say(f"autotune: R={R} -> {by_rounds[R] / 1e9:.3f} G updates/s")
         for sk in sks:
             sk.close()
         del sks
-    chosen = choose_rounds(results, tolerance)
+    chosen = choose_rounds(by_rounds, tolerance)
     chunks = chunk_sizes(ns, chosen)
-    plan = {"rounds": chosen, "chunks": chunks, "graph": graph,
-            "round_slots": sum((c + 31) // 32 * 32 for c in chunks),
-            "trials": {str(k): v for k, v in results.items()}, "tolerance": tolerance}
+    slots = sum((c + 31) // 32 * 32 for c in chunks)
+    sks = make_sketches(chunks)
+    # stage 2: launch shape at that round count
+    by_block = {}
+    for blk in blocks:
+        by_block[blk] = total / _time_batch(sf, torch, sks, streams, graph, slots, trials, block=blk)
+        say(f"autotune: R={chosen} block={blk} -> {by_block[blk] / 1e9:.3f} G updates/s")
+    block = choose_fastest(by_block, blocks)
+    # stage 3: launch-group budget at that round count and shape
+    by_group = {}
+    for gbytes in group_budgets:
+        by_group[gbytes] = total / _time_batch(sf, torch, sks, streams, graph, slots, trials, block=block,
+                                               group=gbytes)
+        say(f"autotune: R={chosen} block={block} group={gbytes} -> {by_group[gbytes] / 1e9:.3f} G updates/s")
+    group = choose_fastest(by_group, list(group_budgets))
+    for sk in sks:
+        sk.close()
+    del sks
+    plan = {"rounds": chosen, "chunks": chunks, "graph": graph, "round_slots": slots,
+            "block_threads": block, "group_bytes": group,
+            "trials": {str(k): v for k, v in by_rounds.items()},
+            "trials_block": {str(k): v for k, v in by_block.items()},
+            "trials_group": {("default" if k is None else str(k)): v for k, v in by_group.items()},
+            "best_rounds_bracketed": bracketed(by_rounds), "rounds_skipped_for_memory": skipped,
+            "mem_budget": mem_budget, "tolerance": tolerance}
     if cache_path and cache_key:
         cache = json.load(open(cache_path)) if os.path.exists(cache_path) else {}
         cache[cache_key] = plan

@@ -41,7 +41,8 @@ sf_status run_update(sf_sketch* s, const void* keys_in, const int8_t* ops_in, in
     if (n == 0) return SF_OK;
     if (!keys_in) return SF_ERR_INVALID;
     const void *keys = nullptr, *ops_v = nullptr;
-    if (sf_device_access(keys_in, &keys) != SF_OK || sf_device_access(ops_in, &ops_v) != SF_OK)
+    bool keys_host = false, ops_host = false;
+    if (sf_device_access(keys_in, &keys, &keys_host) != SF_OK || sf_device_access(ops_in, &ops_v, &ops_host) != SF_OK)
         return SF_ERR_INVALID;
     const int8_t* ops = static_cast<const int8_t*>(ops_v);
     const uint32_t kb = s->p.key_bytes;
@@ -74,7 +75,8 @@ sf_status run_update(sf_sketch* s, const void* keys_in, const int8_t* ops_in, in
         one.dict = s->dict;
         one.cap_mask = s->cap - 1u;
         one.claim_mask = sfk::claim_capacity(s->p.chunk) - 1u;
-        e = sfk::launch_chunk_update(one, s->ctrl, s->bar_epoch, s->claims_cap, s->chunk_grid, s->stream);
+        e = sfk::launch_chunk_update(one, s->ctrl, s->bar_epoch, s->claims_cap, s->chunk_grid, s->stream,
+                                     keys_host || ops_host);
         if (e == cudaSuccess) s->bar_epoch += 2ull * ((n + s->p.chunk - 1) / s->p.chunk);
     }
     return e == cudaSuccess ? SF_OK : SF_ERR_CUDA;

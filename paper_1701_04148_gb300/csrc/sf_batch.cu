@@ -32,11 +32,14 @@ struct sf_batch {
     std::vector<sfk::BatchArgs> exec_plan;
     uint32_t exec_d;
     int exec_grid;
+    int exec_block;
+    int block;  // threads per block of the launches (sf_batch_set_block_threads)
     uint32_t graph_launches, graph_captures;
     uint64_t rounds_last;
     uint64_t group_bytes;                        // counter footprint per launch group (0: one launch)
     uint32_t groups_last;
     std::vector<const void*> keys_acc, ops_acc;  // device-usable item pointers of the current call
+    std::vector<uint8_t> in_host;                // the item's keys or operations live in host memory
     std::vector<uint32_t> order;                 // item of each table row (group by group)
     std::vector<sfk::BatchArgs> plan;            // one cooperative launch per group
 };
@@ -48,7 +51,7 @@ constexpr uint64_t kBatchCtrlBytes = 256;
 bool same_shape(const sfk::BatchArgs& x, const sfk::BatchArgs& y) {
     return x.n_runs == y.n_runs && x.claims_cap == y.claims_cap && x.flat_len == y.flat_len &&
            x.n_rounds == y.n_rounds && x.may_ins == y.may_ins && x.may_del == y.may_del && x.runs == y.runs &&
-           x.claims_global == y.claims_global;
+           x.claims_global == y.claims_global && x.max_chunk == y.max_chunk && x.keys_in_host == y.keys_in_host;
 }
 
 bool same_plan(const std::vector<sfk::BatchArgs>& x, const std::vector<sfk::BatchArgs>& y) {
@@ -59,12 +62,12 @@ bool same_plan(const std::vector<sfk::BatchArgs>& x, const std::vector<sfk::Batc
 }
 
 // One table upload, then per launch group: barrier-counter reset and the cooperative launch.
-cudaError_t enqueue(sf_batch* b, const std::vector<sfk::BatchArgs>& plan, uint32_t d, int grid,
+cudaError_t enqueue(sf_batch* b, const std::vector<sfk::BatchArgs>& plan, uint32_t d, int grid, int block,
                     size_t table_bytes, cudaStream_t st) {
     cudaError_t e = cudaMemcpyAsync(b->table_dev, b->staging, table_bytes, cudaMemcpyHostToDevice, st);
     for (size_t g = 0; e == cudaSuccess && g < plan.size(); ++g) {
         e = cudaMemsetAsync(b->ctrl + sfk::kCtrlBarrier64, 0, sizeof(unsigned long long), st);
-        if (e == cudaSuccess) e = sfk::launch_batch_update(plan[g], d, grid, st);
+        if (e == cudaSuccess) e = sfk::launch_batch_update(plan[g], d, grid, block, st);
     }
     return e;
 }
@@ -102,6 +105,7 @@ sf_status sf_batch_create(uint32_t max_sketches, uint64_t max_round_slots, void*
     try {
         b->keys_acc.assign(max_sketches, nullptr);
         b->ops_acc.assign(max_sketches, nullptr);
+        b->in_host.assign(max_sketches, 0);
         b->order.reserve(max_sketches);
     } catch (...) {
         delete b;
@@ -113,6 +117,7 @@ sf_status sf_batch_create(uint32_t max_sketches, uint64_t max_round_slots, void*
     b->table_dev = (sfk::SketchRun*)((uint8_t*)scratch_dev + kBatchCtrlBytes);
     b->stream = (cudaStream_t)cuda_stream;
     b->flags = flags;
+    b->block = sfk::kChunkBlock;
     uint64_t xb = kBatchCtrlBytes + table_bytes_of(max_sketches);  // claim lists need no zeroing
     if (cudaGetDevice(&b->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess ||
@@ -145,9 +150,11 @@ sf_status sf_batch_update(sf_batch* b, uint32_t n_items, const sf_batch_item* it
         if (!s || s->p.d != d || s->p.chunk < 2 || s->device != b->device || (s->p.flags & SF_FLAG_EXPLICIT_INDEX))
             return SF_ERR_INVALID;
         if (items[i].n && !items[i].keys_dev) return SF_ERR_INVALID;
-        if (sf_device_access(items[i].keys_dev, &b->keys_acc[i]) != SF_OK ||
-            sf_device_access(items[i].ops_dev, &b->ops_acc[i]) != SF_OK)
+        bool kh = false, oh = false;
+        if (sf_device_access(items[i].keys_dev, &b->keys_acc[i], &kh) != SF_OK ||
+            sf_device_access(items[i].ops_dev, &b->ops_acc[i], &oh) != SF_OK)
             return SF_ERR_INVALID;
+        b->in_host[i] = (kh || oh) ? 1 : 0;
         const uint32_t kb = s->p.key_bytes;
         if ((kb == 4 || kb == 8) && ((uintptr_t)b->keys_acc[i] % kb) != 0) return SF_ERR_INVALID;
     }
@@ -155,9 +162,12 @@ sf_status sf_batch_update(sf_batch* b, uint32_t n_items, const sf_batch_item* it
     if (!guard.ok) return SF_ERR_CUDA;
     if (b->staging_busy && cudaEventSynchronize(b->staged) != cudaSuccess) return SF_ERR_CUDA;
 
-    const int bps = sfk::chunk_update_blocks_per_sm(d);
+    // every launch shape keeps 512 threads per SM: 512 / block co-resident blocks of `block` threads
+    const int block = b->block;
+    const int bps = sfk::chunk_update_blocks_per_sm(d, block);
     if (bps <= 0) return SF_ERR_CUDA;
-    const int grid = b->num_sms * (bps < 2 ? bps : 2);
+    const int per_sm = sfk::kChunkBlock / block;
+    const int grid = b->num_sms * (bps < per_sm ? bps : per_sm);
 
     // Launch groups.  Sketches are independent, so they may run in any grouping.  Sketches whose
     // counters fit the group budget are packed, in input order, into groups whose counters fit it
@@ -169,7 +179,7 @@ sf_status sf_batch_update(sf_batch* b, uint32_t n_items, const sf_batch_item* it
     std::vector<std::pair<uint32_t, uint32_t>> groups;  // [first, last) rows of the table
     {
         const uint64_t budget = b->group_bytes;
-        const uint64_t min_slots = (uint64_t)grid * sfk::kChunkBlock;
+        const uint64_t min_slots = (uint64_t)grid * (uint64_t)block;
         std::vector<uint32_t> shared, cur_g;
         uint64_t gb = 0, gs = 0;
         auto close = [&]() {
@@ -206,7 +216,7 @@ sf_status sf_batch_update(sf_batch* b, uint32_t n_items, const sf_batch_item* it
     for (const auto& gr : groups) {
         uint64_t flat = 0, rounds = 0;
         uint32_t max_chunk = 0;
-        bool may_ins = false, may_del = false;
+        bool may_ins = false, may_del = false, in_host = false;
         for (uint32_t row = gr.first; row < gr.second; ++row) {
             const uint32_t i = b->order[row];
             const sf_sketch* s = items[i].sketch;
@@ -231,6 +241,7 @@ sf_status sf_batch_update(sf_batch* b, uint32_t n_items, const sf_batch_item* it
             R.claim_mask = sfk::claim_capacity(R.S) - 1u;
             flat += sfk::round_up32(R.S);
             max_chunk = R.S > max_chunk ? R.S : max_chunk;
+            in_host |= b->in_host[i] != 0;
             const uint64_t nr = (R.n + R.S - 1) / R.S;
             rounds = nr > rounds ? nr : rounds;
             if (R.n) {
@@ -246,16 +257,17 @@ sf_status sf_batch_update(sf_batch* b, uint32_t n_items, const sf_batch_item* it
         a.n_runs = gr.second - gr.first;
         a.flat_len = flat;
         a.n_rounds = rounds;
-        a.claims_cap = sfk::chunk_claims_cap(flat, grid);
+        a.claims_cap = sfk::chunk_claims_cap(flat, grid, block);
         a.ctrl = b->ctrl;
         a.bar_base = 0;  // each launch zeroes the barrier counter first
         a.timeout_ns = sfk::kBarrierTimeoutNs;
         a.may_ins = may_ins;
         a.may_del = may_del;
         a.max_chunk = max_chunk;
+        a.keys_in_host = in_host ? 1 : 0;
         // claim lists in shared memory when they fit, else in the batch scratch (launches run in order)
         a.claims_global =
-            ((uint64_t)a.claims_cap * sizeof(uint2) > (uint64_t)sfk::kMaxClaimSmem) ? b->claims_dev : nullptr;
+            ((uint64_t)a.claims_cap * sizeof(uint2) > (uint64_t)sfk::claim_smem_max(block)) ? b->claims_dev : nullptr;
         b->plan.push_back(a);
         rounds_all = rounds > rounds_all ? rounds : rounds_all;
     }
@@ -266,7 +278,8 @@ sf_status sf_batch_update(sf_batch* b, uint32_t n_items, const sf_batch_item* it
     cudaError_t e = cudaSuccess;
     bool launched = false;
     if (b->flags & SF_BATCH_GRAPH) {
-        if (!b->have_exec || !same_plan(b->exec_plan, b->plan) || b->exec_d != d || b->exec_grid != grid) {
+        if (!b->have_exec || !same_plan(b->exec_plan, b->plan) || b->exec_d != d || b->exec_grid != grid ||
+            b->exec_block != block) {
             if (b->have_exec) {
                 cudaGraphExecDestroy(b->exec);
                 b->have_exec = false;
@@ -274,7 +287,7 @@ sf_status sf_batch_update(sf_batch* b, uint32_t n_items, const sf_batch_item* it
             cudaGraph_t g = nullptr;
             bool ok = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
             if (ok) {
-                const cudaError_t ce = enqueue(b, b->plan, d, grid, table_bytes, b->cap_stream);
+                const cudaError_t ce = enqueue(b, b->plan, d, grid, block, table_bytes, b->cap_stream);
                 ok = cudaStreamEndCapture(b->cap_stream, &g) == cudaSuccess && ce == cudaSuccess && g;
             }
             if (ok) ok = cudaGraphInstantiate(&b->exec, g, 0) == cudaSuccess;
@@ -284,6 +297,7 @@ sf_status sf_batch_update(sf_batch* b, uint32_t n_items, const sf_batch_item* it
                 b->exec_plan = b->plan;
                 b->exec_d = d;
                 b->exec_grid = grid;
+                b->exec_block = block;
                 b->graph_captures++;
             } else {
                 cudaGetLastError();           // capture not supported here: launch directly from now on
@@ -296,7 +310,7 @@ sf_status sf_batch_update(sf_batch* b, uint32_t n_items, const sf_batch_item* it
             if (e == cudaSuccess) b->graph_launches++;
         }
     }
-    if (!launched) e = enqueue(b, b->plan, d, grid, table_bytes, b->stream);
+    if (!launched) e = enqueue(b, b->plan, d, grid, block, table_bytes, b->stream);
     if (e == cudaSuccess) e = cudaEventRecord(b->staged, b->stream);
     b->staging_busy = true;
     return e == cudaSuccess ? SF_OK : SF_ERR_CUDA;
@@ -321,6 +335,12 @@ sf_status sf_batch_sync(sf_batch* b) {
 sf_status sf_batch_set_group_bytes(sf_batch* b, uint64_t bytes) {
     if (!b) return SF_ERR_INVALID;
     b->group_bytes = bytes;
+    return SF_OK;
+}
+
+sf_status sf_batch_set_block_threads(sf_batch* b, uint32_t threads) {
+    if (!b || (threads != 512 && threads != 256 && threads != 128)) return SF_ERR_INVALID;
+    b->block = (int)threads;
     return SF_OK;
 }
 

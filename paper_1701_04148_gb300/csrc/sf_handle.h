@@ -12,8 +12,10 @@
 // cudaHostRegister) through its mapping into the device's address space, so the kernel itself
 // moves those bytes over the host link and no staging copy is needed.  Pageable host memory and
 // unknown pointers are refused with SF_ERR_INVALID before anything is launched.  NULL maps to NULL.
-inline sf_status sf_device_access(const void* p, const void** out) {
+// *host (if given) tells whether the bytes live in host memory.
+inline sf_status sf_device_access(const void* p, const void** out, bool* host = nullptr) {
     *out = nullptr;
+    if (host) *host = false;
     if (!p) return SF_OK;
     cudaPointerAttributes at{};
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
@@ -28,6 +30,7 @@ inline sf_status sf_device_access(const void* p, const void** out) {
         case cudaMemoryTypeHost:
             if (!at.devicePointer) return SF_ERR_INVALID;
             *out = at.devicePointer;
+            if (host) *host = true;
             return SF_OK;
         default:
             return SF_ERR_INVALID;

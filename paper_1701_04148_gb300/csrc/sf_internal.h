@@ -37,6 +37,7 @@ struct BatchArgs {
     int32_t may_del;        // ... a deletion
     uint2* claims_global;   // per-block claim lists in global memory (claims_cap each), or nullptr: shared memory
     uint32_t max_chunk;     // largest S of the launch's sketches
+    int32_t keys_in_host;   // some sketch's keys (or operations) live in host memory, read over the host link
 };
 
 inline uint64_t round_up32(uint64_t x) { return (x + 31) & ~31ull; }
@@ -95,43 +96,58 @@ struct MultiQueryArgs {
     uint32_t* out;
 };
 
-constexpr int kChunkBlock = 512;
+constexpr int kChunkBlock = 512;  // default block of the chunked-update kernels (also built for 256 and 128)
 constexpr int kSeqBlock = 256;
 constexpr int kQueryBlock = 256;
 constexpr uint64_t kBarrierTimeoutNs = 2000000000ull;  // 2 s per wait
 constexpr int kMaxClaimSmem = 96 * 1024;               // dynamic shared memory for the claim list
 
 // Chunked update: one cooperative persistent launch per call (one sketch or a batch of sketches
-// sharing d); 2 grid barriers per round.
-cudaError_t launch_batch_update(const BatchArgs& a, uint32_t d, int grid, cudaStream_t st);
+// sharing d) of `grid` blocks of `block` threads (512, 256 or 128); 2 grid barriers per round.
+cudaError_t launch_batch_update(const BatchArgs& a, uint32_t d, int grid, int block, cudaStream_t st);
+// Per-block dispatch over d, instantiated for each block size in its own translation unit.
+template <int B>
+cudaError_t launch_batch_block(const BatchArgs& a, uint32_t d, int grid, cudaStream_t st);
+template <int B>
+int blocks_per_sm_block(uint32_t d);
+// Dynamic shared memory a block may use for its claim list: 96 KiB at 512 threads, in proportion
+// below, so that 512 / block blocks of a launch fit one SM.
+inline int claim_smem_max(int block) { return kMaxClaimSmem * block / kChunkBlock; }
 // Global claim-list bytes a launch over rounds of up to max_round_slots slots may need (any grid <= 1024 blocks).
 inline uint64_t claims_global_bytes(uint64_t max_round_slots) {
     return (max_round_slots + 1024ull * kChunkBlock) * 8ull;
 }
-int chunk_update_blocks_per_sm(uint32_t d);
+int chunk_update_blocks_per_sm(uint32_t d, int block = kChunkBlock);
 // A launch whose rounds give every worker lane at most one update, with chunks of at most
 // kClaimMaxChunk updates, runs the single-iteration kernel, which builds each chunk's dictionary one round ahead
 // (8-byte claim entries with 16-bit positions and counts).  Both kernels pass two grid barriers per
 // round.
 constexpr uint32_t kClaimMaxChunk = 65536;
-inline bool chunk_rounds_single(uint64_t flat_len, uint32_t max_chunk, int grid) {
-    // warp 0 of each block only passes the grid barriers, so the workers hold kChunkBlock - 32 slots
-    return flat_len <= (uint64_t)grid * (uint64_t)(kChunkBlock - 32) && max_chunk <= kClaimMaxChunk;
+// Keys in host memory go to the multi-iteration kernel: the single-iteration kernel reads each
+// chunk's keys inside a barrier window and re-reads a claimer's key to confirm a fingerprint match,
+// so host-link latency would sit on its critical path (measured: 1.39x the multi-iteration kernel's
+// time at Zipf 1 with pinned 13-byte keys, although 1.18x faster with device-resident ones).
+inline bool chunk_rounds_single(uint64_t flat_len, uint32_t max_chunk, int grid, bool keys_in_host = false,
+                                int block = kChunkBlock) {
+    // warp 0 of each block only passes the grid barriers, so the workers hold block - 32 slots
+    return !keys_in_host && flat_len <= (uint64_t)grid * (uint64_t)(block - 32) && max_chunk <= kClaimMaxChunk;
 }
-// Entries per half of the claim dictionary: a power of two >= kClaimLoad S (load factor <= 1/8).  Two
-// halves of 8-byte entries take 16 x that many bytes: no more than the DictEntry dictionary of a
-// sketch (32 B x pow2 >= 16 S) or of the allocation-free entry point (32 B x pow2 >= 4 S).
-constexpr uint32_t kClaimLoad = 8;
-inline uint32_t claim_capacity(uint32_t S) {
-    uint64_t need = (uint64_t)kClaimLoad * (uint64_t)S;
+// Entries per half of the claim dictionary: a power of two >= load x S.  Two halves of 8-byte entries
+// take 16 x that many bytes.  Sketches use load 16 (factor <= 1/16: short probe chains, measured
+// faster than 1/8 and 1/4), which fits their DictEntry dictionary bytes (32 B x pow2 >= 16 S); the
+// allocation-free entry point uses 8, which fits its fixed array (32 B x pow2 >= 4 S).
+constexpr uint32_t kClaimLoad = 16;
+constexpr uint32_t kClaimLoadNoAlloc = 8;
+inline uint32_t claim_capacity(uint32_t S, uint32_t load = kClaimLoad) {
+    uint64_t need = (uint64_t)load * (uint64_t)S;
     uint64_t cap = 64;
     while (cap < need) cap <<= 1;
     return (uint32_t)cap;
 }
-uint32_t chunk_claims_cap(uint64_t flat_len, int grid);
+uint32_t chunk_claims_cap(uint64_t flat_len, int grid, int block = kChunkBlock);
 // Single sketch: a batch of one.
 cudaError_t launch_chunk_update(const SketchRun& one, uint32_t* ctrl, uint64_t bar_base, uint32_t claims_cap,
-                                int grid, cudaStream_t st);
+                                int grid, cudaStream_t st, bool keys_in_host = false);
 // One-at-a-time update (S = 1).
 cudaError_t launch_seq_update(const SeqArgs& a, cudaStream_t st, int smem_limit);
 // One-at-a-time insertions as a dependency graph over pieces of up to kDagN updates (sf_seqdag.cu):

@@ -28,7 +28,8 @@ constexpr uint32_t noalloc_capacity(uint32_t S) {
 static_assert(kNoAllocCtrlBytes + (uint64_t)noalloc_capacity(SF_NOALLOC_MAX_CHUNK) * sizeof(sfk::DictEntry) <=
                   kNoAllocScratchBytes,
               "the largest dictionary must fit the fixed scratch array");
-static_assert(sfk::kClaimLoad <= 8, "two halves of claim entries must fit the dictionary bytes of 4 S DictEntry slots");
+static_assert(sfk::kClaimLoadNoAlloc <= 8, "two halves of claim entries must fit the dictionary bytes of 4 S DictEntry slots");
+static_assert(sfk::kClaimLoad <= 32, "two halves of claim entries must fit a sketch's dictionary bytes of 16 S DictEntry slots");
 
 // The shared scratch: control words (error bits, barrier counter) then the key dictionary.
 static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
@@ -64,7 +65,9 @@ extern "C" sf_status sf_update_batch_noalloc(const sf_params* p, uint32_t* fat_d
     if (n == 0) return SF_OK;
     if (!keys_dev) return SF_ERR_INVALID;
     const void *keys_acc = nullptr, *ops_acc = nullptr;
-    if (sf_device_access(keys_dev, &keys_acc) != SF_OK || sf_device_access(ops_dev, &ops_acc) != SF_OK)
+    bool keys_host = false, ops_host = false;
+    if (sf_device_access(keys_dev, &keys_acc, &keys_host) != SF_OK ||
+        sf_device_access(ops_dev, &ops_acc, &ops_host) != SF_OK)
         return SF_ERR_INVALID;
     keys_dev = keys_acc;
     ops_dev = static_cast<const int8_t*>(ops_acc);
@@ -106,10 +109,10 @@ extern "C" sf_status sf_update_batch_noalloc(const sf_params* p, uint32_t* fat_d
     one.n = n;
     one.dict = (sfk::DictEntry*)((uint8_t*)scratch + kNoAllocCtrlBytes);
     one.cap_mask = cap - 1u;
-    one.claim_mask = sfk::claim_capacity(p->chunk) - 1u;
+    one.claim_mask = sfk::claim_capacity(p->chunk, sfk::kClaimLoadNoAlloc) - 1u;
     // the barrier counter was just zeroed, so this launch starts from barrier 0
     if (sfk::launch_chunk_update(one, (uint32_t*)scratch, 0, sfk::chunk_claims_cap(sfk::round_up32(p->chunk), grid),
-                                 grid, stream) != cudaSuccess)
+                                 grid, stream, keys_host || ops_host) != cudaSuccess)
         return SF_ERR_CUDA;
     if (err_dev && cudaMemcpyAsync(err_dev, scratch, sizeof(uint32_t), cudaMemcpyDeviceToDevice, stream) != cudaSuccess)
         return SF_ERR_CUDA;

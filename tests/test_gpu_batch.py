@@ -104,6 +104,33 @@ def test_one_ranks_share_of_a_sharded_batch(sf, world, rank):
         assert np.array_equal(bsk[i].slim.cpu().numpy().view(np.uint32).reshape(o.A.shape), o.A), mine[i]
 
 
+@pytest.mark.parametrize("threads", [128, 256, 512])
+def test_launch_shapes_give_the_same_sketches(sf, threads):
+    """Every block shape of sf_batch_set_block_threads (512 / threads blocks per SM) leaves each
+    sketch equal to one sf_update_batch call per sketch: rounds of a few thousand slots (one update
+    per worker lane: the single-iteration kernel) and rounds of several hundred thousand (the
+    multi-iteration kernel)."""
+    import torch
+    plan = _plan(20, seed=41, w_log2=(8.0, 12.0), n_log10=(3.0, 5.3))
+    streams = _streams(plan)
+    for rounds in (40, 2):
+        chunks = [_chunk_for(p, rounds) for p in plan]
+        bsk = [sf.Sketch(4, p["w"], 16, 4, p["seed"], c) for p, c in zip(plan, chunks)]
+        psk = [sf.Sketch(4, p["w"], 16, 4, p["seed"], c) for p, c in zip(plan, chunks)]
+        b = sf.Batch(len(plan), block_threads=threads, group_bytes=0)
+        b.update([(sk, st.keys, st.ops) for sk, (st, _) in zip(bsk, streams)])
+        for sk, (st, _) in zip(psk, streams):
+            sk.update(st.keys, st.ops)
+        assert b.sync() == sf.SF_OK
+        for sk in psk:
+            sk.sync()
+        for i in range(len(plan)):
+            assert torch.equal(bsk[i].fat, psk[i].fat) and torch.equal(bsk[i].slim, psk[i].slim), (threads, rounds, i)
+        b.close()
+    with pytest.raises(sf.SFError):
+        sf.Batch(4, block_threads=384)
+
+
 def test_batch_with_13_byte_keys_and_empty_items(sf):
     import torch
     sks, items, refs = [], [], []

@@ -12,3 +12,19 @@ def test_autotuner_chunks_and_choice():
     k1 = autotune.shape_key([1024, 2048], [10, 20], 4, 16, 4)
     assert k1 == autotune.shape_key([1024, 2048], [10, 20], 4, 16, 4)
     assert k1 != autotune.shape_key([1024, 2048], [10, 21], 4, 16, 4)
+
+
+def test_autotuner_shape_and_group_choice_and_bracketing():
+    """Block shape and launch-group budget are not semantic: the fastest wins, ties go to the
+    candidate listed first; the round-count search reports whether its fastest candidate lies inside
+    the range tried (bracketed) or at an end."""
+    from paper_1701_04148_gb300 import autotune
+    assert autotune.choose_fastest({512: 6.0, 256: 6.4, 128: 5.1}, (512, 256, 128)) == 256
+    assert autotune.choose_fastest({512: 6.0, 256: 6.0, 128: 5.1}, (512, 256, 128)) == 512
+    assert autotune.choose_fastest({None: 5.0, 1 << 26: 5.2, 0: 4.0}, [None, 1 << 26, 0]) == 1 << 26
+    assert autotune.choose_fastest({None: 5.0, 0: 5.0}, [None, 0]) is None
+    assert autotune.bracketed({8: 6.0, 16: 7.1, 32: 7.0, 64: 6.1})
+    assert not autotune.bracketed({16: 6.0, 32: 7.1, 64: 6.1, 8: 7.2})
+    assert not autotune.bracketed({8: 6.0, 16: 6.5, 1024: 6.6})
+    assert autotune.ROUND_CANDIDATES[0] < 32 < autotune.ROUND_CANDIDATES[-1]
+    assert set(autotune.BLOCK_CANDIDATES) == {512, 256, 128}
