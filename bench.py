@@ -228,6 +228,9 @@ def main():
     ap.add_argument("--ref-queries", type=int, default=20_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="flows: skip the chunked-vs-sequential accuracy report (its one-at-a-time runs launch "
+                         "thousands of kernels)")
     ap.add_argument("--workload", choices=["all", "flows", "batch", "serve", "accuracy", "pipeline", "profile",
                                            "l2curve", "seq", "outofl2"],
                     default="all",
@@ -276,7 +279,8 @@ def main():
     L = sf.load()
     stream = torch.cuda.current_stream(dev)
 
-    ctx = dict(world=world, rank=rank, local=local, dist=dist, dev=dev, L=L, stream=stream)
+    # the measurement kernels (roofline denominators) come from their own library
+    ctx = dict(world=world, rank=rank, local=local, dist=dist, dev=dev, L=L, B=sf.load_bench(), stream=stream)
     line = None
     if args.workload in ("all", "flows"):
         line = run_flows(args, ctx)
@@ -350,12 +354,26 @@ def run_flows(args, ctx):
     # update launches plus a query per sketch
     launches_per_step = (2 if batched else 2 * len(SWEEP)) + len(SWEEP)
 
-    def step(evs=None, host=None, direct=False):
+    pipe = None  # (staging, copy stream) of the pipelined host form
+
+    def step(evs=None, host=None, direct=False, pipelined=False):
         """One step.  host: pinned host copies of the inputs (and answer buffers).  direct=False
         copies them to the device first and the answers back; direct=True hands the pinned host
         buffers to the same calls, and the kernels read the keys and write the answers over the
-        host link themselves."""
+        host link themselves; pipelined=True updates each sketch through sf_update_pipelined (host
+        keys copied in chunk-aligned pieces, overlapped with the updates) and queries with the host
+        keys and answers directly."""
         src, out = inputs, answers
+        if pipelined:
+            for idx, sk in enumerate(sketches):
+                sk.reset()
+            for idx, sk in enumerate(sketches):
+                sk.update_pipelined(host[idx][0], None, 1, staging=pipe[0], copy_stream=pipe[1])
+                sk.update_pipelined(host[idx][1], None, -1, staging=pipe[0], copy_stream=pipe[1])
+            hdrs = [sketches[idx].export_slim(slims[idx])[1] for idx in range(len(SWEEP))]
+            for idx in range(len(SWEEP)):
+                sf.query(slims[idx], hdrs[idx], host[idx][2], out=host[idx][3], stream=stream)
+            return
         if host is not None and not direct:
             for idx in range(len(SWEEP)):
                 ins_h, dels_h, flows_h, _ = host[idx]
@@ -438,7 +456,7 @@ def run_flows(args, ctx):
     # minimum, Fat estimate), and on GB300 random L2 traffic of that 1:1 mix runs well below
     # either kind alone, so the peak is the measured rate of the mix (half the warps reduce, half
     # load); the load-only rate is reported beside it.
-    best = l2_random_peaks(L, dev, stream)
+    best = l2_random_peaks(ctx["B"], dev, stream)
     upd_timed = args.steps * len(SWEEP) * (N_INS + n_del)
     chunk_ms = t_ins + t_del
     launches_chunk = args.steps * (2 if batched else 2 * len(SWEEP))
@@ -488,15 +506,17 @@ def run_flows(args, ctx):
         h2d = sum(h[0].numel() + h[1].numel() + h[2].numel() for h in host)
         d2h = sum(h[3].numel() * 4 for h in host)
 
-        def timed_e2e(direct):
-            step(host=host, direct=direct)
+        pipe = (torch.empty(2 * ((1 << 22) * KB + 16), dtype=torch.uint8, device=dev), torch.cuda.Stream(device=dev))
+
+        def timed_e2e(direct, pipelined=False):
+            step(host=host, direct=direct, pipelined=pipelined)
             torch.cuda.synchronize()
             if dist is not None:
                 dist.barrier()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
             for _ in range(args.steps):
-                step(host=host, direct=direct)
+                step(host=host, direct=direct, pipelined=pipelined)
             b.record(stream)
             torch.cuda.synchronize()
             ems = a.elapsed_time(b) / args.steps
@@ -509,13 +529,19 @@ def run_flows(args, ctx):
             return {"value": round(world * ops_per_step / (ems / 1e3) / 1e6, 2), "unit": "M ops/s",
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ems, 3)}
 
-        e2e = timed_e2e(True)
-        e2e["transfer"] = ("pinned host buffers passed to the same calls: the update kernel reads each key "
-                           "over the host link as it consumes it, the query kernel writes the answers to "
-                           "host memory; no staging copy")
+        e2e = timed_e2e(False, pipelined=True)
+        e2e["transfer"] = ("sf_update_pipelined per sketch and call: pinned host keys copied in chunk-aligned "
+                           "pieces of 2^22 keys into two staging halves on a copy stream, overlapped with the "
+                           "updates; the query kernel reads the pinned flow keys and writes the answers to "
+                           "pinned host memory")
         # the answers the host received equal the device-resident run's (same inputs)
         e2e["answers_equal_device_resident"] = all(torch.equal(host[i][3], answers[i].cpu())
                                                    for i in range(len(SWEEP)))
+        direct_ = timed_e2e(True)
+        direct_["transfer"] = ("pinned host buffers passed to the same calls: the update kernel reads each key "
+                               "over the host link as it consumes it, the query kernel writes the answers to "
+                               "host memory; no staging copy")
+        e2e["direct"] = direct_
         staged = timed_e2e(False)
         staged["transfer"] = "cudaMemcpyAsync of the keys to device buffers, kernels, copy of the answers back"
         e2e["staged"] = staged
@@ -609,7 +635,7 @@ def run_flows(args, ctx):
             g.sync()
             exact &= bool(np.array_equal(got.cpu().numpy().view(np.uint32), want[idx]))
 
-    accuracy = accuracy_report(inputs, dev, stream) if rank == 0 else None
+    accuracy = accuracy_report(inputs, dev, stream) if rank == 0 and not args.no_accuracy else None
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 2), "unit": "M ops/s", "n_gpus": world, "steps": args.steps,
@@ -877,7 +903,7 @@ def run_outofl2(args, ctx):
     alg_bytes = n_ins * (OOL2_KB + 1 + OOL2_D * 3 * OOL2_SECTOR) + n_del * (OOL2_KB + 1 + OOL2_D * 4 * OOL2_SECTOR)
     peaks, psrc = measured_peaks()
     achieved = alg_bytes / (t_upd / 1e3) / 1e9
-    peaks_r = hbm_random_peaks(L, dev, stream)
+    peaks_r = hbm_random_peaks(ctx["B"], dev, stream)
     tr = traffic_record()
     traffic = None
     if tr is not None and "outofl2" in tr:
@@ -904,7 +930,7 @@ def run_outofl2(args, ctx):
     roofline["random_hbm_rates_g_ops"] = {k: round(v, 2) for k, v in peaks_r.items()}
     # queries: d random gathers per key from the exported 64 MiB Slim, against random 32-bit loads
     # on a 64 MiB buffer (measured in this run)
-    ld64 = l2_random_peaks(L, dev, stream)["ld"]
+    ld64 = l2_random_peaks(ctx["B"], dev, stream)["ld"]
     g_q = nq * OOL2_D / (t_q_only / 1e3) / 1e9
     roofline_query = {"bound": "l2", "kernel": "query_kernel", "achieved": round(g_q, 2), "peak": round(ld64, 2),
                       "unit": "G random L2 ops/s", "frac": round(g_q / ld64, 4),
@@ -973,7 +999,7 @@ def run_l2curve(args, ctx):
     2^28 operations, best of three) over buffers of 32-160 MiB: where the L2 stops holding a
     random working set; then the returning atomic forms (kinds 1, 3, 4, 6) at 64 MiB and 1 GiB."""
     import torch
-    L, dev, stream = ctx["L"], ctx["dev"], ctx["stream"]
+    L, dev, stream = ctx["B"], ctx["dev"], ctx["stream"]
     mib = 1 << 20
     buf = torch.zeros((160 * mib) // 4, dtype=torch.int32, device=dev)
     h_st = int(stream.cuda_stream)

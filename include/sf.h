@@ -202,6 +202,21 @@ sf_status sf_query_pipelined(const sf_slim_view *slim, const void *keys_host, ui
                              void *keys_dev, uint32_t *out_dev, uint32_t n_streams, void *const *streams);
 
 /*
+ * Update from host memory, copies overlapped with the kernels (the multi-stream pipeline of Sec.
+ * 4.2.2, applied to insertions and deletions).  The n keys (and operations) at keys_host / ops_host
+ * -- page-locked host memory for the copies to overlap -- are copied in pieces of a whole number of
+ * chunks (params.chunk updates each) into two alternating halves of staging_dev, on copy_stream
+ * (a cudaStream_t other than the sketch's), and each piece is applied on the sketch's stream as soon
+ * as it has landed, while the next piece is copied.  Pieces end on chunk boundaries, so the counters
+ * equal one sf_update_batch call over all n updates.  ops_host NULL: every update is op_const
+ * (+1 insert or -1 delete).  staging_dev: device memory of staging_bytes >= 2 * chunk * (key_bytes +
+ * (ops_host ? 1 : 0)) bytes, else SF_ERR_OOM.  Asynchronous: the host buffers and the staging stay
+ * in use until sf_sync on the sketch returns.
+ */
+sf_status sf_update_pipelined(sf_sketch *s, const void *keys_host, const int8_t *ops_host, int32_t op_const,
+                              uint64_t n, void *staging_dev, uint64_t staging_bytes, void *copy_stream);
+
+/*
  * ---- Batched many-sketch update --------------------------------------------------------------
  * Monitoring nodes each fill their own sketch (Sec. 1.1); a collector-side or node-side host may
  * hold thousands of them.  The paper updates one sketch at a time; a batch applies one call's

@@ -18,6 +18,7 @@ import threading
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libsfgb300.so")
+BENCH_LIB_PATH = os.path.join(_HERE, "_build", "libsfbench.so")
 
 SF_OK = 0
 SF_ERR_INVALID = -1
@@ -92,6 +93,8 @@ _SIGS = {
     "sf_query_batch": (ctypes.c_int32, [ctypes.POINTER(SlimView), ctypes.c_void_p, ctypes.c_uint64,
                                         ctypes.c_void_p, ctypes.c_void_p]),
     "sf_sync": (ctypes.c_int32, [ctypes.c_void_p]),
+    "sf_update_pipelined": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                             ctypes.c_uint64, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]),
     "sf_query_pipelined": (ctypes.c_int32, [ctypes.POINTER(SlimView), ctypes.c_void_p, ctypes.c_uint64,
                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32,
                                             ctypes.c_void_p]),
@@ -120,15 +123,42 @@ _SIGS = {
     "sf_update_batch_noalloc": (ctypes.c_int32, [ctypes.POINTER(Params), ctypes.c_void_p, ctypes.c_void_p,
                                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
                                                  ctypes.c_void_p]),
+}
+
+# The measurement library (include/sf_bench.h): roofline denominators and the bounded-wait test kernel.
+_BENCH_SIGS = {
     "sf_bench_random_access": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
                                                 ctypes.c_uint32, ctypes.c_void_p]),
     "sf_bench_grid_barrier": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]),
     "sf_bench_wait_timeout": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p]),
 }
+_bench_lib = None
 
 
 def exported_symbols() -> list[str]:
     return list(_SIGS)
+
+
+def exported_bench_symbols() -> list[str]:
+    return list(_BENCH_SIGS)
+
+
+def load_bench(path: str | None = None):
+    """Load the measurement library libsfbench.so (raises if it was not built)."""
+    global _bench_lib
+    with _lock:
+        if _bench_lib is None:
+            p = path or BENCH_LIB_PATH
+            if not os.path.exists(p):
+                raise RuntimeError(f"measurement library not built ({p}); run "
+                                   "`python -m paper_1701_04148_gb300.build` on a machine with nvcc")
+            L = ctypes.CDLL(p)
+            for name, (res, args) in _BENCH_SIGS.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _bench_lib = L
+    return _bench_lib
 
 
 def load(path: str | None = None):
@@ -291,6 +321,23 @@ class Sketch:
         if ops.numel() != n:
             raise ValueError("ops must have one entry per key")
         check(load().sf_update_batch(self.handle, _io_ptr(k, "keys"), _io_ptr(ops, "ops"), n), "sf_update_batch")
+
+    def update_pipelined(self, keys_host, ops_host=None, op_const: int = 1, staging=None, copy_stream=None):
+        """sf_update_pipelined: host keys (pinned CPU tensor) copied in chunk-aligned pieces on
+        copy_stream while the previous piece is applied.  staging: device uint8 tensor (default: two
+        pieces of 2^22 updates); keep the tensors alive until sync()."""
+        torch = _torch()
+        k, n = self._keys(keys_host)
+        if staging is None:
+            per = self.params.key_bytes + (1 if ops_host is not None else 0)
+            piece = max(1, (1 << 22) // self.params.chunk) * self.params.chunk
+            staging = torch.empty(2 * (piece * per + 16), dtype=torch.uint8, device=self.device)
+        if copy_stream is None:
+            copy_stream = torch.cuda.Stream(device=self.device)
+        self._pipeline = (k, ops_host, staging, copy_stream)
+        check(load().sf_update_pipelined(self.handle, k.data_ptr(), ops_host.data_ptr() if ops_host is not None else 0,
+                                         op_const, n, _dev_ptr(staging, "staging"), staging.numel(),
+                                         int(copy_stream.cuda_stream)), "sf_update_pipelined")
 
     def sync(self) -> int:
         return check(load().sf_sync(self.handle), "sf_sync")

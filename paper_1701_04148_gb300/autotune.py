@@ -96,8 +96,9 @@ def tune(make_sketches, streams, ns, candidates=ROUND_CANDIDATES, blocks=BLOCK_C
     """make_sketches(chunks) -> list of Sketch; streams: list of (keys, ops) device tensors.
     group_budgets: launch-group budgets to try (None entries: the library default); by default the
     default, half of L2 and 0 (one launch).  widths (with d, z): the sketches' widths, to skip round
-    counts whose sketches exceed mem_budget bytes (default: a quarter of the device's free memory, so
-    that a caller can hold a second set of the tuned sketches beside its inputs).
+    counts whose sketches exceed mem_budget bytes (default: a sixth of the device's memory, so that a
+    caller can hold a second set of the tuned sketches beside its inputs, and the choice does not
+    depend on what else happens to be allocated).
     Returns {"rounds", "chunks", "block_threads", "group_bytes", "graph", "trials", ...}."""
     import torch
 
@@ -113,7 +114,7 @@ def tune(make_sketches, streams, ns, candidates=ROUND_CANDIDATES, blocks=BLOCK_C
     total = sum(int(n) for n in ns)
     say = log or (lambda m: None)
     if mem_budget is None:
-        mem_budget = torch.cuda.mem_get_info()[0] // 4
+        mem_budget = torch.cuda.get_device_properties(torch.cuda.current_device()).total_memory // 6
     skipped = []
 
     # stage 1: round count at the default shape and grouping

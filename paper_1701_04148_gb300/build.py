@@ -1,7 +1,9 @@
-"""Build the in-tree CUDA library libsfgb300.so for sm_103a (nvcc, no cmake).
+"""Build the in-tree CUDA libraries for sm_103a (nvcc, no cmake): libsfgb300.so (the sketch
+library, csrc/*.cu) and libsfbench.so (the measurement kernels of the benchmark and the bounded-wait
+failure test, csrc/bench/*.cu).
 
-Each translation unit compiles in parallel (`nvcc -c`), then one `nvcc -shared` links them.
-The result lands in paper_1701_04148_gb300/_build/ (git-ignored).  Usage:
+Each translation unit compiles in parallel (`nvcc -c`), then one `nvcc -shared` per library links
+them.  The results land in paper_1701_04148_gb300/_build/ (git-ignored).  Usage:
     python -m paper_1701_04148_gb300.build [--force] [--verbose]
 """
 from __future__ import annotations
@@ -17,6 +19,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libsfgb300.so")
+BENCH_LIB = os.path.join(BUILD, "libsfbench.so")
+BENCH_SRC = os.path.join(CSRC, "bench")
 ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 
@@ -32,13 +36,13 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the SF-sketch CUDA library cannot be built")
 
 
-def sources() -> list[str]:
-    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
+def sources(folder: str = CSRC) -> list[str]:
+    return sorted(os.path.join(folder, f) for f in os.listdir(folder) if f.endswith(".cu"))
 
 
 def _deps() -> list[str]:
     out = []
-    for d in (CSRC, INCLUDE):
+    for d in (CSRC, BENCH_SRC, INCLUDE):
         for f in os.listdir(d):
             if f.endswith((".cu", ".cuh", ".h")):
                 out.append(os.path.join(d, f))
@@ -46,9 +50,9 @@ def _deps() -> list[str]:
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(BENCH_LIB):
         return False
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(BENCH_LIB))
     return all(os.path.getmtime(p) <= t for p in _deps() + [__file__])
 
 
@@ -60,7 +64,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
     flags = NVCC_FLAGS + (extra_flags or [])
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(BUILD, os.path.basename(src).replace(".cu", ".o"))
+        sub = "bench_" if os.path.dirname(src) == BENCH_SRC else ""
+        obj = os.path.join(BUILD, sub + os.path.basename(src).replace(".cu", ".o"))
         cmd = [nv] + ARCH + flags + ["-c", src, "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
@@ -71,15 +76,16 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
             sys.stderr.write(r.stdout + r.stderr)
         return obj
 
-    srcs = sources()
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
-    r = subprocess.run([nv] + ARCH + ["-shared", "-Xcompiler", "-pthread", "-o", tmp] + objs, capture_output=True,
-                       text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    srcs, bsrcs = sources(), sources(BENCH_SRC)
+    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs) + len(bsrcs))) as ex:
+        objs = list(ex.map(compile_one, srcs + bsrcs))
+    for lib, part in ((LIB, objs[:len(srcs)]), (BENCH_LIB, objs[len(srcs):])):
+        tmp = lib + f".tmp{os.getpid()}"
+        r = subprocess.run([nv] + ARCH + ["-shared", "-Xcompiler", "-pthread", "-o", tmp] + part, capture_output=True,
+                           text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, lib)
     return LIB
 
 

@@ -1,4 +1,8 @@
 // sf_microbench.cu -- roofline denominators measured on the device (no sketch arithmetic).
+//
+// Built into its own library (libsfbench.so), apart from the sketch library: the benchmark and the
+// bounded-wait failure test load it; nothing on the sketch path does.  It shares only the device
+// header's building blocks (barrier, CAS forms) with the sketch kernels, compiled here on their own.
 #include "sf_bench.h"
 #include "sf_internal.h"
 
@@ -83,8 +87,10 @@ sf_status sf_bench_grid_barrier(void* scratch_dev, uint32_t n_barriers, void* cu
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return SF_ERR_CUDA;
-    const int bps = sfk::chunk_update_blocks_per_sm(4);
-    if (bps <= 0) return SF_ERR_CUDA;
+    int bps = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, sfk::barrier_kernel, sfk::kChunkBlock, 0) != cudaSuccess ||
+        bps <= 0)
+        return SF_ERR_CUDA;
     if (cudaMemsetAsync(scratch_dev, 0, 256, st) != cudaSuccess) return SF_ERR_CUDA;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(sms * (bps < 2 ? bps : 2)));

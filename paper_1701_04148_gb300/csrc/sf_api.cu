@@ -265,6 +265,61 @@ sf_status sf_query_pipelined(const sf_slim_view* v, const void* keys_host, uint6
     return SF_OK;
 }
 
+sf_status sf_update_pipelined(sf_sketch* s, const void* keys_host, const int8_t* ops_host, int32_t op_const,
+                              uint64_t n, void* staging_dev, uint64_t staging_bytes, void* copy_stream) {
+    if (!s) return SF_ERR_INVALID;
+    if (n == 0) return SF_OK;
+    if (!keys_host || !staging_dev || (!ops_host && op_const != 1 && op_const != -1)) return SF_ERR_INVALID;
+    const uint64_t kb = s->p.key_bytes, per = kb + (ops_host ? 1u : 0u), S = s->p.chunk;
+    // a piece is a whole number of chunks that fits half of the staging buffer
+    const uint64_t chunks_per_piece = (staging_bytes / 2) / (S * per);
+    if (chunks_per_piece == 0) return SF_ERR_OOM;
+    const uint64_t piece = chunks_per_piece * S;
+    // the ops bytes of a half follow its keys, 16-byte aligned
+    const uint64_t keys_half = (piece * kb + 15) & ~15ull;
+    const uint64_t half = keys_half + (ops_host ? piece : 0);
+    if (2 * half > staging_bytes) return SF_ERR_OOM;
+    DeviceGuard guard(s->device);
+    if (!guard.ok) return SF_ERR_CUDA;
+    cudaStream_t cs = (cudaStream_t)copy_stream;
+    cudaEvent_t start = nullptr, copied[2] = {nullptr, nullptr}, used[2] = {nullptr, nullptr};
+    auto cleanup = [&]() {
+        for (cudaEvent_t e : {start, copied[0], copied[1], used[0], used[1]})
+            if (e) cudaEventDestroy(e);  // released once the work recorded on it has completed
+    };
+    if (cudaEventCreateWithFlags(&start, cudaEventDisableTiming) != cudaSuccess) return SF_ERR_CUDA;
+    for (int h = 0; h < 2; ++h)
+        if (cudaEventCreateWithFlags(&copied[h], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&used[h], cudaEventDisableTiming) != cudaSuccess) {
+            cleanup();
+            return SF_ERR_CUDA;
+        }
+    // the copies start after the sketch's earlier work (which may still read the staging buffer)
+    if (cudaEventRecord(start, s->stream) != cudaSuccess || cudaStreamWaitEvent(cs, start, 0) != cudaSuccess) {
+        cleanup();
+        return SF_ERR_CUDA;
+    }
+    sf_status st = SF_OK;
+    for (uint64_t off = 0, i = 0; off < n && st == SF_OK; off += piece, ++i) {
+        const uint64_t len = n - off < piece ? n - off : piece;
+        const int h = (int)(i & 1);
+        uint8_t* kd = (uint8_t*)staging_dev + (uint64_t)h * half;
+        int8_t* od = ops_host ? (int8_t*)(kd + keys_half) : nullptr;
+        if ((i >= 2 && cudaStreamWaitEvent(cs, used[h], 0) != cudaSuccess) ||
+            cudaMemcpyAsync(kd, (const uint8_t*)keys_host + off * kb, len * kb, cudaMemcpyHostToDevice, cs) !=
+                cudaSuccess ||
+            (od && cudaMemcpyAsync(od, ops_host + off, len, cudaMemcpyHostToDevice, cs) != cudaSuccess) ||
+            cudaEventRecord(copied[h], cs) != cudaSuccess || cudaStreamWaitEvent(s->stream, copied[h], 0) != cudaSuccess) {
+            st = SF_ERR_CUDA;
+            break;
+        }
+        st = run_update(s, kd, od, ops_host ? 0 : op_const, len);
+        if (st == SF_OK && cudaEventRecord(used[h], s->stream) != cudaSuccess) st = SF_ERR_CUDA;
+    }
+    cleanup();
+    return st;
+}
+
 sf_status sf_sync(sf_sketch* s) {
     if (!s) return SF_ERR_INVALID;
     uint32_t err = 0;

@@ -11,9 +11,9 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _declared_functions():
+def _declared_functions(header="sf.h"):
     names = set()
-    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+    for h in glob.glob(os.path.join(ROOT, "include", header)):
         text = open(h).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
         for m in re.finditer(r"^[A-Za-z_][\w \t\*]*?\b(sfc?_\w+)\s*\(", text, flags=re.M):
@@ -37,18 +37,26 @@ def test_header_declares_the_boundary():
         assert must in names
 
 
+def _exported(path):
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    return {ln.split()[-1] for ln in out.splitlines() if ln.strip()}
+
+
 def test_library_exports_every_declared_symbol(lib_path):
-    L = ctypes.CDLL(lib_path)
-    missing = [n for n in sorted(_declared_functions()) if not hasattr(L, n)]
-    assert not missing, f"declared in include/*.h but not exported: {missing}"
-    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True, text=True).stdout
-    exported = {ln.split()[-1] for ln in out.splitlines() if ln.strip()}
-    assert _declared_functions() <= exported
+    from paper_1701_04148_gb300 import build
+    for path, header in ((lib_path, "sf.h"), (build.BENCH_LIB, "sf_bench.h")):
+        L = ctypes.CDLL(path)
+        missing = [n for n in sorted(_declared_functions(header)) if not hasattr(L, n)]
+        assert not missing, f"declared in include/{header} but not exported by {os.path.basename(path)}: {missing}"
+        assert _declared_functions(header) <= _exported(path)
+    # the measurement kernels live only in the measurement library
+    assert not (_declared_functions("sf_bench.h") & _exported(lib_path))
 
 
 def test_binding_covers_the_header(lib_path):
     import paper_1701_04148_gb300 as sf
-    assert _declared_functions() <= set(sf.exported_symbols())
+    assert _declared_functions("sf.h") <= set(sf.exported_symbols())
+    assert _declared_functions("sf_bench.h") <= set(sf.exported_bench_symbols())
 
 
 def test_argument_checks_need_no_gpu(lib_path):

@@ -11,7 +11,7 @@ pytestmark = pytest.mark.gpu
 
 def test_barrier_wait_times_out_and_the_context_survives(sf):
     import torch
-    L = sf.load()
+    L = sf.load_bench()
     scratch = torch.zeros(64, dtype=torch.int32, device="cuda")
     st = torch.cuda.current_stream().cuda_stream
     assert L.sf_bench_wait_timeout(scratch.data_ptr(), 0, 20_000_000, st) == sf.SF_OK
@@ -27,7 +27,7 @@ def test_barrier_wait_times_out_and_the_context_survives(sf):
 
 def test_wait_limit_is_bounded_by_the_api(sf):
     import torch
-    L = sf.load()
+    L = sf.load_bench()
     scratch = torch.zeros(64, dtype=torch.int32, device="cuda")
     st = torch.cuda.current_stream().cuda_stream
     assert L.sf_bench_wait_timeout(scratch.data_ptr(), 1, 5_000_000_000, st) == sf.SF_ERR_INVALID

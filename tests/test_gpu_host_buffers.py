@@ -68,3 +68,36 @@ def test_pageable_host_memory_is_refused_before_launch(sf):
         import torch
         g.insert(torch.from_numpy(keys))             # the binding refuses it too
     assert g.sync_status() == sf.SF_OK               # nothing ran, nothing latched
+
+
+@pytest.mark.parametrize("kb,S,with_ops", [(13, 4096, False), (4, 1000, True), (8, 65536, True), (4, 1, False)])
+def test_pipelined_update_from_host_equals_one_call(sf, kb, S, with_ops):
+    """sf_update_pipelined: host keys copied in chunk-aligned pieces through a small staging buffer
+    (several pieces, both halves reused), overlapped with the updates, leave every counter equal to
+    one sf_update_batch call over the whole stream; deletions through op_const as well."""
+    import torch
+    if kb == 13:
+        ins, dels, _ = wl.flows_with_deletes(150_000, 20_000, 1.0, 0.1, seed=61)
+        calls = [(ins, None, 1), (dels, None, -1)]
+    else:
+        st, _ = wl.mixed_stream(150_000, 20_000, 1.0, 0.2 if with_ops else 0.0, kb, seed=62)
+        calls = [(st.keys, st.ops if with_ops else None, 1)]
+    a = sf.Sketch(4, 2000, 16, kb, 5, S)
+    b = sf.Sketch(4, 2000, 16, kb, 5, S)
+    per = kb + (1 if with_ops else 0)
+    staging = torch.empty(2 * (max(S, 7000) * per + 16) + 64, dtype=torch.uint8, device="cuda")
+    for keys, ops, op_const in calls:
+        kd = keys.cuda()
+        if ops is not None:
+            a.update(kd, ops.cuda())
+        elif op_const > 0:
+            a.insert(kd)
+        else:
+            a.delete(kd)
+        b.update_pipelined(_pinned(keys), _pinned(ops) if ops is not None else None, op_const, staging=staging)
+        a.sync()
+        b.sync()
+        assert torch.equal(a.fat, b.fat) and torch.equal(a.slim, b.slim)
+    with pytest.raises(sf.SFError) as ei:
+        b.update_pipelined(_pinned(calls[0][0]), None, 1, staging=torch.empty(16, dtype=torch.uint8, device="cuda"))
+    assert ei.value.status == sf.SF_ERR_OOM

@@ -368,3 +368,38 @@ def test_query_pipeline_splits_like_the_paper_and_matches(sf):
         for s_ in streams:
             s_.synchronize()
         assert np.array_equal(oh.numpy().view(np.uint32), want), n_streams
+
+
+@pytest.mark.parametrize("S", [1, 64, 4096])
+def test_correct_rate_bound_eq_cr_on_gpu(sf, S):
+    """Sec. 3.5, Eq. (cr), through the CUDA path: v items of frequencies 1..v over an error-free
+    Fat (explicit indices, no two items on one Fat counter), d = 3, w = 64.  The share of items the
+    GPU's Slim answers exactly is at least (1/v) sum_l [1 - (1 - (1 - 1/w)^(v-l))^d] (averaged over
+    trials, 0.02 slack); every counter also equals the oracle's (SEQ for S = 1, chunked otherwise;
+    with an error-free Fat both give each Slim counter its maximum true frequency, Sec. 3.5)."""
+    import torch
+    from tests.test_oracle_pins import _collision_free_fat_table
+    v, d, w, z = 120, 3, 64, 64
+    bound = np.mean([1 - (1 - (1 - 1 / w) ** (v - l)) ** d for l in range(1, v + 1)])
+    rates = []
+    for trial in range(12):
+        rng = np.random.default_rng(1000 + trial)
+        table = _collision_free_fat_table(rng, v, d, w, z)
+        ids = np.repeat(np.arange(v, dtype=np.uint32), np.arange(1, v + 1))
+        rng.shuffle(ids)
+        g = sf.Sketch(d, w, z, 4, 0, S, explicit_index=True)
+        g.set_index_table(torch.from_numpy(table.astype(np.int32)))
+        g.insert(torch.from_numpy(ids.astype(np.int32)).cuda())
+        slim, hdr = g.export_slim()
+        q = _np_u32(sf.query(slim, hdr, torch.arange(v, dtype=torch.int32, device="cuda"),
+                             index_table=g._index_table))
+        g.sync()
+        o = oracle.Sketch(d, w, z)
+        h, f, ident = oracle.explicit_indices(table, ids)
+        if S == 1:
+            o.seq_apply(h, f, np.ones(len(ids), np.int8))
+        else:
+            o.chunk_apply(h, f, np.ones(len(ids), np.int8), S, ident)
+        assert np.array_equal(_np_u32(g.slim_view()), o.A) and np.array_equal(_np_u32(g.fat_view()), o.B)
+        rates.append(float(np.mean(q == np.arange(1, v + 1))))
+    assert np.mean(rates) >= bound - 0.02
