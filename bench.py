@@ -137,7 +137,7 @@ def l2_random_peaks(L, dev, stream):
     return out
 
 
-CHUNK_KERNEL_SOURCES = ("sf_update.cu", "sf_device.cuh", "sf_internal.h")
+CHUNK_KERNEL_SOURCES = ("sf_update_kernels.cuh", "sf_update.cu", "sf_device.cuh", "sf_internal.h")
 
 
 def chunk_kernel_source_sha256():
@@ -148,10 +148,11 @@ def chunk_kernel_source_sha256():
     return h.hexdigest()
 
 
-def traffic_record():
-    """DRAM bytes per update of the chunk kernel from the committed ncu summary, if the kernel
-    sources have not changed since the counters were taken."""
-    p = os.path.join(ROOT, "profiles", "chunk_update_kernel_traffic.json")
+def traffic_record(name="chunk_single_kernel_traffic.json"):
+    """DRAM bytes per update of a chunk kernel from a committed ncu summary (the single-iteration
+    kernel's by default; chunk_update_kernel_traffic.json for the multi-iteration kernel), if the
+    kernel sources have not changed since the counters were taken."""
+    p = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(p):
         return None
     rec = json.load(open(p))
@@ -232,7 +233,7 @@ def main():
                     help="flows: skip the chunked-vs-sequential accuracy report (its one-at-a-time runs launch "
                          "thousands of kernels)")
     ap.add_argument("--workload", choices=["all", "flows", "batch", "serve", "accuracy", "pipeline", "profile",
-                                           "l2curve", "seq", "outofl2"],
+                                           "l2curve", "seq", "outofl2", "batchprof"],
                     default="all",
                     help="all: the flows line with the batched and serving results embedded; profile: the small "
                          "fixed case the committed ncu summaries capture (two insert launches, the second profiled)")
@@ -296,6 +297,8 @@ def main():
         line = run_pipeline(args, ctx)
     if args.workload == "profile":
         line = run_profile(args, ctx)
+    if args.workload == "batchprof":
+        line = run_batch_profile(args, ctx)
     if args.workload == "l2curve":
         line = run_l2curve(args, ctx)
     if args.workload in ("all", "outofl2"):
@@ -367,12 +370,18 @@ def run_flows(args, ctx):
         if pipelined:
             for idx, sk in enumerate(sketches):
                 sk.reset()
+            if evs is not None:
+                evs[0].record(stream)
             for idx, sk in enumerate(sketches):
                 sk.update_pipelined(host[idx][0], None, 1, staging=pipe[0], copy_stream=pipe[1])
                 sk.update_pipelined(host[idx][1], None, -1, staging=pipe[0], copy_stream=pipe[1])
+            if evs is not None:
+                evs[2].record(stream)
             hdrs = [sketches[idx].export_slim(slims[idx])[1] for idx in range(len(SWEEP))]
             for idx in range(len(SWEEP)):
                 sf.query(slims[idx], hdrs[idx], host[idx][2], out=host[idx][3], stream=stream)
+            if evs is not None:
+                evs[4].record(stream)
             return
         if host is not None and not direct:
             for idx in range(len(SWEEP)):
@@ -514,12 +523,15 @@ def run_flows(args, ctx):
             if dist is not None:
                 dist.barrier()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            pev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
             a.record(stream)
-            for _ in range(args.steps):
-                step(host=host, direct=direct, pipelined=pipelined)
+            for k in range(args.steps):
+                step(evs=pev[k], host=host, direct=direct, pipelined=pipelined)
             b.record(stream)
             torch.cuda.synchronize()
             ems = a.elapsed_time(b) / args.steps
+            upd_ms = sum(pev[k][0].elapsed_time(pev[k][2]) for k in range(args.steps)) / args.steps
+            rest_ms = sum(pev[k][2].elapsed_time(pev[k][4]) for k in range(args.steps)) / args.steps
             if dist is not None:
                 t = torch.tensor([ems], dtype=torch.float64, device=dev)
                 dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -527,7 +539,8 @@ def run_flows(args, ctx):
             for sk in sketches:
                 sk.sync()
             return {"value": round(world * ops_per_step / (ems / 1e3) / 1e6, 2), "unit": "M ops/s",
-                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ems, 3)}
+                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ems, 3),
+                    "update_ms_per_step": round(upd_ms, 3), "export_query_ms_per_step": round(rest_ms, 3)}
 
         e2e = timed_e2e(False, pipelined=True)
         e2e["transfer"] = ("sf_update_pipelined per sketch and call: pinned host keys copied in chunk-aligned "
@@ -735,6 +748,54 @@ def run_profile(args, ctx):
             "query_mean": float(q.to(torch.float64).mean())}
 
 
+def run_batch_profile(args, ctx):
+    """The small case of the batched update that ncu captures: one launch group of the many-sketch
+    batch (the first sketches of the 1,024-sketch plan, in order, whose counters fit the default
+    group budget of 3/4 of L2, as sf_batch_update groups them), chunks for R = 32 rounds, one launch
+    per call (group budget 0 on this subset).  A warm-up call, then the profiled call (launch index 1
+    of the chunk kernel)."""
+    import torch
+    import paper_1701_04148_gb300 as sf
+    from paper_1701_04148_gb300 import autotune
+    import workloads as wl
+    dev, stream = ctx["dev"], ctx["stream"]
+    plan = wl.many_sketch_plan(1024, seed=3)
+    budget = torch.cuda.get_device_properties(dev).L2_cache_size * 3 // 4
+    chunks_all = autotune.chunk_sizes([p["n"] for p in plan], 32)
+    group, used = [], 0
+    for p, c in zip(plan, chunks_all):
+        fb = 4 * p["w"] * 16 * 4 + 4 * p["w"] * 4 + c * 32  # Fat + Slim + the dictionary a chunk touches
+        if fb > budget:
+            continue
+        if used + fb > budget:
+            break
+        group.append((p, c))
+        used += fb
+    streams = []
+    for p, _ in group:
+        st, _ = wl.mixed_stream(p["n"], p["distinct"], p["s"], 0.1, 4, seed=p["seed"], device=dev)
+        streams.append((st.keys, st.ops))
+    sks = [sf.Sketch(4, p["w"], 16, 4, p["seed"], c, stream=stream) for p, c in group]
+    slots = sum((c + 31) // 32 * 32 for _, c in group)
+    b = sf.Batch(len(sks), graph=False, stream=stream, max_round_slots=slots, group_bytes=0)
+    items = [(sk, k, o) for sk, (k, o) in zip(sks, streams)]
+    b.update(items)
+    for sk in sks:
+        sk.reset()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.update(items)
+    e1.record(stream)
+    st = b.sync_status()
+    torch.cuda.synchronize()
+    if st != sf.SF_OK:
+        raise SystemExit(f"batch profile case failed: status {st}")
+    n = sum(p["n"] for p, _ in group)
+    ms = e0.elapsed_time(e1)
+    return {"workload": "batchprof", "sketches": len(group), "updates": n, "counter_bytes": used,
+            "round_slots": slots, "launch_ms": round(ms, 4), "M_updates_per_s": round(n / ms / 1e3, 1)}
+
+
 def run_seq(args, ctx):
     """The paper's one-at-a-time rule (chunk 1) on the insertion-only u32 workload: 100,000 keys
     Zipf(1.0) over 10,000 ids, d=4, w=4096, z=16; then all 10,000 ids queried.  GPU time of the
@@ -904,7 +965,7 @@ def run_outofl2(args, ctx):
     peaks, psrc = measured_peaks()
     achieved = alg_bytes / (t_upd / 1e3) / 1e9
     peaks_r = hbm_random_peaks(ctx["B"], dev, stream)
-    tr = traffic_record()
+    tr = traffic_record("chunk_update_kernel_traffic.json")
     traffic = None
     if tr is not None and "outofl2" in tr:
         rec = tr["outofl2"]
@@ -1248,6 +1309,31 @@ def run_batch(args, ctx):
     st_b = batch.sync_status()
     exact = all(torch.equal(a.fat, b.fat) and torch.equal(a.slim, b.slim) for a, b in zip(bsk, psk))
     info = batch.info()
+    # roofline of this rank's batched step: each update makes 4d random counter accesses (L2 ops; the
+    # launch groups keep each launch's counters within L2), against the 1:1 mix measured in this run;
+    # and its algorithmic HBM bytes (key 4 B + op 1 B + 4 B per counter access) against the copy peak
+    best = l2_random_peaks(ctx["B"], dev, stream)
+    ops_s = total * L2_OPS_PER_UPDATE / (tb / 1e3) / 1e9
+    tr = traffic_record("chunk_update_kernel_traffic.json")
+    traffic = None
+    if tr is not None and "c3_group" in tr and info["groups_last"]:
+        g = tr["c3_group"]
+        traffic = round(g["dram_bytes"] / g["updates"] * total / info["groups_last"])
+    roofline = {"bound": "l2", "kernel": "chunk_update_kernel", "achieved": round(ops_s, 2), "peak": round(best["mix"], 2),
+                "unit": "G random L2 ops/s", "frac": round(ops_s / best["mix"], 4),
+                "peak_red_only": round(best["red"], 2), "frac_of_red_only": round(ops_s / best["red"], 4),
+                "peak_load_only": round(best["ld"], 2), "frac_of_load_only": round(ops_s / best["ld"], 4),
+                "ops_per_update": L2_OPS_PER_UPDATE, "traffic": traffic,
+                "traffic_note": "DRAM bytes per launch: one launch group's application-replay capture "
+                                "(chunk_update_kernel_traffic.json, c3_group) scaled to this step's updates "
+                                "and launch groups",
+                "avg_launch_ms": round(tb / max(1, info["groups_last"]), 4)}
+    hbm_b = total * (4 + 1 + L2_OPS_PER_UPDATE * 4)
+    peaks, psrc = measured_peaks()
+    roofline_hbm = {"bound": "hbm", "achieved": round(hbm_b / (tb / 1e3) / 1e9, 1), "peak": peaks.get("hbm_gbs"),
+                    "unit": "GB/s", "frac": round(hbm_b / (tb / 1e3) / 1e9 / peaks.get("hbm_gbs", 1.0), 4),
+                    "note": f"algorithmic bytes = 4 B key + 1 B op + 4 B per counter access ({4 + 1 + 4 * L2_OPS_PER_UPDATE} "
+                            f"B per update); peak {psrc}"}
     out = {"workload": "batched-many-sketch", "metric": "M updates/s", "sketches": len(plan_all),
            "updates_per_step": total_all, "value": round(total_all / (tb / 1e3) / 1e6, 2), "unit": "M updates/s",
            "plain_value": round(total_all / (tp / 1e3) / 1e6, 2), "batched_vs_plain_speedup": round(tp / tb, 3),
@@ -1257,7 +1343,7 @@ def run_batch(args, ctx):
            "autotune_group": tuned["trials_group"], "autotune_best_rounds_bracketed": tuned["best_rounds_bracketed"],
            "autotune_rounds_skipped_for_memory": tuned["rounds_skipped_for_memory"],
            "sketch_bytes": autotune.sketch_bytes(ws, chunks, 4, 16),
-           "graph": info, "status": st_b,
+           "graph": info, "status": st_b, "roofline": roofline, "roofline_hbm": roofline_hbm,
            "launch_groups": {"groups": info["groups_last"], "group_bytes": info["group_bytes"],
                              "rule": "sketches whose counters fit the budget packed into L2-sized launch "
                                      "groups, larger ones share one launch"},

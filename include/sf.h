@@ -142,6 +142,15 @@ sf_status sf_create(const sf_params *p, void *fat_dev, void *slim_dev, void *scr
 sf_status sf_destroy(sf_sketch *s);
 
 /*
+ * Initialisation again on the same buffers (Sec. 3.1: all counters zero): zeroes the Fat, the Slim
+ * and the control words on the handle's stream, after its queued work.  The chunk dictionary is left
+ * as it is, because every update call leaves it zeroed (and sf_sync re-zeroes the whole scratch after
+ * SF_ERR_TIMEOUT); chunk-1 sketches also re-zero their one-at-a-time workspace.  Cheaper than a new
+ * handle when the dictionary is large (it reserves 512 B per chunk slot).
+ */
+sf_status sf_reset(sf_sketch *s);
+
+/*
  * Explicit-index mode (params.flags & SF_FLAG_EXPLICIT_INDEX): keys are uint32 ids and the
  * device table holds, for id q and row i, h_i = table[(q*d + i)*2], f_i = table[(q*d + i)*2 + 1]
  * (h_i < w, f_i < z).  Used to replay worked examples with hand-chosen indices (Sec. 3.2).

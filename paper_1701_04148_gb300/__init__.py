@@ -84,6 +84,7 @@ _SIGS = {
     "sf_create": (ctypes.c_int32, [ctypes.POINTER(Params), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
     "sf_destroy": (ctypes.c_int32, [ctypes.c_void_p]),
+    "sf_reset": (ctypes.c_int32, [ctypes.c_void_p]),
     "sf_set_index_table": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32]),
     "sf_insert_batch": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64]),
     "sf_delete_batch": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64]),
@@ -265,15 +266,8 @@ class Sketch:
         self._index_table = None
 
     def reset(self):
-        """Initialisation again (Sec. 3.1: all counters zero) on the same device buffers."""
-        self.close()
-        h = ctypes.c_void_p()
-        check(load().sf_create(ctypes.byref(self.params), self.fat.data_ptr(), self.slim.data_ptr(),
-                               self.scratch.data_ptr(), _stream_handle(self.stream), ctypes.byref(h)), "sf_create")
-        self.handle = h
-        if self._index_table is not None:
-            check(load().sf_set_index_table(self.handle, self._index_table.data_ptr(), self._index_table.shape[0]),
-                  "sf_set_index_table")
+        """Initialisation again (Sec. 3.1: all counters zero) on the same device buffers (sf_reset)."""
+        check(load().sf_reset(self.handle), "sf_reset")
 
     # shapes of the caller-visible views
     @property

@@ -166,6 +166,21 @@ sf_status sf_destroy(sf_sketch* s) {
     return SF_OK;
 }
 
+sf_status sf_reset(sf_sketch* s) {
+    if (!s) return SF_ERR_INVALID;
+    DeviceGuard guard(s->device);
+    if (!guard.ok) return SF_ERR_CUDA;
+    uint64_t fb = 0, sb = 0, xb = 0;
+    if (sf_required_bytes(&s->p, &fb, &sb, &xb) != SF_OK) return SF_ERR_INVALID;
+    // chunked sketches: control words only (the dictionary is zero between calls); chunk-1: all
+    const uint64_t scratch_bytes = s->p.chunk > 1 ? kCtrlBytes : xb;
+    if (cudaMemsetAsync(s->B, 0, fb, s->stream) != cudaSuccess || cudaMemsetAsync(s->A, 0, sb, s->stream) != cudaSuccess ||
+        cudaMemsetAsync(s->scratch, 0, scratch_bytes, s->stream) != cudaSuccess)
+        return SF_ERR_CUDA;
+    s->bar_epoch = 0;
+    return SF_OK;
+}
+
 sf_status sf_set_index_table(sf_sketch* s, const uint32_t* table_dev, uint32_t n_keys) {
     if (!s || !(s->p.flags & SF_FLAG_EXPLICIT_INDEX) || !table_dev) return SF_ERR_INVALID;
     s->idx_table = table_dev;

@@ -403,3 +403,22 @@ def test_correct_rate_bound_eq_cr_on_gpu(sf, S):
         assert np.array_equal(_np_u32(g.slim_view()), o.A) and np.array_equal(_np_u32(g.fat_view()), o.B)
         rates.append(float(np.mean(q == np.arange(1, v + 1))))
     assert np.mean(rates) >= bound - 0.02
+
+
+@pytest.mark.parametrize("S", [1, 4096, 65536])
+def test_reset_equals_a_fresh_sketch(sf, S):
+    """sf_reset (Sec. 3.1 initialisation on the same buffers) zeroes Fat, Slim and control words;
+    the dictionary left zeroed by the previous calls is reused: a reset sketch fed a stream ends
+    with exactly the counters of a fresh sketch fed the same stream (and of the oracle)."""
+    import torch
+    ins, dels, flows = wl.flows_with_deletes(120_000, 9_000, 1.1, 0.1, seed=71)
+    g = sf.Sketch(4, 3000, 16, 13, 4, S)
+    g.insert(ins.cuda())
+    g.delete(dels.cuda())
+    g.sync()
+    g.reset()
+    g.insert(ins[:70_000].cuda())
+    g.sync()
+    o = oracle.Sketch(4, 3000, 16, 13, 4)
+    o.update(ins[:70_000].numpy(), np.ones(70_000, np.int8), S=S)
+    _assert_same(g, o)
