@@ -121,7 +121,8 @@ const char *sf_status_str(sf_status s);
  *   fat_bytes     = d*w*z*4, layout B[((i*w + j)*z + k]  (bucket-contiguous, Sec. 3.4: all z
  *                   counters of a bucket sit together so one access reads them)
  *   slim_bytes    = d*w*4,   layout A[i*w + j]
- *   scratch_bytes = control words + the per-chunk key dictionary (grows with params.chunk);
+ *   scratch_bytes = control words + the per-chunk key dictionary: 32 B x a power of two
+ *                   >= 16*chunk slots for chunks up to 65,536, >= 8*chunk above;
  *                   sketches with chunk == 1 and w >= 1024 also hold the one-at-a-time
  *                   dependency-graph workspace (about (16 + 8d) * 512 KiB)
  * Any output pointer may be NULL.  Returns SF_ERR_INVALID for parameters out of range.
@@ -146,7 +147,7 @@ sf_status sf_destroy(sf_sketch *s);
  * and the control words on the handle's stream, after its queued work.  The chunk dictionary is left
  * as it is, because every update call leaves it zeroed (and sf_sync re-zeroes the whole scratch after
  * SF_ERR_TIMEOUT); chunk-1 sketches also re-zero their one-at-a-time workspace.  Cheaper than a new
- * handle when the dictionary is large (it reserves 512 B per chunk slot).
+ * handle when the dictionary is large (it reserves 256 to 1,024 B per chunk slot).
  */
 sf_status sf_reset(sf_sketch *s);
 

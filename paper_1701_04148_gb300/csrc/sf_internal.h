@@ -162,11 +162,15 @@ cudaError_t launch_seq_dag(const SketchDesc& s, const uint8_t* keys, uint64_t n,
 cudaError_t launch_query(const QueryArgs& a, int num_sms, cudaStream_t st);
 cudaError_t launch_multi_query(const MultiQueryArgs& a, int num_sms, cudaStream_t st);
 
-// Dictionary capacity: a power of two >= 16 S.  Each probe of the open-addressing table is one
-// 128-bit CAS round trip and a chunk waits for its slowest key, so the longest probe chain
-// matters: at load 1/4 it reaches ~11 slots over 65,536 keys, at load 1/16 ~5.
+// Dictionary capacity: a power of two >= 16 S for chunks of up to 65,536 updates, >= 8 S above.
+// Each probe of the open-addressing table is one 128-bit CAS round trip and a chunk waits for its
+// slowest key, so the longest probe chain matters: at load 1/4 it reaches ~11 slots over 65,536
+// keys, at load 1/16 ~5.  Larger chunks run many warp-iterations per round, which hide a longer
+// chain: there load 1/8 measured as fast as 1/16 (batches of 1,024 sketches at 16 and 32 rounds,
+// a 2^28-update stream in chunks of 2^20) with half the bytes, and 1/4 1-2 % slower.  Chunks of
+// up to 65,536 updates keep 16 S: the single-iteration kernel's two claim halves live in these bytes.
 inline uint32_t dict_capacity(uint32_t S) {
-    uint64_t need = 16ull * (uint64_t)S;
+    uint64_t need = (S > kClaimMaxChunk ? 8ull : 16ull) * (uint64_t)S;
     uint64_t cap = 64;
     while (cap < need) cap <<= 1;
     return (uint32_t)cap;

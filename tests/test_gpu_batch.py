@@ -131,6 +131,39 @@ def test_launch_shapes_give_the_same_sketches(sf, threads):
         sf.Batch(4, block_threads=384)
 
 
+def test_batch_rounds_at_the_single_iteration_boundary(sf):
+    """A batch whose rounds hold exactly one slot per worker lane of the grid (152 x 15 warps x 32 =
+    72,960 slots on a 152-SM GB300: the single-iteration kernel) and one warp of slots more (the
+    multi-iteration kernel): every sketch equals one sf_update_batch call and sampled sketches the
+    oracle."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    lanes = sms * (512 - 32)
+    for extra in (0, 32):
+        # ten sketches whose chunk sizes (multiples of 32) sum to lanes + extra
+        base = (lanes + extra) // 10 // 32 * 32
+        chunks = [base] * 9 + [lanes + extra - 9 * base]
+        plan = _plan(10, seed=51 + extra, w_log2=(9.0, 11.0), n_log10=(4.6, 5.0))
+        streams = _streams(plan)
+        bsk = [sf.Sketch(4, p["w"], 16, 4, p["seed"], c) for p, c in zip(plan, chunks)]
+        psk = [sf.Sketch(4, p["w"], 16, 4, p["seed"], c) for p, c in zip(plan, chunks)]
+        b = sf.Batch(len(plan), group_bytes=0)
+        b.update([(sk, st.keys, st.ops) for sk, (st, _) in zip(bsk, streams)])
+        for sk, (st, _) in zip(psk, streams):
+            sk.update(st.keys, st.ops)
+        assert b.sync() == sf.SF_OK
+        for sk in psk:
+            sk.sync()
+        for i in range(len(plan)):
+            assert torch.equal(bsk[i].fat, psk[i].fat) and torch.equal(bsk[i].slim, psk[i].slim), (extra, i)
+        for i in (0, 9):
+            p, (st, _) = plan[i], streams[i]
+            o = oracle.Sketch(4, p["w"], 16, 4, p["seed"])
+            o.update(st.keys.cpu().numpy(), st.ops.cpu().numpy(), S=chunks[i])
+            assert np.array_equal(bsk[i].slim.cpu().numpy().view(np.uint32).reshape(o.A.shape), o.A), (extra, i)
+            assert np.array_equal(bsk[i].fat.cpu().numpy().view(np.uint32).reshape(o.B.shape), o.B), (extra, i)
+
+
 def test_batch_with_13_byte_keys_and_empty_items(sf):
     import torch
     sks, items, refs = [], [], []

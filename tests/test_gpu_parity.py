@@ -422,3 +422,18 @@ def test_reset_equals_a_fresh_sketch(sf, S):
     o = oracle.Sketch(4, 3000, 16, 13, 4)
     o.update(ins[:70_000].numpy(), np.ones(70_000, np.int8), S=S)
     _assert_same(g, o)
+
+
+@pytest.mark.parametrize("S", [65_536, 65_537])
+def test_both_update_kernels_at_the_chunk_size_boundary(sf, S):
+    """S = 65,536 is the largest chunk of the single-iteration kernel (16-bit claim positions and
+    counts; the hot key of a Zipf-3 stream fills most of a chunk, so its counts approach that limit),
+    S = 65,537 runs the multi-iteration kernel: both equal the oracle, with ragged last chunks and a
+    mixed stream."""
+    ins, dels, flows = wl.flows_with_deletes(400_003, 40_000, 3.0, 0.1, seed=81)
+    g, o = _run_both(sf, 4, 1 << 12, 16, 13, 9, S, [(ins, None), (dels, "del")])
+    _assert_same(g, o)
+    _queries_match(sf, g, o, flows)
+    st, ids = wl.mixed_stream(300_001, 30_000, 1.2, 0.2, 8, seed=82)
+    g, o = _run_both(sf, 4, 5000, 16, 8, 9, S, [(st.keys, st.ops)])
+    _assert_same(g, o)

@@ -75,3 +75,29 @@ def test_same_seed_same_stream():
     c = wl.mixed_stream(5_000, 700, 1.0, 0.1, 4, seed=22)[0]
     assert torch.equal(a.keys, b.keys) and torch.equal(a.ops, b.ops)
     assert not torch.equal(a.keys, c.keys)
+
+
+def test_zipf_table_is_built_on_the_host():
+    """The Zipf table of a device stream equals the host table bit for bit (a device scan may
+    change the order of its partial sums between runs)."""
+    c = wl.zipf_cdf(1 << 16, 1.2, "cpu")
+    assert c.dtype == torch.float64 and float(c[-1]) == 1.0
+    assert bool((c[1:] >= c[:-1]).all())
+    k = torch.arange(1, (1 << 16) + 1, dtype=torch.float64)
+    assert torch.equal(c, torch.cumsum(k ** -1.2, 0) / torch.cumsum(k ** -1.2, 0)[-1])
+
+
+@pytest.mark.gpu
+def test_device_streams_repeat_for_a_seed():
+    """Two calls with one seed give the same device stream, at the size of the out-of-L2
+    workload's id table (2^26 ranks, many scan tiles)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    dev = torch.device("cuda", 0)
+    a, ta = wl.mixed_stream(1 << 22, 1 << 26, 1.2, 0.2, 8, seed=5, device=dev)
+    b, tb = wl.mixed_stream(1 << 22, 1 << 26, 1.2, 0.2, 8, seed=5, device=dev)
+    assert torch.equal(ta, tb)
+    assert torch.equal(a.keys, b.keys) and torch.equal(a.ops, b.ops)
+    g1, g2 = wl._gen(9, dev), wl._gen(9, dev)
+    assert torch.equal(wl.sample_ranks(1 << 20, 1 << 26, 0.99, g1, dev),
+                       wl.sample_ranks(1 << 20, 1 << 26, 0.99, g2, dev))

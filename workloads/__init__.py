@@ -3,7 +3,8 @@
 This module only draws random inputs (keys, +1/-1 operations, query sets).  It holds none
 of the sketch's arithmetic, so both the CUDA path and the CPU oracle may consume what it
 makes.  Everything is a torch tensor on the requested device; the same seed on the same
-device type gives the same stream.
+device type gives the same stream (every step is deterministic there: seeded draws, sorts,
+gathers; the one floating-point reduction, the Zipf table, runs on the host).
 
 Recipe (stand-ins for the paper's YCSB uniform/Zipf-0.99 traces and campus trace, Sec. 5.1,
 which are not available):
@@ -33,10 +34,13 @@ def _gen(seed: int, device) -> torch.Generator:
 
 
 def zipf_cdf(n: int, s: float, device="cpu") -> torch.Tensor:
-    k = torch.arange(1, n + 1, dtype=torch.float64, device=device)
+    """float64 cumulative Zipf(s) table over ranks 1..n, built on the host and then moved to
+    `device`: a scan on the GPU may add its partial sums in a different order from run to run,
+    which moves the table's last bits and, with them, some sampled ranks."""
+    k = torch.arange(1, n + 1, dtype=torch.float64)
     p = torch.pow(k, -float(s))
     c = torch.cumsum(p, 0)
-    return c / c[-1]
+    return (c / c[-1]).to(device)
 
 
 def sample_ranks(n_samples: int, n: int, s: float, g: torch.Generator, device="cpu",
