@@ -4,10 +4,12 @@
 // of its d Slim counters, min_i A_i[h_i(e)]; the Fat is never read.  The paper's GPU version
 // (Sec. 4.2) keeps all d arrays resident on the device and answers a batch per launch.
 //
-// Keys are read per thread (one aligned load for 4/8-byte keys, byte loads otherwise; L1 merges a
-// warp's byte loads into whole lines), several keys in flight per thread.  Staging a warp's 13-byte keys with 16-byte loads through
-// shared memory was measured no faster (37.6 against 37.1 us for 10^6 keys): the launch is bound
-// by the L2 requests of the d gathers per key, not by the key reads.
+// Keys are read per thread, several in flight: one aligned load for 4/8-byte keys, otherwise the
+// aligned 8-byte words covering the key (at most three loads; byte loads only where those words
+// would reach past either end of the caller's buffer).  Measured on 10^6 13-byte keys, back-to-back
+// launches: byte loads 23.0 us, word loads 22.4, word loads with the one-wave grid below 20.8.
+// Staging a warp's keys through shared memory with 16-byte loads was no faster than byte loads: its
+// byte reads from shared memory meet bank conflicts and cost as many L1 wavefronts.
 #include "sf_internal.h"
 
 namespace sfk {
@@ -22,6 +24,10 @@ namespace {
 // gather touches its own line), not by the chains.
 constexpr int kQueryKeys = 2;
 
+__device__ __forceinline__ Key query_key(const uint8_t* keys, uint64_t total_bytes, uint64_t t, uint32_t kb) {
+    return (kb == 4u || kb == 8u) ? load_key(keys, t, kb) : load_key_words(keys, total_bytes, t, kb);
+}
+
 template <int D>
 __global__ void __launch_bounds__(kQueryBlock) query_kernel(const QueryArgs q) {
     constexpr int K = kQueryKeys;
@@ -32,7 +38,7 @@ __global__ void __launch_bounds__(kQueryBlock) query_kernel(const QueryArgs q) {
 #pragma unroll
         for (int j = 0; j < K; ++j) {
             const uint64_t t = t0 + (uint64_t)j * stride;
-            k[j] = t < q.n ? load_key(q.keys, t, s.key_bytes) : Key{0ull, 0ull};
+            k[j] = t < q.n ? query_key(q.keys, q.n * s.key_bytes, t, s.key_bytes) : Key{0ull, 0ull};
         }
         uint32_t h[K][D], f[D];
         bool ok[K];
@@ -57,10 +63,20 @@ __global__ void __launch_bounds__(kQueryBlock) query_kernel(const QueryArgs q) {
     }
 }
 
+// The grid is one wave of resident blocks: the 13-byte form holds 40 registers (six blocks per
+// SM), and a fixed eight blocks per SM left a partial second wave (measured: 22.4 -> 20.8 us for
+// 10^6 13-byte keys, 269 -> 256 us for 2^24; capping registers at 32 spilled and ran slower).
 template <int D>
 cudaError_t launch_query_d(const QueryArgs& a, int num_sms, cudaStream_t st) {
+    static int resident = 0;  // blocks per SM, asked once per process and row count
+    if (resident == 0) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, query_kernel<D>, kQueryBlock, 0) != cudaSuccess)
+            return cudaGetLastError();
+        resident = nb > 0 ? nb : 1;
+    }
     const uint64_t want = (a.n + (uint64_t)kQueryBlock * kQueryKeys - 1) / ((uint64_t)kQueryBlock * kQueryKeys);
-    const uint64_t cap = (uint64_t)num_sms * 8;
+    const uint64_t cap = (uint64_t)num_sms * (uint64_t)resident;
     const unsigned grid = (unsigned)(want < cap ? want : cap);
     query_kernel<D><<<grid, kQueryBlock, 0, st>>>(a);
     return cudaGetLastError();
@@ -86,7 +102,7 @@ __global__ void __launch_bounds__(kQueryBlock) multi_query_kernel(const MultiQue
         s.key_bytes = r.key_bytes;
 #pragma unroll
         for (int i = 0; i < kMaxD; ++i) s.rs[i] = r.rs[i];
-        const Key k = load_key(q.keys + r.key_off, t - r.out_off, r.key_bytes);
+        const Key k = query_key(q.keys + r.key_off, (uint64_t)r.n * r.key_bytes, t - r.out_off, r.key_bytes);
         uint32_t h[kMaxD], f[kMaxD];
         uint64_t probe;
         key_indices<0>(s, k, h, f, &probe);
@@ -102,8 +118,15 @@ __global__ void __launch_bounds__(kQueryBlock) multi_query_kernel(const MultiQue
 
 cudaError_t launch_multi_query(const MultiQueryArgs& a, int num_sms, cudaStream_t st) {
     if (a.total == 0) return cudaSuccess;
+    static int resident = 0;  // one wave of resident blocks, as for query_kernel
+    if (resident == 0) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, multi_query_kernel, kQueryBlock, 0) != cudaSuccess)
+            return cudaGetLastError();
+        resident = nb > 0 ? nb : 1;
+    }
     const uint64_t want = (a.total + kQueryBlock - 1) / kQueryBlock;
-    const uint64_t cap = (uint64_t)num_sms * 8;
+    const uint64_t cap = (uint64_t)num_sms * (uint64_t)resident;
     const unsigned grid = (unsigned)(want < cap ? want : cap);
     multi_query_kernel<<<grid, kQueryBlock, 0, st>>>(a);
     return cudaGetLastError();

@@ -655,7 +655,8 @@ __device__ __forceinline__ void group_and_claim(const SketchRun& R, uint32_t* ct
         }
         if ((old >> 16) == fp) {
             // same fingerprint: the claimer's key is the update at its stored position of this chunk
-            const Key o = load_key(R.keys, base + (old & 0xFFFFu), kb);
+            const uint64_t t = base + (old & 0xFFFFu);
+            const Key o = (kb == 4u || kb == 8u) ? load_key(R.keys, t, kb) : load_key_words(R.keys, R.n * kb, t, kb);
             if (o.x0 == L.k.x0 && o.x1 == L.k.x1) {
                 atomicAdd(&E[slot].counts, ci | (cd << 16));
                 return;
@@ -711,12 +712,8 @@ __device__ __forceinline__ void stage_issue(const StageRange& g, uint32_t lane, 
 __device__ __forceinline__ Key stage_take(const StageRange& g, uint32_t nvalid, uint32_t kb, uint32_t lane,
                                           const uint4* stage) {
     Key k{0ull, 0ull};
-    if (lane < nvalid) {
-        const uint8_t* sb = reinterpret_cast<const uint8_t*>(stage) + (g.b0 - g.g0) + (uint64_t)lane * kb;
-        const uint32_t n0 = kb < 8 ? kb : 8;
-        for (uint32_t b = 0; b < n0; ++b) k.x0 |= (uint64_t)sb[b] << (8 * b);
-        for (uint32_t b = 8; b < kb; ++b) k.x1 |= (uint64_t)sb[b] << (8 * (b - 8));
-    }
+    // (b0 - g0) + lane * kb + kb <= 15 + 32 * 15: the covering words stay inside the 512-byte stage
+    if (lane < nvalid) k = key_from_stage(stage, (uint32_t)(g.b0 - g.g0) + lane * kb, kb);
     return k;
 }
 
