@@ -140,11 +140,39 @@ def l2_random_peaks(L, dev, stream):
 CHUNK_KERNEL_SOURCES = ("sf_update_kernels.cuh", "sf_update.cu", "sf_device.cuh", "sf_internal.h")
 
 
+def code_without_comments(text: str) -> str:
+    """C/C++/CUDA source with its comments removed and every run of whitespace made one space;
+    string and character literals (the kernels' inline PTX) are kept as they are."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def chunk_kernel_source_sha256():
-    """sha256 over the files the chunk kernel is compiled from, in CHUNK_KERNEL_SOURCES order."""
+    """sha256 over the code (comments and layout aside) of the files the chunk kernels are compiled
+    from, in CHUNK_KERNEL_SOURCES order: a traffic record stays valid across comment edits."""
     h = hashlib.sha256()
     for name in CHUNK_KERNEL_SOURCES:
-        h.update(open(os.path.join(ROOT, "paper_1701_04148_gb300", "csrc", name), "rb").read())
+        text = open(os.path.join(ROOT, "paper_1701_04148_gb300", "csrc", name), encoding="utf-8").read()
+        h.update(code_without_comments(text).encode())
+        h.update(b"\0")
     return h.hexdigest()
 
 

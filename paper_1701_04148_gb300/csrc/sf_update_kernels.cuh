@@ -573,16 +573,14 @@ __device__ __forceinline__ bool grid_barrier_overlapped(uint32_t* ctrl, unsigned
     return s_ok_ov != 0;
 }
 
-// Group the updates of one chunk (warp match, then the block merge when enabled) and claim each
-// distinct key's dictionary entry (in `E`, the chunk's half of the sketch's dictionary, claim_mask + 1
-// entries).  Leaders that find their key already claimed add their counts to its entry.  Runs
-// between a grid barrier's arrival and its wait: it touches no counter, only the chunk's half.
+// Group the updates of one chunk, in place in P (whose L holds the lane's hashed update): the warp
+// match, then the block merge when enabled.  Lanes left as leaders (P.lead) carry their group's
+// insert and delete counts.  Touches shared memory only, so it may run in either barrier window.
 template <int D, int B>
-__device__ __forceinline__ void group_and_claim(const SketchRun& R, uint32_t* ctrl, const LaneWork<D>& L, bool live,
-                                                uint32_t k, uint64_t base, uint32_t pos, ClaimEntry* E,
-                                                bool use_merge, MergeTable<B>& mt, uint32_t* s_act, uint32_t* s_lead,
-                                                uint32_t lane, Pending<D>& P) {
-    P.L = L;
+__device__ __forceinline__ void group_keys(const SketchRun& R, bool live, uint32_t k, bool use_merge,
+                                           MergeTable<B>& mt, uint32_t* s_act, uint32_t* s_lead, uint32_t lane,
+                                           Pending<D>& P) {
+    const LaneWork<D>& L = P.L;
     P.ci = P.cd = 0u;
     P.slot = kNoSlot;
     P.lead = false;
@@ -643,6 +641,17 @@ __device__ __forceinline__ void group_and_claim(const SketchRun& R, uint32_t* ct
     P.lead = true;
     P.ci = ci;
     P.cd = cd;
+}
+
+// Claim a leader's dictionary entry in `E`, the chunk's half of the sketch's dictionary (claim_mask + 1
+// entries); a leader that finds its key already claimed adds its counts to that entry.  Runs between
+// a grid barrier's arrival and its wait, once the previous round's second barrier has passed (that
+// half was cleared by the phase 2 two rounds back): it touches no counter.
+template <int D>
+__device__ __forceinline__ void claim_key(const SketchRun& R, uint32_t* ctrl, uint64_t base, uint32_t pos,
+                                          ClaimEntry* E, Pending<D>& P) {
+    if (!P.lead) return;
+    const LaneWork<D>& L = P.L;
     const uint32_t fp = 0x8000u | (uint32_t)(L.probe >> 49);  // 15 bits of the key's 64-bit probe
     const uint32_t mine = (fp << 16) | pos;
     const uint32_t kb = R.s.key_bytes;
@@ -658,7 +667,7 @@ __device__ __forceinline__ void group_and_claim(const SketchRun& R, uint32_t* ct
             const uint64_t t = base + (old & 0xFFFFu);
             const Key o = (kb == 4u || kb == 8u) ? load_key(R.keys, t, kb) : load_key_words(R.keys, R.n * kb, t, kb);
             if (o.x0 == L.k.x0 && o.x1 == L.k.x1) {
-                atomicAdd(&E[slot].counts, ci | (cd << 16));
+                atomicAdd(&E[slot].counts, P.ci | (P.cd << 16));
                 return;
             }
         }
@@ -793,35 +802,58 @@ __global__ void __launch_bounds__(B, 512 / B) chunk_single_kernel(const __grid_c
         }
         return lane < nv;
     };
-    // group and claim chunk r (its dictionary half r & 1); every worker thread takes part
-    auto claim_round = [&](uint64_t r, const LaneWork<D>& L, bool live, Pending<D>& P) {
+    // Where chunk c's grouping runs.  Its claims must wait for the round that clears its dictionary
+    // half, so they run in the first barrier window of round c - 1; its keys are loaded and hashed in
+    // the second window of round c - 2, and the grouping follows them there unless the block's last
+    // grouping found fewer than one leader per kDeferLeaders updates.  Such skewed rounds leave the
+    // first window idle (little phase-1 work) and make the grouping costly (merges on a few hot
+    // slots), so there it waits for the first window.  Measured on the single-sketch 13-byte Zipf
+    // sweep (per exponent 32 M inserts + 3.2 M deletes, same counters): grouping always in the first
+    // window 32.24 ms, always in the second 32.75, adaptive with kDeferLeaders 2 / 4 / 8: 31.90 /
+    // 32.25 / 32.37 (s = 1: 6.44 -> 6.13 ms).
+    constexpr uint32_t kDeferLeaders = 2;
+    __shared__ int s_defer;
+    // thread 32 between two worker barriers: the merge choice from the last grouping's counts (s_act
+    // updates, s_lead leaders), which it then resets for the grouping about to run
+    auto decide = [&]() {
+        s_use_merge = (s_act > 0u) ? (16u * (s_act - s_lead) >= s_act) : s_use_merge;
+        s_act = 0u;
+        s_lead = 0u;
+    };
+    auto group_round = [&](bool live, Pending<D>& G) {
         workers_sync<B>();
-        if (threadIdx.x == 32) {
-            s_use_merge = (s_act > 0u) ? (16u * (s_act - s_lead) >= s_act) : s_use_merge;
-            s_act = 0u;
-            s_lead = 0u;
-        }
+        if (threadIdx.x == 32) decide();
         workers_sync<B>();
-        group_and_claim<D, B>(R, a.ctrl, L, live, k, r * (uint64_t)R.S, (uint32_t)o,
-                           dict2 + (r & 1ull) * (R.claim_mask + 1ull), s_use_merge != 0, s_merge, &s_act, &s_lead,
-                           lane, P);
+        group_keys<D, B>(R, live, k, s_use_merge != 0, s_merge, &s_act, &s_lead, lane, G);
+    };
+    auto claim_round = [&](uint64_t r, Pending<D>& P) {
+        claim_key<D>(R, a.ctrl, r * (uint64_t)R.S, (uint32_t)o, dict2 + (r & 1ull) * (R.claim_mask + 1ull), P);
     };
 
     if (a.n_rounds == 0) return;
-    // chunk 0 is hashed and claimed before the first round; the counts other leaders add to its
-    // entries are read in its phase 2, behind round 0's first barrier
-    Pending<D> P;
+    // chunk 0 is hashed, grouped and claimed before the first round (the counts other leaders add to
+    // its entries are read in its phase 2, behind round 0's first barrier); chunk 1 is hashed and
+    // grouped
+    Pending<D> P;  // the chunk of the current round
     P.lead = false;
     P.slot = kNoSlot;
     P.ci = P.cd = 0u;
-    LaneWork<D> N;
-    bool n_live = false;
+    Pending<D> G;  // the next chunk: hashed, and grouped when g_done
+    G.lead = false;
+    G.slot = kNoSlot;
+    G.ci = G.cd = 0u;
+    bool n_live = false, g_done = false;  // g_done is the same in every worker thread of a block
     if (wib != 0) {
         fetch_round(0);
-        const bool live0 = hash_round(0, N);
+        const bool live0 = hash_round(0, P.L);
         if (a.n_rounds > 1) fetch_round(1);
-        claim_round(0, N, live0, P);
-        n_live = a.n_rounds > 1 ? hash_round(1, N) : false;
+        group_round(live0, P);
+        claim_round(0, P);
+        if (a.n_rounds > 1) {
+            n_live = hash_round(1, G.L);
+            group_round(n_live, G);
+            g_done = true;
+        }
     }
 
     for (uint64_t r = 0; r < a.n_rounds; ++r) {
@@ -859,9 +891,13 @@ __global__ void __launch_bounds__(B, 512 / B) chunk_single_kernel(const __grid_c
                 }
             }
         }
-        // ---- barrier 1; meanwhile the workers group and claim chunk r + 1 -----------------
+        // ---- barrier 1; meanwhile the workers claim chunk r + 1 (grouping it first if deferred) --
         if (!grid_barrier_overlapped(a.ctrl, target, a.timeout_ns, [&] {
-                if (r + 1 < a.n_rounds) claim_round(r + 1, N, n_live, P);
+                if (r + 1 < a.n_rounds) {
+                    if (!g_done) group_round(n_live, G);
+                    P = G;
+                    claim_round(r + 1, P);
+                }
             }))
             return;
         target += gridDim.x;
@@ -895,11 +931,16 @@ __global__ void __launch_bounds__(B, 512 / B) chunk_single_kernel(const __grid_c
             }
         }
 
-        // ---- barrier 2; meanwhile the workers load and hash chunk r + 2 -------------------
+        // ---- barrier 2; meanwhile the workers load, hash and (mostly) group chunk r + 2 ------
         if (!grid_barrier_overlapped(a.ctrl, target, a.timeout_ns, [&] {
                 if (r + 2 < a.n_rounds) {
                     fetch_round(r + 2);
-                    n_live = hash_round(r + 2, N);
+                    n_live = hash_round(r + 2, G.L);
+                    workers_sync<B>();
+                    if (threadIdx.x == 32) s_defer = s_act > 0u && (uint64_t)kDeferLeaders * s_lead < (uint64_t)s_act;
+                    workers_sync<B>();
+                    g_done = s_defer == 0;
+                    if (g_done) group_round(n_live, G);
                 }
             }))
             return;

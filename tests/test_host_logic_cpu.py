@@ -28,3 +28,17 @@ def test_autotuner_shape_and_group_choice_and_bracketing():
     assert not autotune.bracketed({8: 6.0, 16: 6.5, 1024: 6.6})
     assert autotune.ROUND_CANDIDATES[0] < 32 < autotune.ROUND_CANDIDATES[-1]
     assert set(autotune.BLOCK_CANDIDATES) == {512, 256, 128}
+
+
+def test_kernel_source_hash_ignores_comments_only():
+    """The bench keeps a committed traffic record only while the chunk kernels' code is unchanged:
+    the hash drops comments and layout, keeps string literals (inline PTX) and every code token."""
+    import bench
+    strip = bench.code_without_comments
+    a = 'int x = 1; // note\n/* block */ asm("ld.global.cg.u32 %0, [%1]; // not a comment");'
+    b = 'int  x = 1;\n\n// other note\nasm("ld.global.cg.u32 %0, [%1]; // not a comment");  /* */'
+    assert strip(a) == strip(b)
+    assert "// not a comment" in strip(a)
+    assert strip(a) != strip(a.replace("x = 1", "x = 2"))
+    assert strip('char c = \'"\'; int y; // "') == 'char c = \'"\'; int y;'
+    assert len(bench.chunk_kernel_source_sha256()) == 64
