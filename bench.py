@@ -387,15 +387,15 @@ def run_flows(args, ctx):
     # update launches plus a query per sketch
     launches_per_step = (2 if batched else 2 * len(SWEEP)) + len(SWEEP)
 
-    pipe = None  # (staging, copy stream) of the pipelined host form
+    pipe = None  # the sf.Pipeline of the pipelined host form
 
     def step(evs=None, host=None, direct=False, pipelined=False):
         """One step.  host: pinned host copies of the inputs (and answer buffers).  direct=False
         copies them to the device first and the answers back; direct=True hands the pinned host
         buffers to the same calls, and the kernels read the keys and write the answers over the
-        host link themselves; pipelined=True updates each sketch through sf_update_pipelined (host
-        keys copied in chunk-aligned pieces, overlapped with the updates) and queries with the host
-        keys and answers directly."""
+        host link themselves; pipelined=True updates each sketch through one sf_update_pipeline
+        pipeline kept across the step (host keys copied in chunk-aligned pieces, overlapped with
+        the updates and across calls) and queries with the host keys and answers directly."""
         src, out = inputs, answers
         if pipelined:
             for idx, sk in enumerate(sketches):
@@ -403,8 +403,8 @@ def run_flows(args, ctx):
             if evs is not None:
                 evs[0].record(stream)
             for idx, sk in enumerate(sketches):
-                sk.update_pipelined(host[idx][0], None, 1, staging=pipe[0], copy_stream=pipe[1])
-                sk.update_pipelined(host[idx][1], None, -1, staging=pipe[0], copy_stream=pipe[1])
+                sk.update_through(pipe, host[idx][0], None, 1)
+                sk.update_through(pipe, host[idx][1], None, -1)
             if evs is not None:
                 evs[2].record(stream)
             hdrs = [sketches[idx].export_slim(slims[idx])[1] for idx in range(len(SWEEP))]
@@ -545,7 +545,7 @@ def run_flows(args, ctx):
         h2d = sum(h[0].numel() + h[1].numel() + h[2].numel() for h in host)
         d2h = sum(h[3].numel() * 4 for h in host)
 
-        pipe = (torch.empty(2 * ((1 << 22) * KB + 16), dtype=torch.uint8, device=dev), torch.cuda.Stream(device=dev))
+        pipe = sf.Pipeline(staging_bytes=2 * ((1 << 22) * KB + 16), device=dev)
 
         def timed_e2e(direct, pipelined=False):
             step(host=host, direct=direct, pipelined=pipelined)
@@ -568,6 +568,7 @@ def run_flows(args, ctx):
                 ems = float(t.item())
             for sk in sketches:
                 sk.sync()
+            pipe.release_inputs()
             return {"value": round(world * ops_per_step / (ems / 1e3) / 1e6, 2), "unit": "M ops/s",
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ems, 3),
                     "update_ms_per_step": round(upd_ms, 3), "export_query_ms_per_step": round(rest_ms, 3)}
@@ -609,10 +610,11 @@ def run_flows(args, ctx):
             return r
 
         e2e = median_rep("pipelined")
-        e2e["transfer"] = ("sf_update_pipelined per sketch and call: pinned host keys copied in chunk-aligned "
-                           "pieces of 2^22 keys into two staging halves on a copy stream, overlapped with the "
-                           "updates; the query kernel reads the pinned flow keys and writes the answers to "
-                           "pinned host memory")
+        e2e["transfer"] = ("sf_update_pipeline per sketch and call through one pipeline kept across the "
+                           "step: pinned host keys copied in chunk-aligned pieces of 2^22 keys into two "
+                           "alternating staging halves on a copy stream, overlapped with the updates, each "
+                           "call's first copy with the previous call's last update; the query kernel reads "
+                           "the pinned flow keys and writes the answers to pinned host memory")
         e2e["measurement"] = ("median of three repetitions of --steps steps, the three forms interleaved; "
                               "link_GBps_before_each: a plain 416 MB pinned host-to-device copy timed just "
                               "before each repetition")

@@ -227,6 +227,32 @@ sf_status sf_update_pipelined(sf_sketch *s, const void *keys_host, const int8_t 
                               uint64_t n, void *staging_dev, uint64_t staging_bytes, void *copy_stream);
 
 /*
+ * The same pipeline kept across calls (Sec. 4.2.2's overlap of copies and kernels, carried from
+ * one call to the next).  A pipeline owns a staging buffer's two halves and, per half, the event of
+ * the last update that read it.  A call's first piece then goes into the half the previous call did
+ * not end on and waits only for the last update that read that half -- not for all of the sketch's
+ * earlier work, as sf_update_pipelined does -- so successive calls, on one sketch or on several
+ * sketches sharing the pipeline, overlap each call's first copy with the previous call's last
+ * update.
+ *   sf_pipeline_create: staging_dev: 16-byte aligned device memory of staging_bytes (>= 64) that the
+ *     pipeline uses alone until every update through it has completed (sf_sync of each sketch);
+ *     copy_stream: a cudaStream_t on which no sketch using the pipeline updates.  The pipeline
+ *     belongs to the current device.  SF_ERR_INVALID for a bad argument, SF_ERR_CUDA if its events
+ *     cannot be created.
+ *   sf_update_pipeline: the pieces and results of sf_update_pipelined (equal to one
+ *     sf_update_batch call over the n updates); a piece is the whole number of the sketch's chunks
+ *     that fits half the staging, SF_ERR_OOM when not even one chunk does.  Asynchronous like
+ *     sf_update_pipelined.  One host thread at a time may use a pipeline.
+ *   sf_pipeline_destroy: releases the pipeline (its events go once their work has completed); the
+ *     staging stays the caller's.
+ */
+typedef struct sf_pipeline sf_pipeline;
+sf_status sf_pipeline_create(void *staging_dev, uint64_t staging_bytes, void *copy_stream, sf_pipeline **out);
+sf_status sf_update_pipeline(sf_sketch *s, sf_pipeline *p, const void *keys_host, const int8_t *ops_host,
+                             int32_t op_const, uint64_t n);
+sf_status sf_pipeline_destroy(sf_pipeline *p);
+
+/*
  * ---- Batched many-sketch update --------------------------------------------------------------
  * Monitoring nodes each fill their own sketch (Sec. 1.1); a collector-side or node-side host may
  * hold thousands of them.  The paper updates one sketch at a time; a batch applies one call's

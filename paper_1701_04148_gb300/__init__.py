@@ -106,6 +106,11 @@ _SIGS = {
     "sf_batch_sync": (ctypes.c_int32, [ctypes.c_void_p]),
     "sf_batch_set_group_bytes": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64]),
     "sf_batch_set_block_threads": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint32]),
+    "sf_pipeline_create": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
+                                            ctypes.POINTER(ctypes.c_void_p)]),
+    "sf_update_pipeline": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_int32, ctypes.c_uint64]),
+    "sf_pipeline_destroy": (ctypes.c_int32, [ctypes.c_void_p]),
     "sf_batch_groups": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32),
                                          ctypes.POINTER(ctypes.c_uint64)]),
     "sf_batch_info": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32),
@@ -333,6 +338,19 @@ class Sketch:
                                          op_const, n, _dev_ptr(staging, "staging"), staging.numel(),
                                          int(copy_stream.cuda_stream)), "sf_update_pipelined")
 
+    def update_through(self, pipe: "Pipeline", keys_host, ops_host=None, op_const: int = 1):
+        """sf_update_pipeline: host keys (pinned CPU tensor) through a Pipeline kept across calls and
+        sketches; keep keys_host (and ops_host) alive until sync()."""
+        k, n = self._keys(keys_host)
+        if not k.is_pinned() or (ops_host is not None and not ops_host.is_pinned()):
+            raise ValueError("keys_host and ops_host must be pinned CPU tensors")
+        if ops_host is not None and ops_host.numel() != n:
+            raise ValueError("ops must have one entry per key")
+        pipe._inputs.append((k, ops_host))
+        check(load().sf_update_pipeline(self.handle, pipe.handle, k.data_ptr(),
+                                        ops_host.data_ptr() if ops_host is not None else 0, op_const, n),
+              "sf_update_pipeline")
+
     def sync(self) -> int:
         return check(load().sf_sync(self.handle), "sf_sync")
 
@@ -352,6 +370,38 @@ class Sketch:
     def close(self):
         if getattr(self, "handle", None):
             load().sf_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Pipeline:
+    """sf_pipeline: a device staging buffer and a copy stream kept across sf_update_pipeline calls, on
+    one sketch or several (the first copy of a call overlaps the previous call's last update)."""
+
+    def __init__(self, staging_bytes: int = 2 * ((1 << 22) * 16 + 16), copy_stream=None, device=None):
+        torch = _torch()
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        with torch.cuda.device(self.device):
+            self.staging = torch.empty(int(staging_bytes), dtype=torch.uint8, device=self.device)
+            self.copy_stream = copy_stream if copy_stream is not None else torch.cuda.Stream(device=self.device)
+            h = ctypes.c_void_p()
+            check(load().sf_pipeline_create(self.staging.data_ptr(), self.staging.numel(),
+                                            int(self.copy_stream.cuda_stream), ctypes.byref(h)), "sf_pipeline_create")
+        self.handle = h
+        self._inputs = []  # host tensors of calls in flight (dropped by release_inputs after a sync)
+
+    def release_inputs(self):
+        """Forget the host inputs of earlier calls (call after the sketches that used them synced)."""
+        self._inputs = []
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().sf_pipeline_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

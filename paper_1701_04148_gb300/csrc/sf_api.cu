@@ -280,59 +280,129 @@ sf_status sf_query_pipelined(const sf_slim_view* v, const void* keys_host, uint6
     return SF_OK;
 }
 
+}  // extern "C"
+
+// Two alternating halves of a staging buffer with, per half, the event of its last copy and of the
+// last update that read it.
+struct sf_pipeline {
+    uint8_t* staging = nullptr;
+    uint64_t half_bytes = 0;  // 16-byte multiple
+    cudaStream_t cs = nullptr;
+    int device = 0;
+    cudaEvent_t copied[2] = {nullptr, nullptr}, used[2] = {nullptr, nullptr};
+    bool used_recorded[2] = {false, false};
+    int next = 0;  // the half the next piece goes to
+};
+
+namespace {
+
+void pipeline_release(sf_pipeline* p) {
+    for (cudaEvent_t e : {p->copied[0], p->copied[1], p->used[0], p->used[1]})
+        if (e) cudaEventDestroy(e);  // released once the work recorded on it has completed
+    delete p;
+}
+
+sf_status pipeline_init(sf_pipeline* p, void* staging_dev, uint64_t staging_bytes, void* copy_stream) {
+    p->staging = (uint8_t*)staging_dev;
+    p->half_bytes = (staging_bytes / 2) & ~15ull;
+    p->cs = (cudaStream_t)copy_stream;
+    if (cudaGetDevice(&p->device) != cudaSuccess) return SF_ERR_CUDA;
+    for (int h = 0; h < 2; ++h)
+        if (cudaEventCreateWithFlags(&p->copied[h], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&p->used[h], cudaEventDisableTiming) != cudaSuccess)
+            return SF_ERR_CUDA;
+    return SF_OK;
+}
+
+// The pieces of one call: whole chunks that fit a half (keys, then the operations 16-byte aligned),
+// each copied on the pipeline's copy stream once the last update that read its half is done, and
+// applied on the sketch's stream once it has landed.
+sf_status pipeline_run(sf_sketch* s, sf_pipeline* p, const void* keys_host, const int8_t* ops_host, int32_t op_const,
+                       uint64_t n) {
+    const uint64_t kb = s->p.key_bytes, per = kb + (ops_host ? 1u : 0u), S = s->p.chunk;
+    const uint64_t chunks_per_piece = p->half_bytes > 16 ? (p->half_bytes - 16) / (S * per) : 0;
+    if (chunks_per_piece == 0) return SF_ERR_OOM;
+    const uint64_t piece = chunks_per_piece * S;
+    const uint64_t keys_half = (piece * kb + 15) & ~15ull;  // the operations of a half follow its keys
+    for (uint64_t off = 0; off < n;) {
+        const uint64_t len = n - off < piece ? n - off : piece;
+        const int h = p->next;
+        uint8_t* kd = p->staging + (uint64_t)h * p->half_bytes;
+        int8_t* od = ops_host ? (int8_t*)(kd + keys_half) : nullptr;
+        if ((p->used_recorded[h] && cudaStreamWaitEvent(p->cs, p->used[h], 0) != cudaSuccess) ||
+            cudaMemcpyAsync(kd, (const uint8_t*)keys_host + off * kb, len * kb, cudaMemcpyHostToDevice, p->cs) !=
+                cudaSuccess ||
+            (od && cudaMemcpyAsync(od, ops_host + off, len, cudaMemcpyHostToDevice, p->cs) != cudaSuccess) ||
+            cudaEventRecord(p->copied[h], p->cs) != cudaSuccess ||
+            cudaStreamWaitEvent(s->stream, p->copied[h], 0) != cudaSuccess)
+            return SF_ERR_CUDA;
+        const sf_status st = run_update(s, kd, od, ops_host ? 0 : op_const, len);
+        if (st != SF_OK) return st;
+        if (cudaEventRecord(p->used[h], s->stream) != cudaSuccess) return SF_ERR_CUDA;
+        p->used_recorded[h] = true;
+        p->next = h ^ 1;
+        off += len;
+    }
+    return SF_OK;
+}
+
+bool pipeline_args_ok(const void* keys_host, const int8_t* ops_host, int32_t op_const) {
+    return keys_host && (ops_host || op_const == 1 || op_const == -1);
+}
+
+}  // namespace
+
+extern "C" {
+
 sf_status sf_update_pipelined(sf_sketch* s, const void* keys_host, const int8_t* ops_host, int32_t op_const,
                               uint64_t n, void* staging_dev, uint64_t staging_bytes, void* copy_stream) {
     if (!s) return SF_ERR_INVALID;
     if (n == 0) return SF_OK;
-    if (!keys_host || !staging_dev || (!ops_host && op_const != 1 && op_const != -1)) return SF_ERR_INVALID;
-    const uint64_t kb = s->p.key_bytes, per = kb + (ops_host ? 1u : 0u), S = s->p.chunk;
-    // a piece is a whole number of chunks that fits half of the staging buffer
-    const uint64_t chunks_per_piece = (staging_bytes / 2) / (S * per);
-    if (chunks_per_piece == 0) return SF_ERR_OOM;
-    const uint64_t piece = chunks_per_piece * S;
-    // the ops bytes of a half follow its keys, 16-byte aligned
-    const uint64_t keys_half = (piece * kb + 15) & ~15ull;
-    const uint64_t half = keys_half + (ops_host ? piece : 0);
-    if (2 * half > staging_bytes) return SF_ERR_OOM;
+    if (!staging_dev || !pipeline_args_ok(keys_host, ops_host, op_const)) return SF_ERR_INVALID;
     DeviceGuard guard(s->device);
     if (!guard.ok) return SF_ERR_CUDA;
-    cudaStream_t cs = (cudaStream_t)copy_stream;
-    cudaEvent_t start = nullptr, copied[2] = {nullptr, nullptr}, used[2] = {nullptr, nullptr};
-    auto cleanup = [&]() {
-        for (cudaEvent_t e : {start, copied[0], copied[1], used[0], used[1]})
-            if (e) cudaEventDestroy(e);  // released once the work recorded on it has completed
-    };
-    if (cudaEventCreateWithFlags(&start, cudaEventDisableTiming) != cudaSuccess) return SF_ERR_CUDA;
-    for (int h = 0; h < 2; ++h)
-        if (cudaEventCreateWithFlags(&copied[h], cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&used[h], cudaEventDisableTiming) != cudaSuccess) {
-            cleanup();
-            return SF_ERR_CUDA;
-        }
-    // the copies start after the sketch's earlier work (which may still read the staging buffer)
-    if (cudaEventRecord(start, s->stream) != cudaSuccess || cudaStreamWaitEvent(cs, start, 0) != cudaSuccess) {
-        cleanup();
-        return SF_ERR_CUDA;
-    }
-    sf_status st = SF_OK;
-    for (uint64_t off = 0, i = 0; off < n && st == SF_OK; off += piece, ++i) {
-        const uint64_t len = n - off < piece ? n - off : piece;
-        const int h = (int)(i & 1);
-        uint8_t* kd = (uint8_t*)staging_dev + (uint64_t)h * half;
-        int8_t* od = ops_host ? (int8_t*)(kd + keys_half) : nullptr;
-        if ((i >= 2 && cudaStreamWaitEvent(cs, used[h], 0) != cudaSuccess) ||
-            cudaMemcpyAsync(kd, (const uint8_t*)keys_host + off * kb, len * kb, cudaMemcpyHostToDevice, cs) !=
-                cudaSuccess ||
-            (od && cudaMemcpyAsync(od, ops_host + off, len, cudaMemcpyHostToDevice, cs) != cudaSuccess) ||
-            cudaEventRecord(copied[h], cs) != cudaSuccess || cudaStreamWaitEvent(s->stream, copied[h], 0) != cudaSuccess) {
-            st = SF_ERR_CUDA;
-            break;
-        }
-        st = run_update(s, kd, od, ops_host ? 0 : op_const, len);
-        if (st == SF_OK && cudaEventRecord(used[h], s->stream) != cudaSuccess) st = SF_ERR_CUDA;
-    }
-    cleanup();
+    sf_pipeline* p = new (std::nothrow) sf_pipeline();
+    if (!p) return SF_ERR_OOM;
+    sf_status st = pipeline_init(p, staging_dev, staging_bytes, copy_stream);
+    // the staging may still be read by the sketch's earlier work: the first copy waits for all of it
+    if (st == SF_OK && (cudaEventRecord(p->used[1], s->stream) != cudaSuccess ||
+                        cudaStreamWaitEvent(p->cs, p->used[1], 0) != cudaSuccess))
+        st = SF_ERR_CUDA;
+    if (st == SF_OK) st = pipeline_run(s, p, keys_host, ops_host, op_const, n);
+    pipeline_release(p);
     return st;
+}
+
+sf_status sf_pipeline_create(void* staging_dev, uint64_t staging_bytes, void* copy_stream, sf_pipeline** out) {
+    if (!out) return SF_ERR_INVALID;
+    *out = nullptr;
+    if (!staging_dev || !aligned16(staging_dev) || staging_bytes < 64) return SF_ERR_INVALID;
+    sf_pipeline* p = new (std::nothrow) sf_pipeline();
+    if (!p) return SF_ERR_OOM;
+    const sf_status st = pipeline_init(p, staging_dev, staging_bytes, copy_stream);
+    if (st != SF_OK) {
+        pipeline_release(p);
+        return st;
+    }
+    *out = p;
+    return SF_OK;
+}
+
+sf_status sf_pipeline_destroy(sf_pipeline* p) {
+    if (!p) return SF_ERR_INVALID;
+    DeviceGuard guard(p->device);
+    pipeline_release(p);
+    return SF_OK;
+}
+
+sf_status sf_update_pipeline(sf_sketch* s, sf_pipeline* p, const void* keys_host, const int8_t* ops_host,
+                             int32_t op_const, uint64_t n) {
+    if (!s || !p) return SF_ERR_INVALID;
+    if (n == 0) return SF_OK;
+    if (!pipeline_args_ok(keys_host, ops_host, op_const) || p->device != s->device) return SF_ERR_INVALID;
+    DeviceGuard guard(s->device);
+    if (!guard.ok) return SF_ERR_CUDA;
+    return pipeline_run(s, p, keys_host, ops_host, op_const, n);
 }
 
 sf_status sf_sync(sf_sketch* s) {

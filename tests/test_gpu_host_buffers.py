@@ -101,3 +101,45 @@ def test_pipelined_update_from_host_equals_one_call(sf, kb, S, with_ops):
     with pytest.raises(sf.SFError) as ei:
         b.update_pipelined(_pinned(calls[0][0]), None, 1, staging=torch.empty(16, dtype=torch.uint8, device="cuda"))
     assert ei.value.status == sf.SF_ERR_OOM
+
+
+@pytest.mark.gpu
+def test_pipeline_kept_across_calls_and_sketches(sf):
+    """sf_update_pipeline: one pipeline (small staging: several pieces per call) serves calls of two
+    sketches of different key widths and chunk sizes, on two streams, with no sync between calls;
+    every counter equals the device-resident calls'.  A chunk larger than half the staging is
+    SF_ERR_OOM; a misaligned staging buffer is refused."""
+    import torch
+    ins, dels, _ = wl.flows_with_deletes(120_000, 15_000, 1.0, 0.1, seed=71)
+    st8, _ = wl.mixed_stream(150_000, 20_000, 1.2, 0.2, 8, seed=72)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    a1, b1 = sf.Sketch(4, 3001, 16, 13, 5, 4096), sf.Sketch(4, 3001, 16, 13, 5, 4096, stream=s1)
+    a2, b2 = sf.Sketch(3, 2000, 8, 8, 9, 9000), sf.Sketch(3, 2000, 8, 8, 9, 9000, stream=s2)
+    pipe = sf.Pipeline(staging_bytes=2 * (20_000 * 9 + 16))
+    half = st8.keys.shape[0] // 2
+    calls = [(a1, b1, ins, None, 1), (a2, b2, st8.keys[:half], st8.ops[:half], 1), (a1, b1, dels, None, -1),
+             (a2, b2, st8.keys[half:], st8.ops[half:], 1)]
+    for a, b, keys, ops, op_const in calls:
+        kd = keys.contiguous().cuda()
+        if ops is not None:
+            a.update(kd, ops.contiguous().cuda())
+        elif op_const > 0:
+            a.insert(kd)
+        else:
+            a.delete(kd)
+        b.update_through(pipe, _pinned(keys.contiguous()), _pinned(ops.contiguous()) if ops is not None else None,
+                         op_const)
+    for s in (a1, a2, b1, b2):
+        s.sync()
+    assert torch.equal(a1.fat, b1.fat) and torch.equal(a1.slim, b1.slim)
+    assert torch.equal(a2.fat, b2.fat) and torch.equal(a2.slim, b2.slim)
+    pipe.release_inputs()
+    big = sf.Sketch(4, 2000, 16, 13, 5, 65536)
+    with pytest.raises(sf.SFError) as ei:
+        big.update_through(pipe, _pinned(ins[:70_000].contiguous()))
+    assert ei.value.status == sf.SF_ERR_OOM
+    pipe.close()
+    L = sf.load()
+    buf = torch.empty(4096, dtype=torch.uint8, device="cuda")
+    h = ctypes.c_void_p()
+    assert L.sf_pipeline_create(buf.data_ptr() + 8, 1024, 0, ctypes.byref(h)) == sf.SF_ERR_INVALID
