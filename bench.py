@@ -821,8 +821,8 @@ def run_batch_profile(args, ctx):
     batch (the first sketches of the 1,024-sketch plan, in order, whose counters fit the default
     group budget of 3/4 of L2, as sf_batch_update groups them), chunks for R = --batchprof-rounds
     rounds (16 by default, what the autotuner picks for this batch on a GB300), one launch per call
-    (group budget 0 on this subset).  A warm-up call, then the profiled call (launch index 1 of the
-    chunk kernel)."""
+    (group budget 0 on this subset), dictionaries in an arena.  A warm-up call, then the profiled call
+    (launch index 1 of the chunk kernel)."""
     import torch
     import paper_1701_04148_gb300 as sf
     from paper_1701_04148_gb300 import autotune
@@ -844,9 +844,11 @@ def run_batch_profile(args, ctx):
     for p, _ in group:
         st, _ = wl.mixed_stream(p["n"], p["distinct"], p["s"], 0.1, 4, seed=p["seed"], device=dev)
         streams.append((st.keys, st.ops))
-    sks = [sf.Sketch(4, p["w"], 16, 4, p["seed"], c, stream=stream) for p, c in group]
+    sks = [sf.Sketch(4, p["w"], 16, 4, p["seed"], c, stream=stream, shared_dict=True) for p, c in group]
     slots = sum((c + 31) // 32 * 32 for _, c in group)
-    b = sf.Batch(len(sks), graph=False, stream=stream, max_round_slots=slots, group_bytes=0)
+    # the dictionaries in an arena, as the bench's batched step has them (one launch: they fit)
+    arena = sum(sf.dictionary_bytes(4, p["w"], 16, 4, p["seed"], c) for p, c in group)
+    b = sf.Batch(len(sks), graph=False, stream=stream, max_round_slots=slots, group_bytes=0, dict_arena_bytes=arena)
     items = [(sk, k, o) for sk, (k, o) in zip(sks, streams)]
     b.update(items)
     for sk in sks:
@@ -1355,18 +1357,30 @@ def run_batch(args, ctx):
     ws = [p["w"] for p in plan]
     total = sum(ns)
 
+    # SF_FLAG_SHARED_DICT sketches: the batch's launch groups, which run one after another, reuse one
+    # dictionary arena (1/32 of device memory), and the plain per-sketch calls, one after another on
+    # one stream, reuse one dictionary buffer
+    arena_bytes = torch.cuda.get_device_properties(dev).total_memory // 32
+
     def make(chunks):
-        return [sf.Sketch(4, w, 16, 4, p["seed"], S, stream=stream) for w, p, S in zip(ws, plan, chunks)]
+        return [sf.Sketch(4, w, 16, 4, p["seed"], S, stream=stream, shared_dict=True)
+                for w, p, S in zip(ws, plan, chunks)]
 
     cache = os.path.join(ROOT, "paper_1701_04148_gb300", "_build", "autotune_cache.json")
     key = autotune.shape_key(ws, ns, 4, 16, 4) + "-" + torch.cuda.get_device_name(dev).replace(" ", "_")
     t1 = time.time()
-    tuned = autotune.tune(make, streams, ns, cache_path=cache, cache_key=key, widths=ws, d=4, z=16)
+    tuned = autotune.tune(make, streams, ns, cache_path=cache, cache_key=key, widths=ws, d=4, z=16,
+                          dict_arena_bytes=arena_bytes)
     tune_s = time.time() - t1
     chunks = tuned["chunks"]
     bsk, psk = make(chunks), make(chunks)
+    plain_dict = torch.empty(max(sf.dictionary_bytes(4, w, 16, 4, p["seed"], S) for w, p, S in zip(ws, plan, chunks)),
+                             dtype=torch.uint8, device=dev)
+    for sk in psk:
+        sk.set_dictionary(plain_dict)
     batch = sf.Batch(len(bsk), graph=True, stream=stream, max_round_slots=tuned["round_slots"],
-                     block_threads=tuned["block_threads"], group_bytes=tuned["group_bytes"])
+                     block_threads=tuned["block_threads"], group_bytes=tuned["group_bytes"],
+                     dict_arena_bytes=arena_bytes)
     items = [(sk, k, o) for sk, (k, o) in zip(bsk, streams)]
 
     def batched_step():
@@ -1441,11 +1455,14 @@ def run_batch(args, ctx):
            "autotune_updates_per_s": tuned["trials"], "autotune_block": tuned["trials_block"],
            "autotune_group": tuned["trials_group"], "autotune_best_rounds_bracketed": tuned["best_rounds_bracketed"],
            "autotune_rounds_skipped_for_memory": tuned["rounds_skipped_for_memory"],
-           "sketch_bytes": autotune.sketch_bytes(ws, chunks, 4, 16),
+           "sketch_bytes": autotune.sketch_bytes(ws, chunks, 4, 16, shared_dict=True),
+           "dict_arena_bytes": arena_bytes,
+           "sketch_bytes_with_own_dictionaries": autotune.sketch_bytes(ws, chunks, 4, 16),
            "graph": info, "status": st_b, "roofline": roofline, "roofline_hbm": roofline_hbm,
            "launch_groups": {"groups": info["groups_last"], "group_bytes": info["group_bytes"],
                              "rule": "sketches whose counters fit the budget packed into L2-sized launch "
-                                     "groups, larger ones share one launch"},
+                                     "groups, larger ones share one launch; a group whose dictionaries do "
+                                     "not fit the arena together is split"},
            "batched_equals_plain": bool(exact), "gen_s": round(gen_s, 1), "autotune_s": round(tune_s, 1),
            "n_gpus": world, "scaling": "strong",
            "shard": {"ranks": world, "sketches_rank0": len(mine), "updates_rank0": total,

@@ -84,6 +84,10 @@ typedef int32_t sf_status;
                                         the ablation against SF_F; insertions and queries are
                                         the same.  Chunked updates apply it as a clamp to the
                                         chunk-end bucket sum (equal, since A <= sum holds)   */
+#define SF_FLAG_SHARED_DICT    4u    /* the chunk dictionary is not in the sketch's scratch:
+                                        a batch with a dictionary arena places it there per
+                                        launch group, and standalone updates use the memory
+                                        given by sf_set_dictionary (see below)                */
 
 typedef struct sf_params {
     uint32_t d;          /* rows, 1..SF_MAX_D                                   (Table 1: d) */
@@ -122,7 +126,8 @@ const char *sf_status_str(sf_status s);
  *                   counters of a bucket sit together so one access reads them)
  *   slim_bytes    = d*w*4,   layout A[i*w + j]
  *   scratch_bytes = control words + the per-chunk key dictionary: 32 B x a power of two
- *                   >= 16*chunk slots for chunks up to 65,536, >= 8*chunk above;
+ *                   >= 16*chunk slots for chunks up to 65,536, >= 8*chunk above (no
+ *                   dictionary with SF_FLAG_SHARED_DICT: see sf_set_dictionary);
  *                   sketches with chunk == 1 and w >= 1024 also hold the one-at-a-time
  *                   dependency-graph workspace (about (16 + 8d) * 512 KiB)
  * Any output pointer may be NULL.  Returns SF_ERR_INVALID for parameters out of range.
@@ -160,6 +165,26 @@ sf_status sf_reset(sf_sketch *s);
  * chunk (its stream position still counts towards the chunk boundaries).
  */
 sf_status sf_set_index_table(sf_sketch *s, const uint32_t *table_dev, uint32_t n_keys);
+
+/*
+ * The per-chunk key dictionary outside the sketch's scratch (params.flags & SF_FLAG_SHARED_DICT).
+ * A chunked update keys a dictionary by the distinct keys of each chunk (its entries are zero
+ * between launches: every launch clears the entries it claimed); a sketch owns one in its scratch
+ * unless it was created with SF_FLAG_SHARED_DICT, and then scratch_bytes holds the control words
+ * only.  The dictionary is live only while one of the sketch's updates runs, so sketches whose
+ * updates never run at the same time -- calls on one stream, or the launch groups of one batch --
+ * can share one.
+ *   sf_dictionary_bytes: the dictionary a sketch with these parameters needs (0 for chunk 1).
+ *   sf_set_dictionary: dict_dev, 16-byte aligned device memory of at least that many bytes, is the
+ *     dictionary of the sketch's standalone updates (sf_update_batch and the calls built on it);
+ *     the call zeroes it on the sketch's stream.  The caller keeps it alive, and lets no two
+ *     updates that use it run at the same time.  After an update returns SF_ERR_TIMEOUT call it
+ *     again (it re-zeroes).  SF_ERR_INVALID for a sketch without the flag or too small a buffer.
+ *     A flagged sketch with chunk > 1 and no dictionary refuses standalone updates
+ *     (SF_ERR_INVALID).
+ */
+sf_status sf_dictionary_bytes(const sf_params *p, uint64_t *dict_bytes);
+sf_status sf_set_dictionary(sf_sketch *s, void *dict_dev, uint64_t bytes);
 
 /*
  * Insertion of n items (Sec. 3.4 "Insertion", used unchanged by SF_F, Sec. 3.5), under the
@@ -308,6 +333,18 @@ sf_status sf_batch_sync(sf_batch *b);
  * on the grouping (each sketch's updates are the same); only the speed does.
  */
 sf_status sf_batch_set_group_bytes(sf_batch *b, uint64_t bytes);
+
+/*
+ * Dictionary arena of a batch, for its SF_FLAG_SHARED_DICT sketches: launch groups run one after
+ * another on the batch's stream, so each group's flagged sketches take their dictionaries
+ * (sf_dictionary_bytes each) from the start of the arena, and a group whose flagged sketches'
+ * dictionaries do not fit together is split into launches that fit.  arena_dev: 16-byte aligned
+ * device memory of `bytes` that the batch uses alone while it lives; the call zeroes it on the
+ * batch's stream (sf_batch_sync zeroes it again after SF_ERR_TIMEOUT).  NULL / 0 removes the
+ * arena; flagged sketches then use the dictionary given by sf_set_dictionary (SF_ERR_INVALID
+ * without one).  A flagged sketch whose dictionary alone exceeds the arena is SF_ERR_OOM.
+ */
+sf_status sf_batch_set_dictionary_arena(sf_batch *b, void *arena_dev, uint64_t bytes);
 /*
  * Launch shape of sf_batch_update (no counterpart in the paper): `threads` per block, 512 (the
  * default), 256 or 128, with 512 / threads co-resident blocks per SM, so each shape runs the same

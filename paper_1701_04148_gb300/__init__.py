@@ -31,6 +31,7 @@ SF_ERR_VERSION = -7
 SF_PENDING = 1
 SF_FLAG_EXPLICIT_INDEX = 1
 SF_FLAG_SF4_DELETE = 2
+SF_FLAG_SHARED_DICT = 4
 SF_SLIM_MAGIC = 0x4D494C53
 SF_HASH_SPLITMIX_LEMIRE = 1
 SF_HASH_EXPLICIT = 2
@@ -106,6 +107,9 @@ _SIGS = {
     "sf_batch_sync": (ctypes.c_int32, [ctypes.c_void_p]),
     "sf_batch_set_group_bytes": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64]),
     "sf_batch_set_block_threads": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint32]),
+    "sf_batch_set_dictionary_arena": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64]),
+    "sf_dictionary_bytes": (ctypes.c_int32, [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_uint64)]),
+    "sf_set_dictionary": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64]),
     "sf_pipeline_create": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
                                             ctypes.POINTER(ctypes.c_void_p)]),
     "sf_update_pipeline": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -236,6 +240,14 @@ def make_params(d, w, z, key_bytes, seed, chunk, flags=0) -> Params:
     return Params(d, w, z, key_bytes, seed & (2**64 - 1), chunk, flags)
 
 
+def dictionary_bytes(d, w, z, key_bytes, seed, chunk) -> int:
+    """sf_dictionary_bytes: the chunk dictionary of a sketch with these parameters."""
+    out = ctypes.c_uint64()
+    check(load().sf_dictionary_bytes(ctypes.byref(make_params(d, w, z, key_bytes, seed, chunk)), ctypes.byref(out)),
+          "sf_dictionary_bytes")
+    return out.value
+
+
 def required_bytes(p: Params):
     fb, sb, xb = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
     check(load().sf_required_bytes(ctypes.byref(p), ctypes.byref(fb), ctypes.byref(sb), ctypes.byref(xb)),
@@ -247,8 +259,11 @@ class Sketch:
     """One SF-sketch on the current CUDA device, buffers owned by torch tensors."""
 
     def __init__(self, d: int, w: int, z: int, key_bytes: int = 4, seed: int = 0, chunk: int = 1,
-                 explicit_index: bool = False, stream=None, device=None, delete_rule: str = "sff"):
-        """delete_rule: "sff" (Sec. 3.5, the final design) or "sf4" (Sec. 3.4, the ablation)."""
+                 explicit_index: bool = False, stream=None, device=None, delete_rule: str = "sff",
+                 shared_dict: bool = False):
+        """delete_rule: "sff" (Sec. 3.5, the final design) or "sf4" (Sec. 3.4, the ablation).
+        shared_dict: the chunk dictionary is not in the sketch's scratch (SF_FLAG_SHARED_DICT): a
+        Batch with a dictionary arena supplies it, or set_dictionary for standalone updates."""
         torch = _torch()
         L = load()
         if delete_rule not in ("sff", "sf4"):
@@ -256,7 +271,8 @@ class Sketch:
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device: the SF-sketch library has no CPU path")
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
-        flags = (SF_FLAG_EXPLICIT_INDEX if explicit_index else 0) | (SF_FLAG_SF4_DELETE if delete_rule == "sf4" else 0)
+        flags = ((SF_FLAG_EXPLICIT_INDEX if explicit_index else 0) | (SF_FLAG_SF4_DELETE if delete_rule == "sf4" else 0)
+                 | (SF_FLAG_SHARED_DICT if shared_dict else 0))
         self.params = make_params(d, w, z, key_bytes, seed, chunk, flags)
         fb, sb, xb = required_bytes(self.params)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
@@ -292,6 +308,13 @@ class Sketch:
 
     def slim_view(self):
         return self.slim.view(self.d, self.w)
+
+    def set_dictionary(self, buf):
+        """sf_set_dictionary: a device uint8/int32 tensor of at least dictionary_bytes(...) bytes,
+        shared with other sketches whose updates never run at the same time (zeroed here)."""
+        nbytes = buf.numel() * buf.element_size()
+        check(load().sf_set_dictionary(self.handle, _dev_ptr(buf, "dictionary"), nbytes), "sf_set_dictionary")
+        self._dict = buf
 
     def set_index_table(self, table):
         """Explicit-index mode: table (n_keys, d, 2) uint32/int32 of (h_i, f_i) on the device."""
@@ -423,10 +446,12 @@ class Batch:
     """Many sketches updated by one persistent launch (sf_batch_*), CUDA graph replay by default."""
 
     def __init__(self, max_sketches: int, graph: bool = True, stream=None, device=None,
-                 max_round_slots: int = 1 << 22, group_bytes: int | None = None, block_threads: int | None = None):
+                 max_round_slots: int = 1 << 22, group_bytes: int | None = None, block_threads: int | None = None,
+                 dict_arena_bytes: int | None = None):
         """group_bytes: counter footprint per launch group (None: the library default, 3/4 of L2;
         0: every sketch of a call in one launch).  block_threads: threads per block of the launches,
-        512 (default), 256 or 128."""
+        512 (default), 256 or 128.  dict_arena_bytes: a dictionary arena for shared_dict sketches
+        (sf_batch_set_dictionary_arena)."""
         torch = _torch()
         L = load()
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
@@ -444,6 +469,11 @@ class Batch:
             check(L.sf_batch_set_group_bytes(self.handle, int(group_bytes)), "sf_batch_set_group_bytes")
         if block_threads is not None:
             check(L.sf_batch_set_block_threads(self.handle, int(block_threads)), "sf_batch_set_block_threads")
+        self.arena = None
+        if dict_arena_bytes:
+            self.arena = torch.empty(int(dict_arena_bytes), dtype=torch.uint8, device=self.device)
+            check(L.sf_batch_set_dictionary_arena(self.handle, self.arena.data_ptr(), self.arena.numel()),
+                  "sf_batch_set_dictionary_arena")
 
     def update(self, items):
         """items: list of (Sketch, keys tensor, ops tensor or None)."""

@@ -5,11 +5,13 @@ What it tunes, in three stages on the real batch:
    SF_MAX_CHUNK), so every stream spreads over about R rounds of one launch. Chunk size is part of the
    semantics: it is recorded in the plan and in each sketch's parameters, and the CPU oracle takes it
    as an input. The largest R (smallest chunks, closest to one-at-a-time semantics) whose throughput
-   is within `tolerance` of the best candidate is kept.  Candidates run from 8 to 1024.  Throughput
-   grows with the chunk size (fewer rounds, fewer grid barriers), so the fastest candidate is the
-   smallest R that fits: a candidate whose sketches would need more device memory than `mem_budget`
-   (each chunk slot reserves its dictionary entries in the sketch's scratch) is skipped, and the plan
-   records whether the fastest tried R lay inside the range or at its end.
+   is within `tolerance` of the best candidate is kept.  Candidates run from 4 to 1024.  Throughput
+   grows with the chunk size (fewer rounds, fewer grid barriers) until the dictionaries of a launch
+   no longer fit L2 beside the counters.  A candidate whose sketches would need more device memory
+   than `mem_budget` is skipped: each chunk slot reserves dictionary entries, in the sketch's scratch,
+   or -- with SF_FLAG_SHARED_DICT sketches and `dict_arena_bytes` -- in one arena that the batch's
+   launch groups reuse one after another.  The plan records whether the fastest tried R lay inside
+   the range or at its end.
 2. The launch shape at that R: threads per block (512, 256 or 128, with 512 / threads blocks per SM,
    so every shape runs the same number of threads). The fastest shape is kept; shapes are not
    semantic.
@@ -27,7 +29,7 @@ import os
 import time
 
 SF_MAX_CHUNK = 1 << 20
-ROUND_CANDIDATES = (8, 16, 32, 64, 256, 1024)
+ROUND_CANDIDATES = (4, 8, 16, 32, 64, 256, 1024)
 BLOCK_CANDIDATES = (512, 256, 128)
 
 
@@ -60,8 +62,9 @@ def shape_key(widths, ns, d: int, z: int, key_bytes: int) -> str:
     return h.hexdigest()[:24]
 
 
-def _time_batch(sf, torch, sks, streams, graph, slots, trials, block=None, group=None):
-    b = sf.Batch(len(sks), graph=graph, max_round_slots=slots, block_threads=block, group_bytes=group)
+def _time_batch(sf, torch, sks, streams, graph, slots, trials, block=None, group=None, arena=None):
+    b = sf.Batch(len(sks), graph=graph, max_round_slots=slots, block_threads=block, group_bytes=group,
+                 dict_arena_bytes=arena)
     items = [(sk, k, o) for sk, (k, o) in zip(sks, streams)]
     for sk in sks:
         sk.reset()
@@ -80,20 +83,26 @@ def _time_batch(sf, torch, sks, streams, graph, slots, trials, block=None, group
     return best
 
 
-def sketch_bytes(widths, chunks, d: int, z: int) -> int:
-    """Device bytes of the batch's sketches (Fat, Slim and the chunk dictionary of sf_required_bytes)."""
+def sketch_bytes(widths, chunks, d: int, z: int, shared_dict: bool = False) -> int:
+    """Device bytes of the batch's sketches (Fat, Slim and scratch of sf_required_bytes: with
+    shared_dict, SF_FLAG_SHARED_DICT sketches, whose dictionaries come from the batch's arena)."""
     import paper_1701_04148_gb300 as sf
     total = 0
+    flags = sf.SF_FLAG_SHARED_DICT if shared_dict else 0
     for w, c in zip(widths, chunks):
-        fb, sb, xb = sf.required_bytes(sf.make_params(d, int(w), z, 4, 0, int(c)))
+        fb, sb, xb = sf.required_bytes(sf.make_params(d, int(w), z, 4, 0, int(c), flags))
         total += fb + sb + xb
     return total
 
 
 def tune(make_sketches, streams, ns, candidates=ROUND_CANDIDATES, blocks=BLOCK_CANDIDATES, group_budgets=None,
          tolerance: float = 0.05, trials: int = 1, graph: bool = True, cache_path: str | None = None,
-         cache_key: str | None = None, log=None, widths=None, d: int = 4, z: int = 16, mem_budget: int | None = None):
+         cache_key: str | None = None, log=None, widths=None, d: int = 4, z: int = 16, mem_budget: int | None = None,
+         dict_arena_bytes: int | None = None):
     """make_sketches(chunks) -> list of Sketch; streams: list of (keys, ops) device tensors.
+    dict_arena_bytes: make_sketches creates SF_FLAG_SHARED_DICT sketches, and every timed batch gets
+    a dictionary arena of this size (the memory check then counts the sketches without
+    dictionaries, plus the arena).
     group_budgets: launch-group budgets to try (None entries: the library default); by default the
     default, half of L2 and 0 (one launch).  widths (with d, z): the sketches' widths, to skip round
     counts whose sketches exceed mem_budget bytes (default: a sixth of the device's memory, so that a
@@ -121,13 +130,15 @@ def tune(make_sketches, streams, ns, candidates=ROUND_CANDIDATES, blocks=BLOCK_C
     by_rounds = {}
     for R in candidates:
         chunks = chunk_sizes(ns, R)
-        if widths is not None and sketch_bytes(widths, chunks, d, z) > mem_budget:
+        need = (sketch_bytes(widths, chunks, d, z, dict_arena_bytes is not None) + (dict_arena_bytes or 0)
+                if widths is not None else 0)
+        if widths is not None and need > mem_budget:
             skipped.append(R)
             say(f"autotune: R={R} skipped (sketches above the memory budget)")
             continue
         slots = sum((c + 31) // 32 * 32 for c in chunks)
         sks = make_sketches(chunks)
-        by_rounds[R] = total / _time_batch(sf, torch, sks, streams, graph, slots, trials)
+        by_rounds[R] = total / _time_batch(sf, torch, sks, streams, graph, slots, trials, arena=dict_arena_bytes)
         say(f"autotune: R={R} -> {by_rounds[R] / 1e9:.3f} G updates/s")
         for sk in sks:
             sk.close()
@@ -139,14 +150,15 @@ def tune(make_sketches, streams, ns, candidates=ROUND_CANDIDATES, blocks=BLOCK_C
     # stage 2: launch shape at that round count
     by_block = {}
     for blk in blocks:
-        by_block[blk] = total / _time_batch(sf, torch, sks, streams, graph, slots, trials, block=blk)
+        by_block[blk] = total / _time_batch(sf, torch, sks, streams, graph, slots, trials, block=blk,
+                                            arena=dict_arena_bytes)
         say(f"autotune: R={chosen} block={blk} -> {by_block[blk] / 1e9:.3f} G updates/s")
     block = choose_fastest(by_block, blocks)
     # stage 3: launch-group budget at that round count and shape
     by_group = {}
     for gbytes in group_budgets:
         by_group[gbytes] = total / _time_batch(sf, torch, sks, streams, graph, slots, trials, block=block,
-                                               group=gbytes)
+                                               group=gbytes, arena=dict_arena_bytes)
         say(f"autotune: R={chosen} block={block} group={gbytes} -> {by_group[gbytes] / 1e9:.3f} G updates/s")
     group = choose_fastest(by_group, list(group_budgets))
     for sk in sks:
@@ -158,7 +170,7 @@ def tune(make_sketches, streams, ns, candidates=ROUND_CANDIDATES, blocks=BLOCK_C
             "trials_block": {str(k): v for k, v in by_block.items()},
             "trials_group": {("default" if k is None else str(k)): v for k, v in by_group.items()},
             "best_rounds_bracketed": bracketed(by_rounds), "rounds_skipped_for_memory": skipped,
-            "mem_budget": mem_budget, "tolerance": tolerance}
+            "mem_budget": mem_budget, "tolerance": tolerance, "dict_arena_bytes": dict_arena_bytes}
     if cache_path and cache_key:
         cache = json.load(open(cache_path)) if os.path.exists(cache_path) else {}
         cache[cache_key] = plan

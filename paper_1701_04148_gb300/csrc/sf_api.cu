@@ -64,6 +64,7 @@ sf_status run_update(sf_sketch* s, const void* keys_in, const int8_t* ops_in, in
         a.ctrl = s->ctrl;
         e = sfk::launch_seq_update(a, s->stream, s->smem_optin);
     } else {
+        if (!s->dict) return SF_ERR_INVALID;  // SF_FLAG_SHARED_DICT without sf_set_dictionary
         sfk::SketchRun one{};
         one.s = desc_of(s);
         one.keys = (const uint8_t*)keys;
@@ -107,11 +108,29 @@ sf_status sf_required_bytes(const sf_params* p, uint64_t* fat_bytes, uint64_t* s
     if (fat_bytes) *fat_bytes = (uint64_t)p->d * p->w * p->z * 4ull;
     if (slim_bytes) *slim_bytes = (uint64_t)p->d * p->w * 4ull;
     if (scratch_bytes) {
-        const uint64_t cap = p->chunk > 1 ? sfk::dict_capacity(p->chunk) : 0;
+        const uint64_t cap = (p->chunk > 1 && !(p->flags & SF_FLAG_SHARED_DICT)) ? sfk::dict_capacity(p->chunk) : 0;
         // S = 1 sketches wide enough for the dependency-graph path also hold its workspace
         const uint64_t dag = (p->chunk == 1 && sfk::dag_eligible(p->w, p->z)) ? sfk::dag_workspace_bytes(p->d) : 0;
         *scratch_bytes = kCtrlBytes + cap * sizeof(sfk::DictEntry) + dag;
     }
+    return SF_OK;
+}
+
+sf_status sf_dictionary_bytes(const sf_params* p, uint64_t* dict_bytes) {
+    if (!sf_params_ok(p) || !dict_bytes) return SF_ERR_INVALID;
+    *dict_bytes = p->chunk > 1 ? (uint64_t)sfk::dict_capacity(p->chunk) * sizeof(sfk::DictEntry) : 0;
+    return SF_OK;
+}
+
+sf_status sf_set_dictionary(sf_sketch* s, void* dict_dev, uint64_t bytes) {
+    if (!s || !(s->p.flags & SF_FLAG_SHARED_DICT) || s->p.chunk < 2 || !dict_dev || !aligned16(dict_dev))
+        return SF_ERR_INVALID;
+    const uint64_t need = (uint64_t)s->cap * sizeof(sfk::DictEntry);
+    if (bytes < need) return SF_ERR_INVALID;
+    DeviceGuard guard(s->device);
+    if (!guard.ok) return SF_ERR_CUDA;
+    if (cudaMemsetAsync(dict_dev, 0, need, s->stream) != cudaSuccess) return SF_ERR_CUDA;
+    s->dict = (sfk::DictEntry*)dict_dev;
     return SF_OK;
 }
 
@@ -130,7 +149,7 @@ sf_status sf_create(const sf_params* p, void* fat_dev, void* slim_dev, void* scr
     s->scratch = (uint8_t*)scratch_dev;
     s->stream = (cudaStream_t)cuda_stream;
     s->ctrl = (uint32_t*)scratch_dev;
-    s->dict = (sfk::DictEntry*)((uint8_t*)scratch_dev + kCtrlBytes);
+    s->dict = (p->flags & SF_FLAG_SHARED_DICT) ? nullptr : (sfk::DictEntry*)((uint8_t*)scratch_dev + kCtrlBytes);
     s->cap = p->chunk > 1 ? sfk::dict_capacity(p->chunk) : 0;
     s->dag_ws = (p->chunk == 1 && sfk::dag_eligible(p->w, p->z)) ? (uint8_t*)scratch_dev + kCtrlBytes : nullptr;
     sfk::row_seeds(p->seed, p->d, s->rs);

@@ -42,6 +42,8 @@ struct sf_batch {
     std::vector<uint8_t> in_host;                // the item's keys or operations live in host memory
     std::vector<uint32_t> order;                 // item of each table row (group by group)
     std::vector<sfk::BatchArgs> plan;            // one cooperative launch per group
+    uint8_t* arena = nullptr;                    // dictionary arena of SF_FLAG_SHARED_DICT sketches
+    uint64_t arena_bytes = 0;
 };
 
 namespace {
@@ -71,6 +73,9 @@ cudaError_t enqueue(sf_batch* b, const std::vector<sfk::BatchArgs>& plan, uint32
     }
     return e;
 }
+
+bool shared_dict(const sf_sketch* s) { return (s->p.flags & SF_FLAG_SHARED_DICT) != 0; }
+uint64_t dict_bytes_of(const sf_sketch* s) { return (uint64_t)s->cap * sizeof(sfk::DictEntry); }
 
 // Counter footprint of one sketch in a round: Fat + Slim + the dictionary entries a chunk can touch.
 uint64_t item_footprint(const sf_sketch* s) {
@@ -157,6 +162,10 @@ sf_status sf_batch_update(sf_batch* b, uint32_t n_items, const sf_batch_item* it
         b->in_host[i] = (kh || oh) ? 1 : 0;
         const uint32_t kb = s->p.key_bytes;
         if ((kb == 4 || kb == 8) && ((uintptr_t)b->keys_acc[i] % kb) != 0) return SF_ERR_INVALID;
+        if (shared_dict(s)) {
+            if (b->arena && dict_bytes_of(s) > b->arena_bytes) return SF_ERR_OOM;
+            if (!b->arena && !s->dict) return SF_ERR_INVALID;
+        }
     }
     DeviceGuard guard(b->device);
     if (!guard.ok) return SF_ERR_CUDA;
@@ -211,10 +220,33 @@ sf_status sf_batch_update(sf_batch* b, uint32_t n_items, const sf_batch_item* it
         }
     }
 
+    // With a dictionary arena, the flagged sketches of a launch take their dictionaries from its
+    // start (launches run one after another); a group whose dictionaries do not fit together is
+    // split into launches that fit, in order.
+    if (b->arena) {
+        std::vector<std::pair<uint32_t, uint32_t>> split;
+        for (const auto& gr : groups) {
+            uint32_t first = gr.first;
+            uint64_t used = 0;
+            for (uint32_t row = gr.first; row < gr.second; ++row) {
+                const sf_sketch* s = items[b->order[row]].sketch;
+                const uint64_t need = shared_dict(s) ? dict_bytes_of(s) : 0;
+                if (row > first && used + need > b->arena_bytes) {
+                    split.emplace_back(first, row);
+                    first = row;
+                    used = 0;
+                }
+                used += need;
+            }
+            split.emplace_back(first, gr.second);
+        }
+        groups.swap(split);
+    }
+
     b->plan.clear();
     uint64_t rounds_all = 0;
     for (const auto& gr : groups) {
-        uint64_t flat = 0, rounds = 0;
+        uint64_t flat = 0, rounds = 0, arena_off = 0;
         uint32_t max_chunk = 0;
         bool may_ins = false, may_del = false, in_host = false;
         for (uint32_t row = gr.first; row < gr.second; ++row) {
@@ -236,7 +268,12 @@ sf_status sf_batch_update(sf_batch* b, uint32_t n_items, const sf_batch_item* it
             R.S = s->p.chunk;
             R.n = items[i].n;
             R.flat_base = flat;  // slots are numbered per launch group
-            R.dict = s->dict;
+            if (shared_dict(s) && b->arena) {
+                R.dict = reinterpret_cast<sfk::DictEntry*>(b->arena + arena_off);
+                arena_off += dict_bytes_of(s);
+            } else {
+                R.dict = s->dict;
+            }
             R.cap_mask = s->cap - 1u;
             R.claim_mask = sfk::claim_capacity(R.S) - 1u;
             flat += sfk::round_up32(R.S);
@@ -323,6 +360,9 @@ sf_status sf_batch_sync(sf_batch* b) {
         cudaStreamSynchronize(b->stream) != cudaSuccess)
         return SF_ERR_CUDA;
     if (err == 0) return SF_OK;
+    // a grid wait that gave up may leave dictionary entries claimed: the arena is zeroed again
+    if ((err & sfk::kErrTimeout) && b->arena && cudaMemsetAsync(b->arena, 0, b->arena_bytes, b->stream) != cudaSuccess)
+        return SF_ERR_CUDA;
     if (cudaMemsetAsync(b->ctrl, 0, kBatchCtrlBytes, b->stream) != cudaSuccess ||
         cudaStreamSynchronize(b->stream) != cudaSuccess)
         return SF_ERR_CUDA;
@@ -335,6 +375,21 @@ sf_status sf_batch_sync(sf_batch* b) {
 sf_status sf_batch_set_group_bytes(sf_batch* b, uint64_t bytes) {
     if (!b) return SF_ERR_INVALID;
     b->group_bytes = bytes;
+    return SF_OK;
+}
+
+sf_status sf_batch_set_dictionary_arena(sf_batch* b, void* arena_dev, uint64_t bytes) {
+    if (!b || (arena_dev && ((uintptr_t)arena_dev & 15u))) return SF_ERR_INVALID;
+    if (!arena_dev || bytes == 0) {
+        b->arena = nullptr;
+        b->arena_bytes = 0;
+        return SF_OK;
+    }
+    DeviceGuard guard(b->device);
+    if (!guard.ok) return SF_ERR_CUDA;
+    if (cudaMemsetAsync(arena_dev, 0, bytes, b->stream) != cudaSuccess) return SF_ERR_CUDA;
+    b->arena = (uint8_t*)arena_dev;
+    b->arena_bytes = bytes & ~15ull;
     return SF_OK;
 }
 

@@ -46,7 +46,7 @@ inline bool sf_params_ok(const sf_params* p) {
     if (p->z < 1 || p->z > SF_MAX_Z) return false;
     if (p->key_bytes < 1 || p->key_bytes > SF_MAX_KEY_BYTES) return false;
     if (p->chunk < 1 || p->chunk > SF_MAX_CHUNK) return false;
-    if ((p->flags & ~(SF_FLAG_EXPLICIT_INDEX | SF_FLAG_SF4_DELETE)) != 0) return false;
+    if ((p->flags & ~(SF_FLAG_EXPLICIT_INDEX | SF_FLAG_SF4_DELETE | SF_FLAG_SHARED_DICT)) != 0) return false;
     if ((p->flags & SF_FLAG_EXPLICIT_INDEX) && p->key_bytes != 4) return false;
     if ((uint64_t)p->d * p->w * p->z > (1ull << 40)) return false;
     return true;
@@ -84,7 +84,7 @@ struct sf_sketch {
     int smem_optin;
     uint64_t rs[SF_MAX_D];
     uint32_t* ctrl;
-    sfk::DictEntry* dict;
+    sfk::DictEntry* dict;   // in the scratch, or (SF_FLAG_SHARED_DICT) from sf_set_dictionary, or null
     uint32_t cap;
     const uint32_t* idx_table;
     uint32_t n_ids;

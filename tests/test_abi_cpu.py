@@ -100,3 +100,25 @@ def test_one_at_a_time_workspace_only_where_the_graph_path_applies(lib_path):
     _, _, just_under = sf.required_bytes(sf.make_params(1, (1 << 28) - 1, 16, 4, 1, 1))
     assert narrow < 4096 and wide < 4096
     assert graph > 30_000_000 and just_under > 10_000_000
+
+
+def test_shared_dictionary_sizes(lib_path):
+    """Host-only arithmetic of the boundary: a sketch created with SF_FLAG_SHARED_DICT needs no
+    dictionary in its scratch, and sf_dictionary_bytes gives the one it then takes from elsewhere
+    (32 B x a power of two >= 16 S slots up to S = 65,536, >= 8 S above; none for S = 1)."""
+    import paper_1701_04148_gb300 as sf
+    L = sf.load(lib_path)
+
+    def sizes(chunk, flags):
+        p = sf.make_params(4, 4096, 16, 4, 1, chunk, flags)
+        fb, sb, xb, db = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        assert L.sf_required_bytes(ctypes.byref(p), ctypes.byref(fb), ctypes.byref(sb), ctypes.byref(xb)) == 0
+        assert L.sf_dictionary_bytes(ctypes.byref(p), ctypes.byref(db)) == 0
+        return xb.value, db.value
+
+    for chunk, slots in ((1000, 16384), (65536, 1 << 20), (65537, 1 << 20), (100000, 1 << 20), (1 << 20, 1 << 23)):
+        own, d_own = sizes(chunk, 0)
+        shared, d_shared = sizes(chunk, sf.SF_FLAG_SHARED_DICT)
+        assert d_own == d_shared == 32 * slots, chunk
+        assert own - shared == 32 * slots, chunk
+    assert sizes(1, sf.SF_FLAG_SHARED_DICT)[1] == 0

@@ -277,3 +277,88 @@ def test_underfilled_groups_join_the_shared_launch(sf):
     assert b.info()["groups_last"] == 1
     _same_as_per_sketch_calls(sf, shapes, streams, bsk)
     b.close()
+
+
+def test_dictionary_arena_splits_launches_and_gives_the_same_sketches(sf):
+    """SF_FLAG_SHARED_DICT sketches take their chunk dictionaries from the batch's arena, per launch:
+    twelve sketches with 100,000-slot chunks (32 MiB dictionaries) in one launch (group budget 0)
+    with an 80 MiB arena run as six launches of two, and small sketches of the single-iteration
+    kernel with an arena of three dictionaries split the same way; every sketch equals one
+    sf_update_batch call per sketch, on the second call (graph replay) as on the first.  A sketch
+    whose dictionary exceeds the arena is SF_ERR_OOM; a flagged sketch with neither an arena nor
+    its own dictionary is SF_ERR_INVALID."""
+    shapes = [(256, 40 + i, 100_000) for i in range(12)]
+    streams = [wl.mixed_stream(400_000, 3_000, 1.0, 0.1, 4, seed=seed, device="cuda") for _, seed, _ in shapes]
+    bsk = [sf.Sketch(4, w, 16, 4, seed, S, shared_dict=True) for w, seed, S in shapes]
+    dict_bytes = sf.dictionary_bytes(4, 256, 16, 4, 0, 100_000)
+    assert dict_bytes == 32 << 20
+    b = sf.Batch(len(bsk), group_bytes=0, max_round_slots=12 * 100_000, dict_arena_bytes=80 << 20)
+    for _ in range(2):
+        for sk in bsk:
+            sk.reset()
+        b.update([(sk, st.keys, st.ops) for sk, (st, _) in zip(bsk, streams)])
+    assert b.sync_status() == sf.SF_OK
+    assert b.info()["groups_last"] == 6
+    _same_as_per_sketch_calls(sf, shapes, streams, bsk)
+    b.close()
+
+    plan = _plan(30, seed=13)
+    pstreams = _streams(plan)
+    pshapes = [(p["w"], p["seed"], _chunk_for(p, 6)) for p in plan]
+    psk = [sf.Sketch(4, w, 16, 4, seed, S, shared_dict=True) for w, seed, S in pshapes]
+    needs = [sf.dictionary_bytes(4, w, 16, 4, seed, S) for w, seed, S in pshapes]
+    arena = 3 * max(needs)
+    want, used = 1, 0                 # launches of the greedy in-order split
+    for nb in needs:
+        if used and used + nb > arena:
+            want, used = want + 1, 0
+        used += nb
+    assert want > 1
+    b2 = sf.Batch(len(psk), group_bytes=0, dict_arena_bytes=arena)
+    b2.update([(sk, st.keys, st.ops) for sk, (st, _) in zip(psk, pstreams)])
+    assert b2.sync_status() == sf.SF_OK
+    assert b2.info()["groups_last"] == want
+    _same_as_per_sketch_calls(sf, pshapes, pstreams, psk)
+    b2.close()
+
+    small = sf.Batch(1, dict_arena_bytes=dict_bytes // 2, max_round_slots=100_000)
+    with pytest.raises(sf.SFError) as ei:
+        small.update([(bsk[0], streams[0][0].keys, streams[0][0].ops)])
+    assert ei.value.status == sf.SF_ERR_OOM
+    small.close()
+    bare = sf.Batch(1, max_round_slots=100_000)
+    with pytest.raises(sf.SFError) as ei:
+        bare.update([(bsk[0], streams[0][0].keys, streams[0][0].ops)])
+    assert ei.value.status == sf.SF_ERR_INVALID
+    bare.close()
+
+
+def test_shared_dictionary_for_standalone_updates(sf):
+    """Two SF_FLAG_SHARED_DICT sketches (13-byte keys, chunk 4,096; u32 keys, chunk 100,000) whose
+    calls run one after another on one stream share one dictionary buffer (sf_set_dictionary) and
+    equal sketches that own theirs.  Without a dictionary a flagged sketch refuses an update; too
+    small a buffer is refused."""
+    import torch
+    ins, dels, _ = wl.flows_with_deletes(200_000, 20_000, 1.0, 0.1, seed=81)
+    st4, _ = wl.mixed_stream(300_000, 20_000, 1.2, 0.2, 4, seed=82, device="cuda")
+    a1, a2 = sf.Sketch(4, 3001, 16, 13, 5, 4096), sf.Sketch(4, 777, 8, 4, 6, 100_000)
+    b1 = sf.Sketch(4, 3001, 16, 13, 5, 4096, shared_dict=True)
+    b2 = sf.Sketch(4, 777, 8, 4, 6, 100_000, shared_dict=True)
+    with pytest.raises(sf.SFError) as ei:
+        b1.insert(ins.cuda())
+    assert ei.value.status == sf.SF_ERR_INVALID
+    need = max(sf.dictionary_bytes(4, 3001, 16, 13, 5, 4096), sf.dictionary_bytes(4, 777, 8, 4, 6, 100_000))
+    with pytest.raises(sf.SFError) as ei:
+        b2.set_dictionary(torch.empty(need // 2, dtype=torch.uint8, device="cuda"))
+    assert ei.value.status == sf.SF_ERR_INVALID
+    shared = torch.empty(need, dtype=torch.uint8, device="cuda")
+    b1.set_dictionary(shared)
+    b2.set_dictionary(shared)
+    for a, b, call in ((a1, b1, lambda s: s.insert(ins.cuda())), (a2, b2, lambda s: s.update(st4.keys, st4.ops)),
+                       (a1, b1, lambda s: s.delete(dels.cuda()))):
+        call(a)
+        call(b)
+    for s in (a1, a2, b1, b2):
+        assert s.sync_status() == sf.SF_OK
+    assert torch.equal(a1.fat, b1.fat) and torch.equal(a1.slim, b1.slim)
+    assert torch.equal(a2.fat, b2.fat) and torch.equal(a2.slim, b2.slim)
