@@ -261,7 +261,7 @@ def main():
                     help="flows: skip the chunked-vs-sequential accuracy report (its one-at-a-time runs launch "
                          "thousands of kernels)")
     ap.add_argument("--workload", choices=["all", "flows", "batch", "serve", "accuracy", "pipeline", "profile",
-                                           "l2curve", "seq", "outofl2", "batchprof"],
+                                           "l2curve", "seq", "outofl2", "batchprof", "rounds-accuracy"],
                     default="all",
                     help="all: the flows line with the batched and serving results embedded; profile: the small "
                          "fixed case the committed ncu summaries capture (two insert launches, the second profiled)")
@@ -273,7 +273,7 @@ def main():
                     help="print the chunk kernel's source hash (the key of the committed traffic record) and exit")
     ap.add_argument("--profile-inserts", type=int, default=2_000_000)
     ap.add_argument("--batch-sketches", type=int, default=1024)
-    ap.add_argument("--batchprof-rounds", type=int, default=16,
+    ap.add_argument("--batchprof-rounds", type=int, default=4,
                     help="batchprof: round count of the captured group (the autotuner's choice on this batch)")
     ap.add_argument("--serve-seconds", type=float, default=6.0, help="serve: seconds of each open-loop load (70 %%, 90 %%)")
     ap.add_argument("--ool2-updates", type=int, default=1_000_000_000,
@@ -323,6 +323,8 @@ def main():
             line["batched"] = b
     if args.workload == "accuracy":
         line = run_accuracy(args, ctx)
+    if args.workload == "rounds-accuracy":
+        line = run_rounds_accuracy(args, ctx)
     if args.workload == "pipeline":
         line = run_pipeline(args, ctx)
     if args.workload == "profile":
@@ -820,7 +822,7 @@ def run_batch_profile(args, ctx):
     """The small case of the batched update that ncu captures: one launch group of the many-sketch
     batch (the first sketches of the 1,024-sketch plan, in order, whose counters fit the default
     group budget of 3/4 of L2, as sf_batch_update groups them), chunks for R = --batchprof-rounds
-    rounds (16 by default, what the autotuner picks for this batch on a GB300), one launch per call
+    rounds (4 by default, what the autotuner picks for this batch on a GB300), one launch per call
     (group budget 0 on this subset), dictionaries in an arena.  A warm-up call, then the profiled call
     (launch index 1 of the chunk kernel)."""
     import torch
@@ -1215,6 +1217,47 @@ def run_l2curve(args, ctx):
         raise SystemExit(f"sf_bench_grid_barrier failed: {rc}")
     return {"workload": "l2curve", "unit": "G random 32-bit ops/s", "rows": rows, "atomics": atomics,
             "grid_barrier_us": round(a.elapsed_time(b) * 1e3 / 2000, 3)}
+
+
+def run_rounds_accuracy(args, ctx):
+    """What the batch autotuner's chunk sizes cost in accuracy: six sketches of the many-sketch plan
+    (every 170th by stream length: 10^4 to 2.8 x 10^6 updates of the 90/10 turnstile mix, u32 keys,
+    d=4, z=16), each updated one at a time (S = 1, the paper's rule) and in chunks of ceil(n / R) for
+    the autotuner's round counts R; the average relative error of the point query over the ids with
+    a positive count, against exact counts (a per-id sum of the stream's +1/-1)."""
+    import torch
+
+    import paper_1701_04148_gb300 as sf
+    import workloads as wl
+    dev, stream = ctx["dev"], ctx["stream"]
+    plan = wl.many_sketch_plan(args.batch_sketches, seed=3)
+    picked = sorted(plan, key=lambda p: p["n"])[::170][:6]
+    rounds = (32, 16, 8, 4, 2)
+    out = []
+    for p in picked:
+        st, ids = wl.mixed_stream(p["n"], p["distinct"], p["s"], 0.1, 4, seed=p["seed"], device=dev)
+        kid = st.keys.view(torch.int32).view(-1).to(torch.int64) & 0xFFFFFFFF
+        idv = ids.view(torch.int32).view(-1).to(torch.int64) & 0xFFFFFFFF
+        srt, order = torch.sort(idv)
+        where = order[torch.searchsorted(srt, kid)]
+        true = torch.zeros(idv.numel(), dtype=torch.int64, device=dev)
+        true.index_add_(0, where, st.ops.to(torch.int64))
+        live = true > 0
+        rec = {"n": p["n"], "w": p["w"], "zipf_s": round(p["s"], 3), "ids_live": int(live.sum())}
+        for R in (None,) + rounds:
+            S = 1 if R is None else min(1 << 20, max(2, -(-p["n"] // R)))  # as the autotuner clamps
+            g = sf.Sketch(4, p["w"], 16, 4, p["seed"], S, stream=stream)
+            g.update(st.keys, st.ops)
+            slim, hdr = g.export_slim()
+            est = sf.query(slim, hdr, ids, stream=stream).to(torch.int64) & 0xFFFFFFFF
+            if g.sync_status() != sf.SF_OK:
+                raise SystemExit("rounds-accuracy: update failed")
+            are = ((est[live] - true[live]).abs().to(torch.float64) / true[live].to(torch.float64)).mean()
+            rec["are_one_at_a_time" if R is None else f"are_R{R}"] = round(float(are), 5)
+            g.close()
+        out.append(rec)
+    return {"workload": "rounds-accuracy", "rounds": list(rounds), "sketches": out,
+            "note": "ARE of the point query over ids with a positive count; chunk = ceil(n / R), at most 2^20"}
 
 
 def run_accuracy(args, ctx):

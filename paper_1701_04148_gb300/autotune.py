@@ -5,7 +5,7 @@ What it tunes, in three stages on the real batch:
    SF_MAX_CHUNK), so every stream spreads over about R rounds of one launch. Chunk size is part of the
    semantics: it is recorded in the plan and in each sketch's parameters, and the CPU oracle takes it
    as an input. The largest R (smallest chunks, closest to one-at-a-time semantics) whose throughput
-   is within `tolerance` of the best candidate is kept.  Candidates run from 4 to 1024.  Throughput
+   is within `tolerance` of the best candidate is kept.  Candidates run from 2 to 1024.  Throughput
    grows with the chunk size (fewer rounds, fewer grid barriers) until the dictionaries of a launch
    no longer fit L2 beside the counters.  A candidate whose sketches would need more device memory
    than `mem_budget` is skipped: each chunk slot reserves dictionary entries, in the sketch's scratch,
@@ -29,7 +29,7 @@ import os
 import time
 
 SF_MAX_CHUNK = 1 << 20
-ROUND_CANDIDATES = (4, 8, 16, 32, 64, 256, 1024)
+ROUND_CANDIDATES = (2, 4, 8, 16, 32, 64, 256, 1024)
 BLOCK_CANDIDATES = (512, 256, 128)
 
 
