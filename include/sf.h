@@ -450,7 +450,7 @@ sf_status sfc_destroy(sfc *c);
  * (2 MiB + 256 B), which every GPU that loads the library keeps until the process exits.  Hence:
  *   - params->chunk must be 2..SF_NOALLOC_MAX_CHUNK; larger chunks return SF_ERR_INVALID (the
  *     array is sized for that maximum), as do explicit-index flags (SF_FLAG_SF4_DELETE is
- *     accepted);
+ *     accepted; SF_FLAG_SHARED_DICT changes nothing here, the dictionary being the fixed array);
  *   - all calls share the array, so calls that may overlap on the GPU (different streams,
  *     different threads) race and corrupt each other's result: serialise them;
  *   - the call zeroes the array's control words and dictionary itself before its kernel runs;
