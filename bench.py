@@ -1088,6 +1088,8 @@ def run_outofl2(args, ctx):
             host[3].fill_(-1)
             step(src=host, pipe=pipe if use_pipe else None)
             torch.cuda.synchronize()
+            if dist is not None:
+                dist.barrier()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
             for _ in range(args.steps):
@@ -1096,7 +1098,12 @@ def run_outofl2(args, ctx):
             torch.cuda.synchronize()
             g.sync()
             pipe.release_inputs()
-            return a.elapsed_time(b) / args.steps, bool(torch.equal(host[3], ref))
+            ems = a.elapsed_time(b) / args.steps
+            if dist is not None:  # the slowest rank's time
+                t = torch.tensor([ems], dtype=torch.float64, device=dev)
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+                ems = float(t.item())
+            return ems, bool(torch.equal(host[3], ref))
 
         # the two host forms interleaved, three repetitions each (the host link's rate varies over
         # time on these machines); each reports its median repetition
