@@ -141,6 +141,7 @@ struct sfc {
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<std::shared_ptr<Request>> pending;
+    uint64_t pending_keys = 0;  // keys of the pending requests (kept with the queue, under mu)
     std::unordered_map<uint64_t, std::shared_ptr<Request>> tickets;
     uint64_t next_ticket = 1;
     bool stop = false;
@@ -197,10 +198,8 @@ struct sfc {
             bool launched = false;
             for (auto& s : slots) {
                 if (s.busy || pending.empty()) continue;
-                uint64_t pend_keys = 0;
-                for (auto& r : pending) pend_keys += r->n;
                 const auto waited = std::chrono::duration<double, std::micro>(Clock::now() - pending.front()->t_submit).count();
-                const bool full = pend_keys >= cfg.max_batch_keys || pending.size() >= cfg.max_batch_reqs;
+                const bool full = pending_keys >= cfg.max_batch_keys || pending.size() >= cfg.max_batch_reqs;
                 if (!full && any_busy && waited < (double)cfg.max_wait_us && !stop) break;
                 launch(s);
                 launched = true;
@@ -243,6 +242,7 @@ struct sfc {
             koff += r->n * v->hdr.key_bytes;
             nkeys += r->n;
             s.members.push_back(r);
+            pending_keys -= r->n;
             pending.pop_front();
             ++nreq;
         }
@@ -386,6 +386,7 @@ sf_status sfc_query_submit(sfc* c, uint32_t sketch_id, const void* keys_host, ui
         *ticket = r->ticket;
         c->tickets[r->ticket] = r;
         c->pending.push_back(r);
+        c->pending_keys += n;
         c->st_requests++;
         c->st_keys += n;
         if (!c->window_started) {
