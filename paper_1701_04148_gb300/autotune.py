@@ -95,6 +95,16 @@ def sketch_bytes(widths, chunks, d: int, z: int, shared_dict: bool = False) -> i
     return total
 
 
+def _read_cache(path: str) -> dict:
+    """The plan cache, or {} when it is missing or unreadable (then the batch is tuned again)."""
+    try:
+        with open(path) as f:
+            data = json.load(f)
+        return data if isinstance(data, dict) else {}
+    except (OSError, ValueError):
+        return {}
+
+
 def tune(make_sketches, streams, ns, candidates=ROUND_CANDIDATES, blocks=BLOCK_CANDIDATES, group_budgets=None,
          tolerance: float = 0.05, trials: int = 1, graph: bool = True, cache_path: str | None = None,
          cache_key: str | None = None, log=None, widths=None, d: int = 4, z: int = 16, mem_budget: int | None = None,
@@ -113,8 +123,8 @@ def tune(make_sketches, streams, ns, candidates=ROUND_CANDIDATES, blocks=BLOCK_C
 
     import paper_1701_04148_gb300 as sf
 
-    if cache_path and cache_key and os.path.exists(cache_path):
-        cache = json.load(open(cache_path))
+    if cache_path and cache_key:
+        cache = _read_cache(cache_path)
         if cache_key in cache:
             return cache[cache_key]
     if group_budgets is None:
@@ -172,8 +182,13 @@ def tune(make_sketches, streams, ns, candidates=ROUND_CANDIDATES, blocks=BLOCK_C
             "best_rounds_bracketed": bracketed(by_rounds), "rounds_skipped_for_memory": skipped,
             "mem_budget": mem_budget, "tolerance": tolerance, "dict_arena_bytes": dict_arena_bytes}
     if cache_path and cache_key:
-        cache = json.load(open(cache_path)) if os.path.exists(cache_path) else {}
+        cache = _read_cache(cache_path)
         cache[cache_key] = plan
         os.makedirs(os.path.dirname(cache_path) or ".", exist_ok=True)
-        json.dump(cache, open(cache_path, "w"))
+        # several processes (one per GPU) may tune at once: write a private file, then rename it
+        # over the cache, so a reader sees the old or the new file, never half of one
+        tmp = f"{cache_path}.{os.getpid()}.tmp"
+        with open(tmp, "w") as f:
+            json.dump(cache, f)
+        os.replace(tmp, cache_path)
     return plan

@@ -42,3 +42,15 @@ def test_kernel_source_hash_ignores_comments_only():
     assert strip(a) != strip(a.replace("x = 1", "x = 2"))
     assert strip('char c = \'"\'; int y; // "') == 'char c = \'"\'; int y;'
     assert len(bench.chunk_kernel_source_sha256()) == 64
+
+
+def test_autotune_cache_survives_a_bad_file(tmp_path):
+    """The plan cache is read defensively (a missing, empty or half-written file means: tune again)
+    and replaced atomically, since one process per GPU may tune at the same time."""
+    from paper_1701_04148_gb300 import autotune
+    p = tmp_path / "cache.json"
+    assert autotune._read_cache(str(p)) == {}
+    p.write_text('{"a": {"rounds": 4}')          # cut short
+    assert autotune._read_cache(str(p)) == {}
+    p.write_text('{"a": {"rounds": 4}}')
+    assert autotune._read_cache(str(p)) == {"a": {"rounds": 4}}
