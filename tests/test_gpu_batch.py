@@ -362,3 +362,45 @@ def test_shared_dictionary_for_standalone_updates(sf):
         assert s.sync_status() == sf.SF_OK
     assert torch.equal(a1.fat, b1.fat) and torch.equal(a1.slim, b1.slim)
     assert torch.equal(a2.fat, b2.fat) and torch.equal(a2.slim, b2.slim)
+
+
+def test_dictionary_arena_with_13_byte_keys_and_deletes_and_a_pipelined_sketch(sf):
+    """The arena with 13-byte flow keys and mixed insert/delete operations (single-iteration and
+    multi-iteration chunk sizes in one batch, launches split by the arena), and a flagged sketch
+    updated from pinned host keys through an sf_pipeline with a dictionary of its own: every
+    sketch equals the same sketch that owns its dictionary."""
+    import torch
+    shapes = [(3001, 90 + i, S) for i, S in enumerate((4096, 65536, 100_000, 2048, 70_000, 30_000))]
+    streams = []
+    for w, seed, S in shapes:
+        ins, dels, _ = wl.flows_with_deletes(150_000, 20_000, 1.0, 0.15, seed=seed, device="cuda")
+        keys = torch.cat([ins, dels]).contiguous()
+        ops = torch.cat([torch.ones(ins.shape[0], dtype=torch.int8, device="cuda"),
+                         -torch.ones(dels.shape[0], dtype=torch.int8, device="cuda")]).contiguous()
+        streams.append((keys, ops))
+    flagged = [sf.Sketch(4, w, 16, 13, seed, S, shared_dict=True) for w, seed, S in shapes]
+    arena = 2 * max(sf.dictionary_bytes(4, w, 16, 13, seed, S) for w, seed, S in shapes)
+    b = sf.Batch(len(flagged), group_bytes=0, max_round_slots=sum(S for _, _, S in shapes) + 32 * len(shapes),
+                 dict_arena_bytes=arena)
+    b.update([(sk, k, o) for sk, (k, o) in zip(flagged, streams)])
+    assert b.sync_status() == sf.SF_OK
+    assert b.info()["groups_last"] >= 3
+    for (w, seed, S), (k, o), sk in zip(shapes, streams, flagged):
+        ref = sf.Sketch(4, w, 16, 13, seed, S)
+        ref.update(k, o)
+        assert ref.sync_status() == sf.SF_OK
+        assert torch.equal(ref.fat, sk.fat) and torch.equal(ref.slim, sk.slim), (w, seed, S)
+        ref.close()
+    b.close()
+
+    w, seed, S = shapes[2]
+    k, o = streams[2]
+    ref = sf.Sketch(4, w, 16, 13, seed, S)
+    ref.update(k, o)
+    p_sk = sf.Sketch(4, w, 16, 13, seed, S, shared_dict=True)
+    p_sk.set_dictionary(torch.empty(sf.dictionary_bytes(4, w, 16, 13, seed, S), dtype=torch.uint8, device="cuda"))
+    pipe = sf.Pipeline(staging_bytes=2 * (S * 14 + 32))
+    p_sk.update_through(pipe, k.cpu().pin_memory(), o.cpu().pin_memory())
+    assert ref.sync_status() == sf.SF_OK and p_sk.sync_status() == sf.SF_OK
+    assert torch.equal(ref.fat, p_sk.fat) and torch.equal(ref.slim, p_sk.slim)
+    pipe.close()
