@@ -174,12 +174,18 @@ struct sfc {
         cv_done.notify_all();
     }
 
+    // The worker loop.  The lock guards the queue, the tickets, the version table and the stats;
+    // the slots belong to this thread alone, so the host copies of keys and answers (megabytes per
+    // batch) run unlocked, and submitting threads are not held up by them.
     void run() {
         cudaSetDevice(device);
         std::unique_lock<std::mutex> lk(mu);
         while (true) {
-            // finish batches whose event fired (copy answers out of pinned staging first)
+            // finished batches: copy their answers out of pinned staging (unlocked), then complete
             bool any_busy = false;
+            Slot* fin[16];
+            uint32_t nfin = 0;
+            lk.unlock();
             for (auto& s : slots) {
                 if (!s.busy) continue;
                 if (cudaEventQuery(s.ev) == cudaSuccess) {
@@ -188,11 +194,13 @@ struct sfc {
                         if (r->n) std::memcpy(r->out, s.out_host + off, r->n * sizeof(uint32_t));
                         off += r->n;
                     }
-                    complete(s);
+                    fin[nfin++] = &s;
                 } else {
                     any_busy = true;
                 }
             }
+            lk.lock();
+            for (uint32_t f = 0; f < nfin; ++f) complete(*fin[f]);
             if (stop && pending.empty() && !any_busy) break;
             // launch as many batches as free slots and pending work allow
             bool launched = false;
@@ -201,7 +209,15 @@ struct sfc {
                 const auto waited = std::chrono::duration<double, std::micro>(Clock::now() - pending.front()->t_submit).count();
                 const bool full = pending_keys >= cfg.max_batch_keys || pending.size() >= cfg.max_batch_reqs;
                 if (!full && any_busy && waited < (double)cfg.max_wait_us && !stop) break;
-                launch(s);
+                take(s);
+                lk.unlock();
+                const bool ok = pack_and_launch(s);
+                lk.lock();
+                if (!ok) {
+                    for (auto& r : s.members) r->status = SF_ERR_CUDA;
+                    complete(s);
+                    continue;
+                }
                 launched = true;
                 any_busy = true;
             }
@@ -218,15 +234,31 @@ struct sfc {
         }
     }
 
-    // Packs pending requests into slot s and enqueues the request-table copy and the kernel, which
-    // reads the keys from the slot's pinned host buffer and writes the answers to another one over
-    // the host link (no key or answer copies on the batch's critical path) (holds mu).
-    void launch(Slot& s) {
-        uint64_t nkeys = 0, koff = 0;
+    // Moves pending requests into slot s, up to the batch limits (holds mu).
+    void take(Slot& s) {
+        uint64_t nkeys = 0;
         uint32_t nreq = 0;
         while (!pending.empty() && nreq < cfg.max_batch_reqs) {
             auto& r = pending.front();
             if (nkeys + r->n > cfg.max_batch_keys && nreq > 0) break;
+            nkeys += r->n;
+            pending_keys -= r->n;
+            s.members.push_back(r);
+            pending.pop_front();
+            ++nreq;
+        }
+        s.busy = true;
+        st_batches++;
+    }
+
+    // Packs the slot's requests into its pinned staging and enqueues the request-table copy and the
+    // kernel, which reads the keys from the slot's pinned host buffer and writes the answers to
+    // another one over the host link (no key or answer copies on the batch's critical path).  Runs
+    // unlocked: the requests' versions are pinned by their references and never change.
+    bool pack_and_launch(Slot& s) {
+        uint64_t nkeys = 0, koff = 0;
+        uint32_t nreq = 0;
+        for (auto& r : s.members) {
             const Version* v = r->v;
             sfk::QueryReq& q = s.reqs_host[nreq];
             q.A = (const uint32_t*)(arena_dev + v->off);
@@ -241,13 +273,8 @@ struct sfc {
             if (r->n) std::memcpy(s.keys_host + koff, r->keys, r->n * v->hdr.key_bytes);
             koff += r->n * v->hdr.key_bytes;
             nkeys += r->n;
-            s.members.push_back(r);
-            pending_keys -= r->n;
-            pending.pop_front();
             ++nreq;
         }
-        s.busy = true;
-        st_batches++;
         sfk::MultiQueryArgs a{};
         a.reqs = s.reqs_dev;
         a.n_reqs = nreq;
@@ -259,10 +286,10 @@ struct sfc {
         if (e == cudaSuccess) e = sfk::launch_multi_query(a, num_sms, s.stream);
         if (e == cudaSuccess) e = cudaEventRecord(s.ev, s.stream);
         if (e != cudaSuccess) {
-            for (auto& r : s.members) r->status = SF_ERR_CUDA;
             cudaStreamSynchronize(s.stream);
-            complete(s);
+            return false;
         }
+        return true;
     }
 };
 
