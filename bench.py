@@ -592,10 +592,9 @@ def run_flows(args, ctx):
             torch.cuda.synchronize()
             return host[0][0].numel() / a.elapsed_time(b) / 1e6
 
-        # The host link's rate varies over time on these machines (the same pinned buffers were seen
-        # copying at 17 and at 210 GB/s minutes apart), so the three forms run interleaved, three
-        # times each, each repetition preceded by a plain copy that records the link's rate; each
-        # form reports its median repetition.
+        # A host form's time can differ from one repetition to the next, so the three forms run
+        # interleaved, three times each, each repetition preceded by a plain copy that records the
+        # host link's rate; each form reports its median repetition.
         forms = {"pipelined": (False, True), "direct": (True, False), "staged": (False, False)}
         reps = {k: [] for k in forms}
         links = {k: [] for k in forms}
@@ -1110,8 +1109,7 @@ def run_outofl2(args, ctx):
                 ems = float(t.item())
             return ems, bool(torch.equal(host[3], ref))
 
-        # the two host forms interleaved, three repetitions each (the host link's rate varies over
-        # time on these machines); each reports its median repetition
+        # the two host forms interleaved, three repetitions each; each reports its median repetition
         reps = {True: [], False: []}
         for _ in range(3):
             for use_pipe in (True, False):
