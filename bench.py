@@ -309,9 +309,7 @@ def main():
     dev = torch.device("cuda", local)
     L = sf.load()
     # One created stream for all of the bench's torch work and sketch calls, made current so that
-    # they stay ordered as before.  The legacy default stream synchronises implicitly with other
-    # blocking work; with the sketches on it, runs of the pipelined host form saw 1.6-4x their usual
-    # time at full host-link rate, while on a created stream the same step held its time.
+    # they stay ordered; no implicit synchronisation with other work, as on the legacy default stream.
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(stream)
 
