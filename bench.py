@@ -38,6 +38,9 @@ SWEEP = (0.0, 0.5, 1.0, 1.5, 2.0, 3.0)
 D, W, Z, KB, S = 4, 1 << 18, 16, 13, 65536
 N_INS, N_FLOWS, DEL_FRAC = 32_000_000, 1_000_000, 0.10
 SEED0 = 2
+# repetitions of each end-to-end form (interleaved); each form reports its median, which stays
+# put when up to two repetitions run slow
+E2E_REPETITIONS = 5
 L2_OPS_PER_UPDATE = 4 * D   # d Fat RMW + d Fat reads + d Slim reads + d Slim RMW (Sec. 3.4/3.5 rules)
 L2_OPS_PER_QUERY = D        # d Slim gathers (Sec. 3.1 query)
 
@@ -591,13 +594,13 @@ def run_flows(args, ctx):
             return host[0][0].numel() / a.elapsed_time(b) / 1e6
 
         # A host form's time can differ from one repetition to the next, so the three forms run
-        # interleaved, three times each, each repetition preceded by a plain copy that records the
-        # host link's rate; each form reports its median repetition.
+        # interleaved, E2E_REPETITIONS times each, each repetition preceded by a plain copy that
+        # records the host link's rate; each form reports its median repetition.
         forms = {"pipelined": (False, True), "direct": (True, False), "staged": (False, False)}
         reps = {k: [] for k in forms}
         links = {k: [] for k in forms}
         equal = {k: True for k in forms}
-        for _ in range(3):
+        for _ in range(E2E_REPETITIONS):
             for name, (direct, pipelined) in forms.items():
                 links[name].append(round(link_gbps(), 1))
                 for h in host:
@@ -606,7 +609,7 @@ def run_flows(args, ctx):
                 equal[name] &= all(torch.equal(host[i][3], ref_answers[i]) for i in range(len(SWEEP)))
 
         def median_rep(name):
-            r = dict(sorted(reps[name], key=lambda x: x["ms_per_step"])[1])
+            r = dict(sorted(reps[name], key=lambda x: x["ms_per_step"])[E2E_REPETITIONS // 2])
             r["repetitions_ms_per_step"] = [x["ms_per_step"] for x in reps[name]]
             r["link_GBps_before_each"] = links[name]
             # the answers the host received equal the device-resident run's (same inputs)
@@ -619,7 +622,8 @@ def run_flows(args, ctx):
                            "alternating staging halves on a copy stream, overlapped with the updates, each "
                            "call's first copy with the previous call's last update; the query kernel reads "
                            "the pinned flow keys and writes the answers to pinned host memory")
-        e2e["measurement"] = ("median of three repetitions of --steps steps, the three forms interleaved; "
+        e2e["measurement"] = (f"median of {E2E_REPETITIONS} repetitions of --steps steps, the three forms "
+                              "interleaved; "
                               "link_GBps_before_each: a plain 416 MB pinned host-to-device copy timed just "
                               "before each repetition")
         direct_ = median_rep("direct")
@@ -1107,15 +1111,15 @@ def run_outofl2(args, ctx):
                 ems = float(t.item())
             return ems, bool(torch.equal(host[3], ref))
 
-        # the two host forms interleaved, three repetitions each; each reports its median repetition
+        # the two host forms interleaved, E2E_REPETITIONS each; each reports its median repetition
         reps = {True: [], False: []}
-        for _ in range(3):
+        for _ in range(E2E_REPETITIONS):
             for use_pipe in (True, False):
                 reps[use_pipe].append(timed(use_pipe))
 
         def form(use_pipe, transfer):
             ms_all = [r[0] for r in reps[use_pipe]]
-            ems = sorted(ms_all)[1]
+            ems = sorted(ms_all)[E2E_REPETITIONS // 2]
             return {"value": round(world * (n + nq) / (ems / 1e3) / 1e6, 2), "unit": "M ops/s",
                     "h2d_bytes_per_step": int(host[0].numel() + host[1].numel() + host[2].numel()),
                     "d2h_bytes_per_step": int(host[3].numel() * 4), "ms_per_step": round(ems, 3),
