@@ -244,9 +244,11 @@ sf_status sf_query_pipelined(const sf_slim_view *slim, const void *keys_host, ui
  * (a cudaStream_t other than the sketch's), and each piece is applied on the sketch's stream as soon
  * as it has landed, while the next piece is copied.  Pieces end on chunk boundaries, so the counters
  * equal one sf_update_batch call over all n updates.  ops_host NULL: every update is op_const
- * (+1 insert or -1 delete).  staging_dev: device memory of staging_bytes >= 2 * chunk * (key_bytes +
- * (ops_host ? 1 : 0)) bytes, else SF_ERR_OOM.  Asynchronous: the host buffers and the staging stay
- * in use until sf_sync on the sketch returns.
+ * (+1 insert or -1 delete).  staging_dev: 16-byte aligned device memory (else SF_ERR_INVALID) of
+ * staging_bytes >= 2 * (chunk * (key_bytes + (ops_host ? 1 : 0)) + 32) bytes, enough for a piece of
+ * one chunk (each half holds a piece's keys padded to a 16-byte multiple, then its operations), else
+ * SF_ERR_OOM.  Asynchronous: the host buffers and the staging stay in use until sf_sync on the
+ * sketch returns.
  */
 sf_status sf_update_pipelined(sf_sketch *s, const void *keys_host, const int8_t *ops_host, int32_t op_const,
                               uint64_t n, void *staging_dev, uint64_t staging_bytes, void *copy_stream);

@@ -362,7 +362,7 @@ class Sketch:
         if staging is None:
             per = self.params.key_bytes + (1 if ops_host is not None else 0)
             piece = max(1, (1 << 22) // self.params.chunk) * self.params.chunk
-            staging = torch.empty(2 * (piece * per + 16), dtype=torch.uint8, device=self.device)
+            staging = torch.empty(2 * (piece * per + 32), dtype=torch.uint8, device=self.device)
         if copy_stream is None:
             copy_stream = torch.cuda.Stream(device=self.device)
         self._pipeline = (k, ops_host, staging, copy_stream)

@@ -339,7 +339,12 @@ sf_status pipeline_init(sf_pipeline* p, void* staging_dev, uint64_t staging_byte
 sf_status pipeline_run(sf_sketch* s, sf_pipeline* p, const void* keys_host, const int8_t* ops_host, int32_t op_const,
                        uint64_t n) {
     const uint64_t kb = s->p.key_bytes, per = kb + (ops_host ? 1u : 0u), S = s->p.chunk;
-    const uint64_t chunks_per_piece = p->half_bytes > 16 ? (p->half_bytes - 16) / (S * per) : 0;
+    // the largest whole number of chunks whose keys (padded to a 16-byte multiple) and operations fit
+    // a half
+    uint64_t chunks_per_piece = p->half_bytes / (S * per);
+    while (chunks_per_piece > 0 &&
+           ((chunks_per_piece * S * kb + 15) & ~15ull) + (ops_host ? chunks_per_piece * S : 0) > p->half_bytes)
+        --chunks_per_piece;
     if (chunks_per_piece == 0) return SF_ERR_OOM;
     const uint64_t piece = chunks_per_piece * S;
     const uint64_t keys_half = (piece * kb + 15) & ~15ull;  // the operations of a half follow its keys
@@ -377,7 +382,8 @@ sf_status sf_update_pipelined(sf_sketch* s, const void* keys_host, const int8_t*
                               uint64_t n, void* staging_dev, uint64_t staging_bytes, void* copy_stream) {
     if (!s) return SF_ERR_INVALID;
     if (n == 0) return SF_OK;
-    if (!staging_dev || !pipeline_args_ok(keys_host, ops_host, op_const)) return SF_ERR_INVALID;
+    if (!staging_dev || !aligned16(staging_dev) || !pipeline_args_ok(keys_host, ops_host, op_const))
+        return SF_ERR_INVALID;
     DeviceGuard guard(s->device);
     if (!guard.ok) return SF_ERR_CUDA;
     sf_pipeline* p = new (std::nothrow) sf_pipeline();

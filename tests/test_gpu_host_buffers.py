@@ -103,6 +103,39 @@ def test_pipelined_update_from_host_equals_one_call(sf, kb, S, with_ops):
     assert ei.value.status == sf.SF_ERR_OOM
 
 
+@pytest.mark.parametrize("kb,S,with_ops", [(13, 1000, True), (13, 999, False), (4, 1001, True), (8, 4096, True)])
+def test_pipelined_staging_at_the_documented_minimum(sf, kb, S, with_ops):
+    """Staging of exactly 2 * (chunk * (key_bytes + ops) + 32) bytes, 16-byte aligned, holds a piece
+    of one chunk whatever the padding of its keys: here every piece is one chunk (both halves reused
+    many times, a ragged last piece) and the counters equal one device-resident call.  Less than two
+    chunks' bytes is SF_ERR_OOM; a staging buffer off a 16-byte boundary is SF_ERR_INVALID."""
+    import torch
+    st, _ = wl.mixed_stream(7 * S + 123, 3_000, 1.0, 0.2 if with_ops else 0.0, 4, seed=kb + S)
+    keys = st.keys if kb == 4 else torch.cat([st.keys] * 4, 1)[:, :kb].contiguous()
+    per = kb + (1 if with_ops else 0)
+    a = sf.Sketch(4, 1500, 16, kb, 6, S)
+    b = sf.Sketch(4, 1500, 16, kb, 6, S)
+    ops = st.ops if with_ops else None
+    if ops is not None:
+        a.update(keys.cuda(), ops.cuda())
+    else:
+        a.insert(keys.cuda())
+    staging = torch.empty(2 * (S * per + 32), dtype=torch.uint8, device="cuda")
+    b.update_pipelined(_pinned(keys), _pinned(ops) if ops is not None else None, 1, staging=staging)
+    a.sync()
+    b.sync()
+    assert torch.equal(a.fat, b.fat) and torch.equal(a.slim, b.slim)
+    small = torch.empty(2 * S * per - 2, dtype=torch.uint8, device="cuda")
+    with pytest.raises(sf.SFError) as ei:
+        b.update_pipelined(_pinned(keys), _pinned(ops) if ops is not None else None, 1, staging=small)
+    assert ei.value.status == sf.SF_ERR_OOM
+    off = torch.empty(2 * (S * per + 32) + 16, dtype=torch.uint8, device="cuda")[8:]
+    with pytest.raises(sf.SFError) as ei:
+        b.update_pipelined(_pinned(keys), _pinned(ops) if ops is not None else None, 1, staging=off)
+    assert ei.value.status == sf.SF_ERR_INVALID
+    assert b.sync_status() == sf.SF_OK
+
+
 @pytest.mark.gpu
 def test_pipeline_kept_across_calls_and_sketches(sf):
     """sf_update_pipeline: one pipeline (small staging: several pieces per call) serves calls of two
