@@ -426,7 +426,9 @@ sf_status sfc_evict(sfc *c, uint32_t sketch_id);
 sf_status sfc_query_submit(sfc *c, uint32_t sketch_id, const void *keys_host, uint64_t n, uint32_t *out_host,
                            uint64_t *ticket);
 
-/* SF_OK when the ticket finished (the ticket is then released), SF_PENDING otherwise. */
+/* The ticket's status once it finished (the ticket is then released): SF_OK, or SF_ERR_CUDA when
+ * its batch could not be launched or its completion event reported a device error (out_host is
+ * then not written); SF_PENDING while it runs. */
 sf_status sfc_poll(sfc *c, uint64_t ticket);
 
 /* Blocks until the ticket finished; then like sfc_poll. */

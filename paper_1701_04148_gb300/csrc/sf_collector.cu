@@ -181,26 +181,37 @@ struct sfc {
         cudaSetDevice(device);
         std::unique_lock<std::mutex> lk(mu);
         while (true) {
-            // finished batches: copy their answers out of pinned staging (unlocked), then complete
+            // finished batches: copy their answers out of pinned staging (unlocked), then complete; a
+            // batch whose event reports an error (not just "not ready") completes with SF_ERR_CUDA, so
+            // no request waits on it forever
             bool any_busy = false;
             Slot* fin[16];
+            bool failed[16];
             uint32_t nfin = 0;
             lk.unlock();
             for (auto& s : slots) {
                 if (!s.busy) continue;
-                if (cudaEventQuery(s.ev) == cudaSuccess) {
+                const cudaError_t q = cudaEventQuery(s.ev);
+                if (q == cudaErrorNotReady) {
+                    any_busy = true;
+                    continue;
+                }
+                if (q == cudaSuccess) {
                     uint64_t off = 0;
                     for (auto& r : s.members) {
                         if (r->n) std::memcpy(r->out, s.out_host + off, r->n * sizeof(uint32_t));
                         off += r->n;
                     }
-                    fin[nfin++] = &s;
-                } else {
-                    any_busy = true;
                 }
+                failed[nfin] = q != cudaSuccess;
+                fin[nfin++] = &s;
             }
             lk.lock();
-            for (uint32_t f = 0; f < nfin; ++f) complete(*fin[f]);
+            for (uint32_t f = 0; f < nfin; ++f) {
+                if (failed[f])
+                    for (auto& r : fin[f]->members) r->status = SF_ERR_CUDA;
+                complete(*fin[f]);
+            }
             if (stop && pending.empty() && !any_busy) break;
             // launch as many batches as free slots and pending work allow
             bool launched = false;
