@@ -178,8 +178,8 @@ sf_status sf_set_index_table(sf_sketch *s, const uint32_t *table_dev, uint32_t n
  *   sf_set_dictionary: dict_dev, 16-byte aligned device memory of at least that many bytes, is the
  *     dictionary of the sketch's standalone updates (sf_update_batch and the calls built on it);
  *     the call zeroes it on the sketch's stream.  The caller keeps it alive, and lets no two
- *     updates that use it run at the same time.  After an update returns SF_ERR_TIMEOUT call it
- *     again (it re-zeroes).  SF_ERR_INVALID for a sketch without the flag or too small a buffer.
+ *     updates that use it run at the same time.  The sf_sync that returns SF_ERR_TIMEOUT re-zeroes
+ *     it with the scratch.  SF_ERR_INVALID for a sketch without the flag or too small a buffer.
  *     A flagged sketch with chunk > 1 and no dictionary refuses standalone updates
  *     (SF_ERR_INVALID).
  */

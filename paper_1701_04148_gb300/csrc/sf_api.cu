@@ -437,16 +437,20 @@ sf_status sf_sync(sf_sketch* s) {
         return SF_ERR_CUDA;
     if (cudaStreamSynchronize(s->stream) != cudaSuccess) return SF_ERR_CUDA;
     if (err == 0) return SF_OK;
+    cudaError_t e;
     if (err & sfk::kErrTimeout) {
-        // a grid wait gave up: barrier words and dictionary may be inconsistent; reset them
+        // a grid wait gave up: barrier words and dictionary may be inconsistent; reset them (a
+        // dictionary set by sf_set_dictionary too)
         uint64_t xb = 0;
         sf_required_bytes(&s->p, nullptr, nullptr, &xb);
-        cudaMemsetAsync(s->scratch, 0, xb, s->stream);
+        e = cudaMemsetAsync(s->scratch, 0, xb, s->stream);
+        if (e == cudaSuccess && (s->p.flags & SF_FLAG_SHARED_DICT) && s->dict)
+            e = cudaMemsetAsync(s->dict, 0, (uint64_t)s->cap * sizeof(sfk::DictEntry), s->stream);
         s->bar_epoch = 0;
     } else {
-        cudaMemsetAsync(s->ctrl + sfk::kCtrlErr, 0, 4, s->stream);
+        e = cudaMemsetAsync(s->ctrl + sfk::kCtrlErr, 0, 4, s->stream);
     }
-    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return SF_ERR_CUDA;
+    if (e != cudaSuccess || cudaStreamSynchronize(s->stream) != cudaSuccess) return SF_ERR_CUDA;
     if (err & sfk::kErrTimeout) return SF_ERR_TIMEOUT;
     if (err & (sfk::kErrBadKey | sfk::kErrDictFull)) return SF_ERR_INVALID;
     if (err & sfk::kErrUnderflow) return SF_ERR_UNDERFLOW;
