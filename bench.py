@@ -627,9 +627,11 @@ def run_flows(args, ctx):
                               "link_GBps_before_each: a plain 416 MB pinned host-to-device copy timed just "
                               "before each repetition")
         direct_ = median_rep("direct")
-        direct_["transfer"] = ("pinned host buffers passed to the same calls: the update kernel reads each key "
-                               "over the host link as it consumes it, the query kernel writes the answers to "
-                               "host memory; no staging copy")
+        direct_["transfer"] = ("pinned host buffers passed to the same calls: the update calls copy the keys in "
+                               "pieces of whole chunks into the idle half of each sketch's dictionary region "
+                               "on a copy stream of the sketch's own, each piece applied while the next is "
+                               "copied; the query kernel reads the pinned flow keys and writes the answers to "
+                               "host memory")
         e2e["direct"] = direct_
         staged = median_rep("staged")
         staged["transfer"] = "cudaMemcpyAsync of the keys to device buffers, kernels, copy of the answers back"

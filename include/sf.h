@@ -38,8 +38,14 @@
  * sf_update_batch_noalloc), operations, and query answers (sf_query_batch out_dev) may be device
  * or managed memory, or page-locked host memory (cudaHostAlloc / cudaHostRegister): the kernels
  * then read the keys and write the answers over the host link themselves, with no staging
- * copy.  Each pointer is checked with cudaPointerGetAttributes before any launch; pageable host
- * memory returns SF_ERR_INVALID.  Fat, Slim and scratch buffers are device memory.
+ * copy -- except the update calls of a sketch that owns its dictionary and whose chunks (2 to
+ * 65,536 updates) fit one round of the grid, given page-locked keys and page-locked (or no)
+ * operations: those copy them, in pieces of whole chunks, into the half of the sketch's dictionary
+ * region that such rounds leave unused, on a copy stream the sketch creates at its first such call,
+ * each piece applied while the next is copied (pieces under 262,144 updates, unless one piece holds
+ * the whole call, read over the link instead).  Either way the host buffers stay in use until
+ * sf_sync returns.  Each pointer is checked with cudaPointerGetAttributes before any launch;
+ * pageable host memory returns SF_ERR_INVALID.  Fat, Slim and scratch buffers are device memory.
  *
  * Errors.  No exception crosses the ABI.  Argument errors return immediately; errors found
  * on the device are latched in the scratch buffer and returned by the next sf_sync.

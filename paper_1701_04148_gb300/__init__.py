@@ -294,6 +294,12 @@ class Sketch:
                               self.scratch.data_ptr(), _stream_handle(self.stream), ctypes.byref(h)), "sf_create")
         self.handle = h
         self._index_table = None
+        self._held = []  # host tensors of calls in flight: the copies and kernels read them later
+
+    def _hold(self, *tensors):
+        for t in tensors:
+            if t is not None and t.device.type == "cpu":
+                self._held.append(t)
 
     def reset(self):
         """Initialisation again (Sec. 3.1: all counters zero) on the same device buffers (sf_reset)."""
@@ -342,16 +348,19 @@ class Sketch:
     def insert(self, keys):
         k, n = self._keys(keys)
         check(load().sf_insert_batch(self.handle, _io_ptr(k, "keys"), n), "sf_insert_batch")
+        self._hold(k)
 
     def delete(self, keys):
         k, n = self._keys(keys)
         check(load().sf_delete_batch(self.handle, _io_ptr(k, "keys"), n), "sf_delete_batch")
+        self._hold(k)
 
     def update(self, keys, ops):
         k, n = self._keys(keys)
         if ops.numel() != n:
             raise ValueError("ops must have one entry per key")
         check(load().sf_update_batch(self.handle, _io_ptr(k, "keys"), _io_ptr(ops, "ops"), n), "sf_update_batch")
+        self._hold(k, ops)
 
     def update_pipelined(self, keys_host, ops_host=None, op_const: int = 1, staging=None, copy_stream=None):
         """sf_update_pipelined: host keys (pinned CPU tensor) copied in chunk-aligned pieces on
@@ -384,10 +393,14 @@ class Sketch:
               "sf_update_pipeline")
 
     def sync(self) -> int:
-        return check(load().sf_sync(self.handle), "sf_sync")
+        st = load().sf_sync(self.handle)
+        self._held = []
+        return check(st, "sf_sync")
 
     def sync_status(self) -> int:
-        return load().sf_sync(self.handle)
+        st = load().sf_sync(self.handle)
+        self._held = []
+        return st
 
     def export_slim(self, out=None):
         torch = _torch()

@@ -21,6 +21,11 @@ constexpr uint64_t kCtrlBytes = 256;
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
+// defined with the pipeline below
+sf_status run_staged(sf_sketch* s, const void* keys_host, const int8_t* ops_host, int op_const, uint64_t n,
+                     bool* staged);
+void pipeline_release(sf_pipeline* p);
+
 sfk::SketchDesc desc_of(const sf_sketch* s) {
     sfk::SketchDesc d{};
     d.A = s->A;
@@ -50,6 +55,17 @@ sf_status run_update(sf_sketch* s, const void* keys_in, const int8_t* ops_in, in
     if ((s->p.flags & SF_FLAG_EXPLICIT_INDEX) && !s->idx_table) return SF_ERR_INVALID;
     DeviceGuard guard(s->device);
     if (!guard.ok) return SF_ERR_CUDA;
+    // page-locked host keys (and operations) of a sketch whose chunk rounds run the single-iteration
+    // kernel: staged through the idle half of its dictionary region, so that kernel reads them from
+    // device memory (the one that reads host keys itself waits on the host link every round)
+    const bool single = s->p.chunk > 1 && sfk::chunk_rounds_single(sfk::round_up32(s->p.chunk), s->p.chunk,
+                                                                   s->chunk_grid, keys_host || ops_host);
+    if (keys_host && (!ops || ops_host) && s->p.chunk > 1 && !(s->p.flags & SF_FLAG_SHARED_DICT) && s->dict &&
+        sfk::chunk_rounds_single(sfk::round_up32(s->p.chunk), s->p.chunk, s->chunk_grid)) {
+        bool staged = false;
+        const sf_status st = run_staged(s, keys_in, ops_in, op_const, n, &staged);
+        if (staged || st != SF_OK) return st;
+    }
     cudaError_t e;
     if (s->p.chunk == 1 && s->dag_ws && !ops && op_const > 0) {
         // insertions only: the dependency-graph path (sf_seqdag.cu)
@@ -65,6 +81,9 @@ sf_status run_update(sf_sketch* s, const void* keys_in, const int8_t* ops_in, in
         e = sfk::launch_seq_update(a, s->stream, s->smem_optin);
     } else {
         if (!s->dict) return SF_ERR_INVALID;  // SF_FLAG_SHARED_DICT without sf_set_dictionary
+        // the multi-iteration kernel reads the whole dictionary region
+        if (!single && !(s->p.flags & SF_FLAG_SHARED_DICT) && sf_stage_release(s, s->stream) != SF_OK)
+            return SF_ERR_CUDA;
         sfk::SketchRun one{};
         one.s = desc_of(s);
         one.keys = (const uint8_t*)keys;
@@ -165,6 +184,7 @@ sf_status sf_create(const sf_params* p, void* fat_dev, void* slim_dev, void* scr
         return SF_ERR_CUDA;
     }
     s->chunk_grid = s->num_sms * (bps < 2 ? bps : 2);
+    s->stage_foreign = true;  // the first staged call waits for the sketch's earlier work
     s->claims_cap = sfk::chunk_claims_cap(sfk::round_up32(p->chunk), s->chunk_grid);
     s->bar_epoch = 0;
     uint64_t fb, sb, xb;
@@ -181,6 +201,11 @@ sf_status sf_create(const sf_params* p, void* fat_dev, void* slim_dev, void* scr
 
 sf_status sf_destroy(sf_sketch* s) {
     if (!s) return SF_ERR_INVALID;
+    {
+        DeviceGuard guard(s->device);
+        if (s->stage_pipe) pipeline_release(s->stage_pipe);  // its events go once their work completed
+        if (s->stage_cs) cudaStreamDestroy(s->stage_cs);
+    }
     delete s;
     return SF_OK;
 }
@@ -336,17 +361,20 @@ sf_status pipeline_init(sf_pipeline* p, void* staging_dev, uint64_t staging_byte
 // The pieces of one call: whole chunks that fit a half (keys, then the operations 16-byte aligned),
 // each copied on the pipeline's copy stream once the last update that read its half is done, and
 // applied on the sketch's stream once it has landed.
+// Updates per piece: the largest whole number of chunks whose keys (padded to a 16-byte multiple)
+// and operations fit a half of half_bytes; 0 when not even one chunk does.
+uint64_t pipeline_piece(uint64_t half_bytes, uint64_t S, uint64_t kb, bool with_ops) {
+    const uint64_t per = kb + (with_ops ? 1u : 0u);
+    uint64_t c = half_bytes / (S * per);
+    while (c > 0 && ((c * S * kb + 15) & ~15ull) + (with_ops ? c * S : 0) > half_bytes) --c;
+    return c * S;
+}
+
 sf_status pipeline_run(sf_sketch* s, sf_pipeline* p, const void* keys_host, const int8_t* ops_host, int32_t op_const,
                        uint64_t n) {
-    const uint64_t kb = s->p.key_bytes, per = kb + (ops_host ? 1u : 0u), S = s->p.chunk;
-    // the largest whole number of chunks whose keys (padded to a 16-byte multiple) and operations fit
-    // a half
-    uint64_t chunks_per_piece = p->half_bytes / (S * per);
-    while (chunks_per_piece > 0 &&
-           ((chunks_per_piece * S * kb + 15) & ~15ull) + (ops_host ? chunks_per_piece * S : 0) > p->half_bytes)
-        --chunks_per_piece;
-    if (chunks_per_piece == 0) return SF_ERR_OOM;
-    const uint64_t piece = chunks_per_piece * S;
+    const uint64_t kb = s->p.key_bytes;
+    const uint64_t piece = pipeline_piece(p->half_bytes, s->p.chunk, kb, ops_host != nullptr);
+    if (piece == 0) return SF_ERR_OOM;
     const uint64_t keys_half = (piece * kb + 15) & ~15ull;  // the operations of a half follow its keys
     for (uint64_t off = 0; off < n;) {
         const uint64_t len = n - off < piece ? n - off : piece;
@@ -372,6 +400,49 @@ sf_status pipeline_run(sf_sketch* s, sf_pipeline* p, const void* keys_host, cons
 
 bool pipeline_args_ok(const void* keys_host, const int8_t* ops_host, int32_t op_const) {
     return keys_host && (ops_host || op_const == 1 || op_const == -1);
+}
+
+// A staged call whose pieces would be smaller than this many updates reads the host keys in the
+// kernel instead (many short launches would cost more than the link's latency).
+constexpr uint64_t kStageMinPiece = 1ull << 18;
+
+// The update calls' own pipeline: the upper half of the sketch's dictionary region (cap x 16 bytes;
+// the single-iteration kernel's two halves of 8-byte claim entries fill the lower half) and a copy
+// stream of the sketch's own.  *staged is false when the call should read the keys in the kernel.
+sf_status run_staged(sf_sketch* s, const void* keys_host, const int8_t* ops_host, int op_const, uint64_t n,
+                     bool* staged) {
+    *staged = false;
+    const uint64_t region = (uint64_t)s->cap * 16ull;
+    const uint64_t piece = pipeline_piece((region / 2) & ~15ull, s->p.chunk, s->p.key_bytes, ops_host != nullptr);
+    if (piece == 0 || (n > piece && piece < kStageMinPiece)) return SF_OK;
+    if (!s->stage_pipe) {
+        cudaStream_t cs = nullptr;
+        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return SF_ERR_CUDA;
+        sf_pipeline* p = new (std::nothrow) sf_pipeline();
+        if (!p) {
+            cudaStreamDestroy(cs);
+            return SF_ERR_OOM;
+        }
+        if (pipeline_init(p, reinterpret_cast<uint8_t*>(s->dict) + region, region, cs) != SF_OK) {
+            pipeline_release(p);
+            cudaStreamDestroy(cs);
+            return SF_ERR_CUDA;
+        }
+        s->stage_pipe = p;
+        s->stage_cs = cs;
+    }
+    sf_pipeline* p = s->stage_pipe;
+    if (s->stage_foreign) {
+        // a launch that read the whole region (or the sketch's creation) came since the last staged
+        // call: the first copies wait for the sketch's stream
+        if (cudaEventRecord(p->used[0], s->stream) != cudaSuccess || cudaEventRecord(p->used[1], s->stream) != cudaSuccess)
+            return SF_ERR_CUDA;
+        p->used_recorded[0] = p->used_recorded[1] = true;
+        s->stage_foreign = false;
+    }
+    *staged = true;
+    s->stage_dirty = true;
+    return pipeline_run(s, p, keys_host, ops_host, op_const, n);
 }
 
 }  // namespace
@@ -447,6 +518,8 @@ sf_status sf_sync(sf_sketch* s) {
         if (e == cudaSuccess && (s->p.flags & SF_FLAG_SHARED_DICT) && s->dict)
             e = cudaMemsetAsync(s->dict, 0, (uint64_t)s->cap * sizeof(sfk::DictEntry), s->stream);
         s->bar_epoch = 0;
+        s->stage_dirty = false;   // the staged half went with the scratch
+        s->stage_foreign = true;
     } else {
         e = cudaMemsetAsync(s->ctrl + sfk::kCtrlErr, 0, 4, s->stream);
     }

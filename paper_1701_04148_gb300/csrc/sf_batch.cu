@@ -170,6 +170,10 @@ sf_status sf_batch_update(sf_batch* b, uint32_t n_items, const sf_batch_item* it
     DeviceGuard guard(b->device);
     if (!guard.ok) return SF_ERR_CUDA;
     if (b->staging_busy && cudaEventSynchronize(b->staged) != cudaSuccess) return SF_ERR_CUDA;
+    // a sketch's own dictionary region must read as empty: zero what its staged calls left there
+    // (only sketches that own their dictionary stage anything)
+    for (uint32_t i = 0; i < n_items; ++i)
+        if (sf_stage_release(items[i].sketch, b->stream) != SF_OK) return SF_ERR_CUDA;
 
     // every launch shape keeps 512 threads per SM: 512 / block co-resident blocks of `block` threads
     const int block = b->block;

@@ -91,5 +91,26 @@ struct sf_sketch {
     uint64_t bar_epoch;     // grid barriers passed on this scratch buffer (monotonic counter)
     uint32_t claims_cap;    // per-block claim list length of the chunk kernel
     void* dag_ws;           // S = 1 sketches of width >= kDagMinW: workspace of the graph path, else nullptr
+    // Update calls with page-locked host keys stage them through the upper half of the dictionary
+    // region (unused by the single-iteration kernel) on a copy stream of their own, created at the
+    // first such call.  stage_dirty: that half holds staged bytes, so it is zeroed before a launch
+    // that reads the whole region as a dictionary; stage_foreign: such a launch ran since the last
+    // staged call, so the next one waits for the sketch's stream before its first copy.
+    sf_pipeline* stage_pipe;
+    cudaStream_t stage_cs;
+    bool stage_dirty, stage_foreign;
 };
+
+// Zeroes the staged half of a sketch's dictionary region on `st` before a launch that reads the
+// whole region (the multi-iteration kernel, a batch), and marks the region as used by it.
+inline sf_status sf_stage_release(sf_sketch* s, cudaStream_t st) {
+    if (s->stage_dirty) {
+        if (cudaMemsetAsync(reinterpret_cast<uint8_t*>(s->dict) + (uint64_t)s->cap * 16ull, 0,
+                            (uint64_t)s->cap * 16ull, st) != cudaSuccess)
+            return SF_ERR_CUDA;
+        s->stage_dirty = false;
+    }
+    s->stage_foreign = true;
+    return SF_OK;
+}
 

@@ -176,3 +176,61 @@ def test_pipeline_kept_across_calls_and_sketches(sf):
     buf = torch.empty(4096, dtype=torch.uint8, device="cuda")
     h = ctypes.c_void_p()
     assert L.sf_pipeline_create(buf.data_ptr() + 8, 1024, 0, ctypes.byref(h)) == sf.SF_ERR_INVALID
+
+
+def test_update_calls_stage_pinned_keys_through_the_idle_dictionary_half(sf):
+    """Update calls on pinned host keys of sketches whose chunk rounds run the single-iteration
+    kernel (chunk <= 65,536) stage them through the idle upper half of the sketch's dictionary
+    region (pieces of whole chunks on a copy stream of the sketch's own).  Several staged calls
+    (insertions, deletions, mixed operations; several pieces each and one short piece), device-key
+    calls between them, and then a batch of two such sketches -- whose multi-iteration launch reads
+    the whole region as its dictionary, so the staged bytes must have been zeroed -- all leave the
+    counters equal to the same calls made with device keys."""
+    import torch
+    ins, dels, _ = wl.flows_with_deletes(1_400_000, 60_000, 1.0, 0.1, seed=95)
+    st, _ = wl.mixed_stream(700_000, 30_000, 1.1, 0.2, 4, seed=96)
+    keys13 = torch.cat([st.keys] * 4, 1)[:, :13].contiguous()
+    a1, b1 = sf.Sketch(4, 20011, 16, 13, 7, 65536), sf.Sketch(4, 20011, 16, 13, 7, 65536)
+    a2, b2 = sf.Sketch(4, 5003, 16, 13, 8, 4096), sf.Sketch(4, 5003, 16, 13, 8, 4096)
+    calls = [
+        (a1, b1, ins, None, 1),              # 22 chunks: several pieces of 9 chunks
+        (a1, b1, keys13, st.ops, 0),         # mixed operations, staged with their ops
+        (a2, b2, ins[:30_000], None, 1),     # one piece (9 chunks of 4,096 hold 36,864 updates)
+        (a1, b1, dels, None, -1),
+    ]
+    held = []                                # host buffers stay alive until the sketches synced
+    for a, b, keys, ops, op in calls:
+        kd = keys.cuda()
+        kh = _pinned(keys)
+        oh = _pinned(ops) if ops is not None else None
+        held += [kh, oh]
+        if ops is not None:
+            a.update(kd, ops.cuda())
+            b.update(kh, oh)
+        elif op > 0:
+            a.insert(kd)
+            b.insert(kh)
+        else:
+            a.delete(kd)
+            b.delete(kh)
+        b.insert(ins[:5_000].cuda())         # a device-key call between staged calls
+        a.insert(ins[:5_000].cuda())
+    for s in (a1, b1, a2, b2):
+        assert s.sync_status() == sf.SF_OK
+    assert torch.equal(a1.fat, b1.fat) and torch.equal(a1.slim, b1.slim)
+    assert torch.equal(a2.fat, b2.fat) and torch.equal(a2.slim, b2.slim)
+    # two chunks of 65,536 in one round: the multi-iteration kernel, over both whole regions
+    more = ins[200_000:500_000].cuda()
+    for x, y in ((a1, a2), (b1, b2)):
+        bt = sf.Batch(2)
+        bt.update([(x, more, None), (y, more[:100_000], None)])
+        assert bt.sync_status() == sf.SF_OK
+        bt.close()
+    assert torch.equal(a1.fat, b1.fat) and torch.equal(a1.slim, b1.slim)
+    assert torch.equal(a2.fat, b2.fat) and torch.equal(a2.slim, b2.slim)
+    # and staged again after the batch
+    kh = _pinned(ins[:300_000])
+    a1.insert(ins[:300_000].cuda())
+    b1.insert(kh)
+    assert a1.sync_status() == sf.SF_OK and b1.sync_status() == sf.SF_OK
+    assert torch.equal(a1.fat, b1.fat) and torch.equal(a1.slim, b1.slim)
