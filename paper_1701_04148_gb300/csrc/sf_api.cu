@@ -358,9 +358,6 @@ sf_status pipeline_init(sf_pipeline* p, void* staging_dev, uint64_t staging_byte
     return SF_OK;
 }
 
-// The pieces of one call: whole chunks that fit a half (keys, then the operations 16-byte aligned),
-// each copied on the pipeline's copy stream once the last update that read its half is done, and
-// applied on the sketch's stream once it has landed.
 // Updates per piece: the largest whole number of chunks whose keys (padded to a 16-byte multiple)
 // and operations fit a half of half_bytes; 0 when not even one chunk does.
 uint64_t pipeline_piece(uint64_t half_bytes, uint64_t S, uint64_t kb, bool with_ops) {
@@ -370,6 +367,9 @@ uint64_t pipeline_piece(uint64_t half_bytes, uint64_t S, uint64_t kb, bool with_
     return c * S;
 }
 
+// The pieces of one call: whole chunks that fit a half (keys, then the operations 16-byte aligned),
+// each copied on the pipeline's copy stream once the last update that read its half is done, and
+// applied on the sketch's stream once it has landed.
 sf_status pipeline_run(sf_sketch* s, sf_pipeline* p, const void* keys_host, const int8_t* ops_host, int32_t op_const,
                        uint64_t n) {
     const uint64_t kb = s->p.key_bytes;
