@@ -438,3 +438,19 @@ def test_both_update_kernels_at_the_chunk_size_boundary(sf, S):
     st, ids = wl.mixed_stream(300_001, 30_000, 1.2, 0.2, 8, seed=82)
     g, o = _run_both(sf, 4, 5000, 16, 8, 9, S, [(st.keys, st.ops)])
     _assert_same(g, o)
+
+
+@pytest.mark.parametrize("S", [65_536, 1 << 20])
+def test_maximum_parameters(sf, S):
+    """Every parameter at its limit at once: d = SF_MAX_D (8) rows, buckets of SF_MAX_Z (64)
+    counters, SF_MAX_KEY_BYTES (15)-byte keys, and chunks of 65,536 (the single-iteration kernel's
+    largest) or SF_MAX_CHUNK (2^20, multi-iteration) updates, over two whole chunks and a ragged
+    tail of a strict-turnstile stream: counters and queries equal the oracle's."""
+    import torch
+    n = 2 * S + 12_345
+    st, ids = wl.mixed_stream(n, 50_000, 1.0, 0.2, 8, seed=S % 997)
+    keys = torch.cat([st.keys, st.keys], 1)[:, :15].contiguous()
+    qk = torch.cat([ids, ids], 1)[:, :15].contiguous()
+    g, o = _run_both(sf, 8, 3001, 64, 15, 11, S, [(keys, st.ops)])
+    _assert_same(g, o)
+    _queries_match(sf, g, o, qk)
